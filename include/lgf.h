@@ -1,0 +1,174 @@
+/*
+ * lgf -- Fourier-accelerated steepest-descent Landau gauge fixing of SU(3)
+ * lattice gauge fields on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: N. Cardoso, P. J. Silva, P. Bicudo, O. Oliveira, "Landau Gauge
+ * Fixing on GPUs", arXiv:1206.0675.  Section 2 defines every quantity used
+ * here: the gauge transformation (eq. 2), the functional F (eq. 3), the
+ * Fourier-accelerated transform g(x) (Eq. (eq:gx)), the lattice divergence
+ * Delta(x) and the stopping quantity theta; Algorithm 1 is the loop.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Lattice: extents[4] = {Lx, Ly, Lz, Lt}, periodic in all directions,
+ *   V = Lx*Ly*Lz*Lt sites numbered s = x + Lx*(y + Ly*(z + Lz*t)).
+ *   Directions mu = 0, 1, 2, 3 are x, y, z, t.
+ * Link layout (user side, FP64): U[mu][t][z][y][x][row][col][re, im], i.e.
+ *   4*V*18 doubles, each 3x3 complex matrix row-major with interleaved real
+ *   and imaginary parts.  Site fields (g, G, Delta) use the same layout
+ *   without the leading mu: V*18 doubles.
+ * where: LGF_HOST means a host pointer (any host memory; pinned memory gives
+ *   the fastest copies), LGF_DEVICE a device pointer on the handle's device.
+ * Ownership: the caller owns every buffer it passes; the library copies in
+ *   and out and never keeps a caller pointer beyond the call, except the
+ *   history buffers registered with lgf_set_trace.  The library owns its
+ *   device workspace (allocated in lgf_create, freed in lgf_destroy).
+ * Streams: all device work of a handle runs on the stream given to
+ *   lgf_create (NULL = the legacy default stream).  lgf_step is asynchronous;
+ *   every call that returns numbers to the host synchronises that stream.
+ * Errors: every call returns an lgf_status and never aborts; no C++
+ *   exception crosses this interface.  A CUDA error is sticky for the handle:
+ *   afterwards only lgf_destroy and lgf_last_error are meaningful.
+ * Threads: a handle may be used by one host thread at a time.
+ *
+ * Readings of the paper fixed by this library
+ * -------------------------------------------
+ *  - theta = (1/(3V)) sum_x Tr[Delta Delta^dagger] with the paper's Delta,
+ *    which is built from U - U^dagger and so equals 2 Delta_A, Delta_A being
+ *    the divergence of the traceless anti-Hermitian parts A_mu of the links.
+ *  - The Fourier filter is K(k) = alpha * p2max / p2(k) with
+ *    p2(k) = sum_mu 4 sin^2(pi k_mu / L_mu) and K(0) = 0.
+ *  - g(x) = reunitarize(1 + F^-1[K F[Delta_A]](x)): the exponential expanded
+ *    to first order, then Gram-Schmidt on rows 1-2 and row 3 = (a x b)^*.
+ *  - Algorithm 1 iterates while theta >= tol; the iteration count is the
+ *    number of link updates.
+ */
+#ifndef LGF_H
+#define LGF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lgf_ctx* lgf_handle;
+
+typedef enum {
+  LGF_OK = 0,
+  LGF_E_ARG = 1,          /* bad argument, or input links not in SU(3) within 1e-10 */
+  LGF_E_NOMEM = 2,        /* device or pinned host allocation failed */
+  LGF_E_CUDA = 3,         /* a CUDA call failed; the handle is now unusable */
+  LGF_E_STATE = 4,        /* call not valid in the handle's state (e.g. no links set) */
+  LGF_E_NONFINITE = 5,    /* non-finite input links, F or theta */
+  LGF_E_NOTCONV = 6,      /* lgf_fix reached max_iter with theta >= tol */
+  LGF_E_TIMEOUT = 7,      /* a bounded device wait gave up */
+  LGF_E_UNSUPPORTED = 8   /* extents or options this build does not handle */
+} lgf_status;
+
+typedef enum {
+  LGF_FP64 = 0,   /* FP64 links, FFTs and updates throughout */
+  LGF_FP32 = 1,   /* FP32 links, Delta and FFTs; FP64 reductions and reunitarisation */
+  LGF_MIXED = 2   /* FP32 phase until theta < switch level, then FP64 rebuilt from the FP64 input */
+} lgf_precision;
+
+enum {
+  LGF_STORE18 = 0,        /* keep all three rows of each link (18 reals) */
+  LGF_STORE12 = 1 << 0,   /* keep rows 1-2 (12 reals), rebuild row 3 = (a x b)^* (Sec. 3.2) */
+  LGF_TRACK_G = 1 << 1,   /* accumulate G(x) = g_k(x)...g_1(x) for lgf_get_transform */
+  LGF_PLAIN_SD = 1 << 3   /* plain steepest descent: filter K(k) = alpha (no Fourier acceleration) */
+};
+
+enum { LGF_HOST = 0, LGF_DEVICE = 1 };
+
+/* Create a handle for one lattice.
+ * extents: {Lx, Ly, Lz, Lt}; each must be 2^a 3^b with 2 <= L <= 128, and
+ *   the (x,y) and (z,t) planes must fit the shared-memory FFT passes
+ *   (all extents up to 96, and 128 in z and t, are accepted); otherwise
+ *   LGF_E_UNSUPPORTED.
+ * prec: LGF_FP64, LGF_FP32 or LGF_MIXED.  flags: LGF_STORE12, LGF_TRACK_G,
+ *   LGF_PLAIN_SD (LGF_MIXED always tracks G).
+ * cuda_stream: a cudaStream_t or NULL.  out: receives the handle.
+ * Allocates all device workspace up front (LGF_E_NOMEM if it does not fit). */
+lgf_status lgf_create(const int32_t extents[4], lgf_precision prec, uint32_t flags, void* cuda_stream,
+                      lgf_handle* out);
+
+/* Free the handle and its device memory.  NULL is accepted. */
+lgf_status lgf_destroy(lgf_handle h);
+
+/* Copy links in (layout above) and make them the current configuration.
+ * Resets G = 1 and the iteration counter, and measures F and theta.
+ * Links must be finite (else LGF_E_NONFINITE) and in SU(3):
+ * max(|U U^dag - 1|, |det U - 1|) <= 1e-10 (else LGF_E_ARG).
+ * Synchronises the handle's stream. */
+lgf_status lgf_set_links(lgf_handle h, const double* U, int where);
+
+/* Copy the current links out as FP64 18-real matrices (12-real storage is
+ * expanded with row 3 = (a x b)^*).  Synchronises. */
+lgf_status lgf_get_links(lgf_handle h, double* U, int where);
+
+/* One body of Algorithm 1: 4D FFT of Delta, filter K(k) (alpha given here),
+ * inverse FFT, g = reunitarize(1 + Delta'), U -> g U g^dag(x+mu), then the
+ * measurement of Delta, F and theta.  Asynchronous (enqueued on the stream).
+ * In LGF_MIXED mode the step runs in the phase the handle is in. */
+lgf_status lgf_step(lgf_handle h, double alpha);
+
+/* F and theta of the current links (Sec. 2, eq. 3 and the theta formula).
+ * Either pointer may be NULL.  Synchronises. */
+lgf_status lgf_measure(lgf_handle h, double* F, double* theta);
+
+/* Algorithm 1: iterate lgf_step while theta >= theta_tol, at most max_iter
+ * updates, with the loop condition evaluated on the device (CUDA graph with
+ * a WHILE node; no host round trip per iteration).  In LGF_MIXED mode the
+ * FP32 phase runs while theta >= max(theta_tol, switch level 1e-9), then G is
+ * projected to SU(3) in FP64, U = G U0 G^dag(x+mu) is rebuilt in FP64 from
+ * the FP64 input U0, and the FP64 phase runs to theta_tol.
+ * iters, F, theta (each may be NULL) receive the update count of this call
+ * and the final measurement.  Returns LGF_E_NOTCONV when max_iter is hit,
+ * LGF_E_NONFINITE when F or theta became non-finite.  Synchronises. */
+lgf_status lgf_fix(lgf_handle h, double theta_tol, int32_t max_iter, double alpha, int32_t* iters, double* F,
+                   double* theta);
+
+/* Copy out the accumulated transform G(x) (site layout, FP64), such that the
+ * current links equal G(x) U_in(x) G^dag(x+mu) for the links given to
+ * lgf_set_links.  LGF_E_STATE unless the handle tracks G.  Synchronises. */
+lgf_status lgf_get_transform(lgf_handle h, double* G, int where);
+
+/* Copy out the gauge transformation g(x) of the last step (site layout,
+ * FP64).  LGF_E_STATE before the first step.  Synchronises. */
+lgf_status lgf_get_gauge(lgf_handle h, double* g, int where);
+
+/* Copy out Delta_A(x), the divergence of the traceless anti-Hermitian parts
+ * of the current links (site layout, FP64; the paper's Delta is twice this).
+ * Synchronises. */
+lgf_status lgf_get_divergence(lgf_handle h, double* D, int where);
+
+/* Register host arrays that receive F and theta after every measurement of
+ * the next lgf_fix (entry 0 = the measurement before the first update,
+ * entry k = after update k), up to cap entries.  cap = 0 unregisters.
+ * The arrays must stay valid until lgf_fix returns. */
+lgf_status lgf_set_trace(lgf_handle h, double* F_hist, double* theta_hist, int32_t cap);
+
+/* The library's own 4D DFT of nfields = 4 complex fields in place, in the
+ * handle's precision: data[f][t][z][y][x][re, im] (FP64 on the user side).
+ * sign = -1: f^(k) = sum_x f(x) e^{-2 pi i k.x/L};  sign = +1: the same sum
+ * with e^{+...}, unnormalised.  Exposed so that the transform can be checked
+ * against the defining sum.  Synchronises. */
+lgf_status lgf_fft4(lgf_handle h, double* data, int32_t nfields, int32_t sign, int where);
+
+/* Phase of an LGF_MIXED handle: 32 while in the FP32 phase, 64 after the
+ * switch (FP64 and FP32 handles report their fixed precision). */
+lgf_status lgf_get_phase(lgf_handle h, int32_t* bits);
+
+/* Human-readable name of a status code (static string). */
+const char* lgf_status_string(lgf_status s);
+
+/* Text of the last error on the handle ("" if none; static for NULL). */
+const char* lgf_last_error(lgf_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LGF_H */

@@ -1,0 +1,656 @@
+// C-ABI of the lgf library (include/lgf.h): handle management, the
+// Algorithm 1 controller (arXiv:1206.0675 Sec. 2) with its loop captured in a
+// CUDA graph whose WHILE node is driven by the measurement kernel, and the
+// FP32 -> FP64 precision switch.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/lgf.h"
+#include "lgf_internal.h"
+
+using namespace lgf;
+
+namespace {
+
+constexpr double kSU3Tol = 1e-10;       // input validation threshold
+constexpr double kSwitchTheta = 1e-9;   // FP32 -> FP64 switch level of LGF_MIXED
+
+// One precision "lane" of the handle: the buffers and the captured loop graph
+// of either the FP64 or the FP32 arithmetic.
+template <typename R> struct Lane {
+  C2<R>* U = nullptr;      // links [4][rows][3][V]
+  C2<R>* g = nullptr;      // gauge transform of the last step [grows][3][V]
+  C2<R>* D = nullptr;      // packed divergence / FFT workspace [4][V]
+  R* K = nullptr;          // filter table [V]
+  C2<R>* tw = nullptr;     // twiddles
+  short* pos = nullptr;    // digit-reversal position tables
+  C2<R>* G = nullptr;      // accumulated transform [3][3][V] (optional)
+  int rows = 3, grows = 3;
+  FFTPlan plan{};
+  double alpha = NAN;      // alpha the filter table holds
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  bool active = false;
+};
+
+}  // namespace
+
+struct lgf_ctx {
+  Geom geom{};
+  lgf_precision prec = LGF_FP64;
+  uint32_t flags = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  int device = 0;
+  std::string err;
+  bool broken = false;
+  bool have_links = false;
+  bool have_g = false;
+  int phase = 64;  // arithmetic of the current configuration
+  Lane<double> d;
+  Lane<float> f;
+  double* U0 = nullptr;           // FP64 AoS copy of the input (LGF_MIXED)
+  double* stage = nullptr;        // device AoS staging [4 V 18]
+  double* partials = nullptr;
+  DevState* st = nullptr;
+  DevState* st_host = nullptr;    // pinned
+  unsigned long long* defect = nullptr;
+  unsigned long long* defect_host = nullptr;
+  double* sin2 = nullptr;
+  int lmax = 0;
+  double p2max = 0;
+  double* hist_F = nullptr;
+  double* hist_T = nullptr;
+  int hist_cap = 0;
+  double* user_F = nullptr;
+  double* user_T = nullptr;
+};
+
+namespace {
+
+lgf_status fail(lgf_ctx* h, lgf_status s, const std::string& msg) {
+  if (h) h->err = msg;
+  return s;
+}
+
+lgf_status fail_cuda(lgf_ctx* h, cudaError_t e, const char* what) {
+  if (h) {
+    h->broken = true;
+    h->err = std::string(what) + ": " + cudaGetErrorString(e);
+  }
+  return e == cudaErrorMemoryAllocation ? LGF_E_NOMEM : LGF_E_CUDA;
+}
+
+#define LGF_CK(h, call)                                 \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return fail_cuda(h, e_, #call); \
+  } while (0)
+
+bool extent_ok(int L) {
+  if (L < 2 || L > 128) return false;
+  while (L % 2 == 0) L /= 2;
+  while (L % 3 == 0) L /= 3;
+  return L == 1;
+}
+
+template <typename T> cudaError_t dalloc(T** p, size_t n) { return cudaMalloc((void**)p, n * sizeof(T)); }
+
+template <typename R> void free_lane(Lane<R>& L) {
+  if (L.exec) cudaGraphExecDestroy(L.exec);
+  if (L.graph) cudaGraphDestroy(L.graph);
+  cudaFree(L.U); cudaFree(L.g); cudaFree(L.D); cudaFree(L.K); cudaFree(L.tw); cudaFree(L.pos); cudaFree(L.G);
+  L = Lane<R>();
+}
+
+template <typename R> lgf_status alloc_lane(lgf_ctx* h, Lane<R>& L, int rows, int grows, bool withG) {
+  const int64_t V = h->geom.V;
+  L.rows = rows;
+  L.grows = grows;
+  LGF_CK(h, dalloc(&L.U, (size_t)4 * rows * 3 * V));
+  LGF_CK(h, dalloc(&L.g, (size_t)grows * 3 * V));
+  LGF_CK(h, dalloc(&L.D, (size_t)4 * V));
+  LGF_CK(h, dalloc(&L.K, (size_t)V));
+  const int nt = h->geom.L[0] + h->geom.L[1] + h->geom.L[2] + h->geom.L[3];
+  LGF_CK(h, dalloc(&L.tw, (size_t)nt));
+  if (withG) LGF_CK(h, dalloc(&L.G, (size_t)9 * V));
+  if (configure_fft_plan(h->geom.L, (int)sizeof(R), &L.plan) != cudaSuccess)
+    return fail(h, LGF_E_UNSUPPORTED, "lattice planes do not fit the shared-memory FFT passes");
+  // twiddles W_N^m = exp(-2 pi i m/N), computed in FP64 on the host
+  std::vector<C2<R>> tw(nt);
+  int off = 0;
+  for (int mu = 0; mu < 4; ++mu) {
+    const int N = h->geom.L[mu];
+    for (int m = 0; m < N; ++m) {
+      const double a = -2.0 * M_PI * (double)m / (double)N;
+      tw[off + m] = mkc<R>((R)std::cos(a), (R)std::sin(a));
+    }
+    off += N;
+  }
+  LGF_CK(h, cudaMemcpy(L.tw, tw.data(), nt * sizeof(C2<R>), cudaMemcpyHostToDevice));
+  std::vector<short> pos(nt);
+  fft_positions(L.plan, pos.data());
+  LGF_CK(h, dalloc(&L.pos, (size_t)nt));
+  LGF_CK(h, cudaMemcpy(L.pos, pos.data(), nt * sizeof(short), cudaMemcpyHostToDevice));
+  L.active = true;
+  return LGF_OK;
+}
+
+// Filter table for the requested alpha (recomputed only when alpha changes).
+template <typename R> lgf_status ensure_filter(lgf_ctx* h, Lane<R>& L, double alpha) {
+  if (L.alpha == alpha) return LGF_OK;
+  LGF_CK(h, launch_filter_table<R>(h->geom, h->sin2, h->lmax, alpha, h->p2max, (h->flags & LGF_PLAIN_SD) ? 1 : 0,
+                                    L.K, h->stream));
+  L.alpha = alpha;
+  return LGF_OK;
+}
+
+// Measurement of the current links of a lane.
+template <typename R> cudaError_t enqueue_measure(lgf_ctx* h, Lane<R>& L, int count_iter,
+                                                   unsigned long long cond, int use_cond, cudaStream_t s) {
+  if (L.rows == 3)
+    return launch_measure<R, 3>(h->geom, L.U, L.D, h->partials, h->st, count_iter, cond, use_cond, s);
+  return launch_measure<R, 2>(h->geom, L.U, L.D, h->partials, h->st, count_iter, cond, use_cond, s);
+}
+
+// Gauge-transform step of a lane given the divergence in L.D (from the last
+// measurement), followed by the next measurement: FFT passes A, B, C(+g),
+// update, measure.
+template <typename R> cudaError_t enqueue_body(lgf_ctx* h, Lane<R>& L, unsigned long long cond, int use_cond,
+                                                cudaStream_t s);
+
+template <> cudaError_t enqueue_body<double>(lgf_ctx* h, Lane<double>& L, unsigned long long cond, int use_cond,
+                                             cudaStream_t s) {
+  const Geom& g = h->geom;
+  cudaError_t e;
+  if ((e = launch_fft_xy<double>(g, L.plan, L.D, L.tw, L.pos, -1, 4, s)) != cudaSuccess) return e;
+  if ((e = launch_fft_zt<double>(g, L.plan, L.D, L.tw, L.pos, L.K, 0, 4, s)) != cudaSuccess) return e;
+  if ((e = launch_fft_xy_inv_gauge<double, double, 3>(g, L.plan, L.D, L.tw, L.pos, L.g, L.G, s)) != cudaSuccess) return e;
+  if (L.rows == 3) e = launch_update<double, 3, 3>(g, L.U, L.g, s);
+  else e = launch_update<double, 2, 3>(g, L.U, L.g, s);
+  if (e != cudaSuccess) return e;
+  return enqueue_measure<double>(h, L, 1, cond, use_cond, s);
+}
+
+template <> cudaError_t enqueue_body<float>(lgf_ctx* h, Lane<float>& L, unsigned long long cond, int use_cond,
+                                            cudaStream_t s) {
+  const Geom& g = h->geom;
+  cudaError_t e;
+  if ((e = launch_fft_xy<float>(g, L.plan, L.D, L.tw, L.pos, -1, 4, s)) != cudaSuccess) return e;
+  if ((e = launch_fft_zt<float>(g, L.plan, L.D, L.tw, L.pos, L.K, 0, 4, s)) != cudaSuccess) return e;
+  if (L.grows == 2) {
+    if ((e = launch_fft_xy_inv_gauge<float, float, 2>(g, L.plan, L.D, L.tw, L.pos, L.g, L.G, s)) != cudaSuccess) return e;
+    if ((e = launch_update<float, 2, 2>(g, L.U, L.g, s)) != cudaSuccess) return e;
+  } else {
+    if ((e = launch_fft_xy_inv_gauge<float, float, 3>(g, L.plan, L.D, L.tw, L.pos, L.g, L.G, s)) != cudaSuccess) return e;
+    if ((e = launch_update<float, 3, 3>(g, L.U, L.g, s)) != cudaSuccess) return e;
+  }
+  return enqueue_measure<float>(h, L, 1, cond, use_cond, s);
+}
+
+// Build (once) the graph  WHILE(cond) { body }  for a lane.
+template <typename R> lgf_status ensure_graph(lgf_ctx* h, Lane<R>& L) {
+  if (L.exec) return LGF_OK;
+  cudaGraph_t graph;
+  LGF_CK(h, cudaGraphCreate(&graph, 0));
+  cudaGraphConditionalHandle cond;
+  LGF_CK(h, cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+  np.conditional.handle = cond;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  LGF_CK(h, cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np));
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  LGF_CK(h, cudaStreamBeginCaptureToGraph(h->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  cudaError_t e = enqueue_body<R>(h, L, (unsigned long long)cond, 1, h->cap_stream);
+  cudaGraph_t captured = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &captured);
+  if (e != cudaSuccess) return fail_cuda(h, e, "capture of the iteration body");
+  if (e2 != cudaSuccess) return fail_cuda(h, e2, "cudaStreamEndCapture");
+  LGF_CK(h, cudaGraphInstantiate(&L.exec, graph, 0));
+  L.graph = graph;
+  return LGF_OK;
+}
+
+lgf_status sync_state(lgf_ctx* h) {
+  LGF_CK(h, cudaMemcpyAsync(h->st_host, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+  LGF_CK(h, cudaStreamSynchronize(h->stream));
+  return LGF_OK;
+}
+
+lgf_status check_handle(lgf_ctx* h) {
+  if (!h) return LGF_E_ARG;
+  if (h->broken) return LGF_E_CUDA;
+  cudaError_t e = cudaSetDevice(h->device);
+  if (e != cudaSuccess) return fail_cuda(h, e, "cudaSetDevice");
+  return LGF_OK;
+}
+
+lgf_status measure_current(lgf_ctx* h) {
+  cudaError_t e = (h->phase == 64) ? enqueue_measure<double>(h, h->d, 0, 0, 0, h->stream)
+                                   : enqueue_measure<float>(h, h->f, 0, 0, 0, h->stream);
+  if (e != cudaSuccess) return fail_cuda(h, e, "measure");
+  return LGF_OK;
+}
+
+// FP32 -> FP64 switch: G64 = proj_SU3(G32) in FP64, U64 = G64 U0 G64^dag(x+mu).
+lgf_status switch_to_fp64(lgf_ctx* h) {
+  const Geom& g = h->geom;
+  LGF_CK(h, launch_project_sites_f32_to_f64(g, h->f.G, h->d.g, h->stream));
+  if (h->d.rows == 3) {
+    LGF_CK(h, (launch_links_from_aos<double, 3>(g, h->U0, h->d.U, h->stream)));
+    LGF_CK(h, (launch_update<double, 3, 3>(g, h->d.U, h->d.g, h->stream)));
+  } else {
+    LGF_CK(h, (launch_links_from_aos<double, 2>(g, h->U0, h->d.U, h->stream)));
+    LGF_CK(h, (launch_update<double, 2, 3>(g, h->d.U, h->d.g, h->stream)));
+  }
+  if (h->d.G) LGF_CK(h, cudaMemcpyAsync(h->d.G, h->d.g, sizeof(double2) * 9 * g.V, cudaMemcpyDeviceToDevice,
+                                        h->stream));
+  h->phase = 64;
+  lgf_status s = measure_current(h);
+  return s;
+}
+
+lgf_status copy_out(lgf_ctx* h, const double* dev_src, double* dst, size_t n_doubles, int where) {
+  if (where == LGF_DEVICE) {
+    if (dev_src != dst)
+      LGF_CK(h, cudaMemcpyAsync(dst, dev_src, n_doubles * 8, cudaMemcpyDeviceToDevice, h->stream));
+  } else {
+    LGF_CK(h, cudaMemcpyAsync(dst, dev_src, n_doubles * 8, cudaMemcpyDeviceToHost, h->stream));
+  }
+  LGF_CK(h, cudaStreamSynchronize(h->stream));
+  return LGF_OK;
+}
+
+template <typename R> lgf_status run_loop(lgf_ctx* h, Lane<R>& L, double tol, int max_iter, int reset) {
+  LGF_CK(h, launch_set_state(h->st, tol, max_iter, reset, h->hist_cap, h->hist_F, h->hist_T, h->stream));
+  lgf_status s = sync_state(h);
+  if (s != LGF_OK) return s;
+  const DevState& S = *h->st_host;
+  if (!(std::isfinite(S.F) && std::isfinite(S.theta))) return LGF_OK;
+  if (S.theta < tol || S.iter >= max_iter) return LGF_OK;
+  s = ensure_graph<R>(h, L);
+  if (s != LGF_OK) return s;
+  LGF_CK(h, cudaGraphLaunch(L.exec, h->stream));
+  return sync_state(h);
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+
+extern "C" {
+
+const char* lgf_status_string(lgf_status s) {
+  switch (s) {
+    case LGF_OK: return "ok";
+    case LGF_E_ARG: return "invalid argument";
+    case LGF_E_NOMEM: return "out of memory";
+    case LGF_E_CUDA: return "CUDA error";
+    case LGF_E_STATE: return "invalid state";
+    case LGF_E_NONFINITE: return "non-finite value";
+    case LGF_E_NOTCONV: return "not converged";
+    case LGF_E_TIMEOUT: return "timeout";
+    case LGF_E_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+const char* lgf_last_error(lgf_handle h) {
+  if (!h) return "null handle";
+  return h->err.c_str();
+}
+
+lgf_status lgf_destroy(lgf_handle h) {
+  if (!h) return LGF_OK;
+  cudaSetDevice(h->device);
+  if (h->stream || h->cap_stream) cudaStreamSynchronize(h->stream);
+  free_lane(h->d);
+  free_lane(h->f);
+  cudaFree(h->U0); cudaFree(h->stage); cudaFree(h->partials); cudaFree(h->st); cudaFree(h->defect);
+  cudaFree(h->sin2); cudaFree(h->hist_F); cudaFree(h->hist_T);
+  if (h->st_host) cudaFreeHost(h->st_host);
+  if (h->defect_host) cudaFreeHost(h->defect_host);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  delete h;
+  return LGF_OK;
+}
+
+lgf_status lgf_create(const int32_t extents[4], lgf_precision prec, uint32_t flags, void* cuda_stream,
+                      lgf_handle* out) {
+  if (!extents || !out) return LGF_E_ARG;
+  *out = nullptr;
+  if (prec != LGF_FP64 && prec != LGF_FP32 && prec != LGF_MIXED) return LGF_E_ARG;
+  if (flags & ~(uint32_t)(LGF_STORE12 | LGF_TRACK_G | LGF_PLAIN_SD)) return LGF_E_ARG;
+  for (int mu = 0; mu < 4; ++mu)
+    if (!extent_ok(extents[mu])) return LGF_E_UNSUPPORTED;
+  lgf_ctx* h = new (std::nothrow) lgf_ctx();
+  if (!h) return LGF_E_NOMEM;
+  try {
+    h->prec = prec;
+    h->flags = flags;
+    h->stream = (cudaStream_t)cuda_stream;
+    if (cudaGetDevice(&h->device) != cudaSuccess) { delete h; return LGF_E_CUDA; }
+    Geom& g = h->geom;
+    g.V = 1;
+    for (int mu = 0; mu < 4; ++mu) {
+      g.L[mu] = extents[mu];
+      g.stride[mu] = g.V;
+      g.V *= extents[mu];
+    }
+    lgf_status s = LGF_OK;
+    const bool store12 = (flags & LGF_STORE12) != 0;
+    const bool track = (flags & LGF_TRACK_G) != 0;
+    if (prec == LGF_FP64) {
+      s = alloc_lane<double>(h, h->d, store12 ? 2 : 3, 3, track);
+      h->phase = 64;
+    } else if (prec == LGF_FP32) {
+      s = alloc_lane<float>(h, h->f, store12 ? 2 : 3, store12 ? 2 : 3, track);
+      h->phase = 32;
+    } else {
+      // FP32 phase in the requested storage; the FP64 phase keeps 18 reals
+      // (it is bound by FP64 arithmetic, which 12-real storage increases).
+      s = alloc_lane<float>(h, h->f, store12 ? 2 : 3, store12 ? 2 : 3, true);
+      if (s == LGF_OK) s = alloc_lane<double>(h, h->d, 3, 3, track);
+      if (s == LGF_OK) {
+        cudaError_t e = dalloc(&h->U0, (size_t)4 * 18 * g.V);
+        if (e != cudaSuccess) s = fail_cuda(h, e, "cudaMalloc U0");
+      }
+      h->phase = 32;
+    }
+    if (s == LGF_OK) {
+      cudaError_t e = cudaSuccess;
+      if (e == cudaSuccess) e = dalloc(&h->stage, (size_t)4 * 18 * g.V);
+      if (e == cudaSuccess) e = dalloc(&h->partials, (size_t)2 * measure_blocks(g.V));
+      if (e == cudaSuccess) e = dalloc(&h->st, 1);
+      if (e == cudaSuccess) e = cudaMemset(h->st, 0, sizeof(DevState));
+      if (e == cudaSuccess) e = dalloc(&h->defect, 1);
+      if (e == cudaSuccess) e = cudaMallocHost((void**)&h->st_host, sizeof(DevState));
+      if (e == cudaSuccess) e = cudaMallocHost((void**)&h->defect_host, sizeof(unsigned long long));
+      if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+      h->lmax = 0;
+      for (int mu = 0; mu < 4; ++mu) h->lmax = std::max(h->lmax, g.L[mu]);
+      std::vector<double> sin2((size_t)4 * h->lmax, 0.0);
+      h->p2max = 0;
+      for (int mu = 0; mu < 4; ++mu) {
+        for (int k = 0; k < g.L[mu]; ++k) {
+          const double sv = std::sin(M_PI * (double)k / (double)g.L[mu]);
+          sin2[(size_t)mu * h->lmax + k] = 4.0 * sv * sv;
+        }
+        const double sm = std::sin(M_PI * (double)(g.L[mu] / 2) / (double)g.L[mu]);
+        h->p2max += 4.0 * sm * sm;
+      }
+      if (e == cudaSuccess) e = dalloc(&h->sin2, sin2.size());
+      if (e == cudaSuccess) e = cudaMemcpy(h->sin2, sin2.data(), sin2.size() * 8, cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) s = fail_cuda(h, e, "lgf_create allocation");
+    }
+    if (s != LGF_OK) {
+      lgf_destroy(h);
+      return s;
+    }
+    std::memset(h->st_host, 0, sizeof(DevState));
+    *out = h;
+    return LGF_OK;
+  } catch (...) {
+    lgf_destroy(h);
+    return LGF_E_NOMEM;
+  }
+}
+
+lgf_status lgf_set_links(lgf_handle h, const double* U, int where) {
+  lgf_status s = check_handle(h);
+  if (s != LGF_OK) return s;
+  if (!U || (where != LGF_HOST && where != LGF_DEVICE)) return fail(h, LGF_E_ARG, "bad links pointer or location");
+  try {
+    const Geom& g = h->geom;
+    const size_t n = (size_t)4 * 18 * g.V;
+    const double* src = U;
+    if (where == LGF_HOST) {
+      LGF_CK(h, cudaMemcpyAsync(h->stage, U, n * 8, cudaMemcpyHostToDevice, h->stream));
+      src = h->stage;
+    }
+    LGF_CK(h, launch_su3_defect(src, 4 * g.V, h->defect, h->stream));
+    LGF_CK(h, cudaMemcpyAsync(h->defect_host, h->defect, 8, cudaMemcpyDeviceToHost, h->stream));
+    LGF_CK(h, cudaStreamSynchronize(h->stream));
+    double defect;
+    std::memcpy(&defect, h->defect_host, 8);
+    if (!std::isfinite(defect)) return fail(h, LGF_E_NONFINITE, "input links contain non-finite values");
+    if (defect > kSU3Tol) {
+      char buf[128];
+      std::snprintf(buf, sizeof(buf), "input links are not in SU(3): defect %.3e > %.1e", defect, kSU3Tol);
+      return fail(h, LGF_E_ARG, buf);
+    }
+    if (h->prec == LGF_FP64) {
+      if (h->d.rows == 3) LGF_CK(h, (launch_links_from_aos<double, 3>(g, src, h->d.U, h->stream)));
+      else LGF_CK(h, (launch_links_from_aos<double, 2>(g, src, h->d.U, h->stream)));
+      if (h->d.G) LGF_CK(h, (launch_set_identity<double, 3>(g, h->d.G, h->stream)));
+      h->phase = 64;
+    } else {
+      if (h->f.rows == 3) LGF_CK(h, (launch_links_from_aos<float, 3>(g, src, h->f.U, h->stream)));
+      else LGF_CK(h, (launch_links_from_aos<float, 2>(g, src, h->f.U, h->stream)));
+      if (h->f.G) LGF_CK(h, (launch_set_identity<float, 3>(g, h->f.G, h->stream)));
+      if (h->prec == LGF_MIXED) {
+        LGF_CK(h, cudaMemcpyAsync(h->U0, src, n * 8, cudaMemcpyDeviceToDevice, h->stream));
+        if (h->d.G) LGF_CK(h, (launch_set_identity<double, 3>(g, h->d.G, h->stream)));
+      }
+      h->phase = 32;
+    }
+    LGF_CK(h, launch_set_state(h->st, 0.0, 0, 1, 0, nullptr, nullptr, h->stream));
+    s = measure_current(h);
+    if (s != LGF_OK) return s;
+    s = sync_state(h);
+    if (s != LGF_OK) return s;
+    h->have_links = true;
+    h->have_g = false;
+    return LGF_OK;
+  } catch (...) {
+    return fail(h, LGF_E_NOMEM, "host allocation failed");
+  }
+}
+
+lgf_status lgf_get_links(lgf_handle h, double* U, int where) {
+  lgf_status s = check_handle(h);
+  if (s != LGF_OK) return s;
+  if (!U || (where != LGF_HOST && where != LGF_DEVICE)) return fail(h, LGF_E_ARG, "bad links pointer or location");
+  if (!h->have_links) return fail(h, LGF_E_STATE, "no links set");
+  const Geom& g = h->geom;
+  double* dst = where == LGF_DEVICE ? U : h->stage;
+  if (h->phase == 64) {
+    if (h->d.rows == 3) LGF_CK(h, (launch_links_to_aos<double, 3>(g, h->d.U, dst, h->stream)));
+    else LGF_CK(h, (launch_links_to_aos<double, 2>(g, h->d.U, dst, h->stream)));
+  } else {
+    if (h->f.rows == 3) LGF_CK(h, (launch_links_to_aos<float, 3>(g, h->f.U, dst, h->stream)));
+    else LGF_CK(h, (launch_links_to_aos<float, 2>(g, h->f.U, dst, h->stream)));
+  }
+  return copy_out(h, dst, U, (size_t)4 * 18 * g.V, where);
+}
+
+lgf_status lgf_step(lgf_handle h, double alpha) {
+  lgf_status s = check_handle(h);
+  if (s != LGF_OK) return s;
+  if (!h->have_links) return fail(h, LGF_E_STATE, "no links set");
+  if (!std::isfinite(alpha)) return fail(h, LGF_E_ARG, "alpha must be finite");
+  cudaError_t e;
+  if (h->phase == 64) {
+    if ((s = ensure_filter<double>(h, h->d, alpha)) != LGF_OK) return s;
+    e = enqueue_body<double>(h, h->d, 0, 0, h->stream);
+  } else {
+    if ((s = ensure_filter<float>(h, h->f, alpha)) != LGF_OK) return s;
+    e = enqueue_body<float>(h, h->f, 0, 0, h->stream);
+  }
+  if (e != cudaSuccess) return fail_cuda(h, e, "lgf_step");
+  h->have_g = true;
+  return LGF_OK;
+}
+
+lgf_status lgf_measure(lgf_handle h, double* F, double* theta) {
+  lgf_status s = check_handle(h);
+  if (s != LGF_OK) return s;
+  if (!h->have_links) return fail(h, LGF_E_STATE, "no links set");
+  s = sync_state(h);
+  if (s != LGF_OK) return s;
+  if (F) *F = h->st_host->F;
+  if (theta) *theta = h->st_host->theta;
+  if (!(std::isfinite(h->st_host->F) && std::isfinite(h->st_host->theta)))
+    return fail(h, LGF_E_NONFINITE, "F or theta is not finite");
+  return LGF_OK;
+}
+
+lgf_status lgf_fix(lgf_handle h, double theta_tol, int32_t max_iter, double alpha, int32_t* iters, double* F,
+                   double* theta) {
+  lgf_status s = check_handle(h);
+  if (s != LGF_OK) return s;
+  if (!h->have_links) return fail(h, LGF_E_STATE, "no links set");
+  if (!(theta_tol >= 0.0) || max_iter < 0 || !std::isfinite(alpha)) return fail(h, LGF_E_ARG, "bad fix arguments");
+  if (h->phase == 32) {
+    if ((s = ensure_filter<float>(h, h->f, alpha)) != LGF_OK) return s;
+    const double tol1 = h->prec == LGF_MIXED ? std::max(theta_tol, kSwitchTheta) : theta_tol;
+    if ((s = run_loop<float>(h, h->f, tol1, max_iter, 1)) != LGF_OK) return s;
+    h->have_g = h->have_g || h->st_host->iter > 0;
+    const DevState& S = *h->st_host;
+    if (h->prec == LGF_MIXED && std::isfinite(S.theta) && S.theta < tol1 && theta_tol < tol1 &&
+        S.iter < max_iter) {
+      if ((s = switch_to_fp64(h)) != LGF_OK) return s;
+    }
+  } else {
+    LGF_CK(h, launch_set_state(h->st, theta_tol, max_iter, 1, h->hist_cap, h->hist_F, h->hist_T, h->stream));
+  }
+  if (h->phase == 64) {
+    if ((s = ensure_filter<double>(h, h->d, alpha)) != LGF_OK) return s;
+    if ((s = run_loop<double>(h, h->d, theta_tol, max_iter, 0)) != LGF_OK) return s;
+    h->have_g = h->have_g || h->st_host->iter > 0;
+  }
+  const DevState& S = *h->st_host;
+  if (iters) *iters = S.iter;
+  if (F) *F = S.F;
+  if (theta) *theta = S.theta;
+  if (h->hist_cap > 0 && h->user_F && h->user_T) {
+    const int n = std::min(h->hist_cap, S.iter + 1);
+    LGF_CK(h, cudaMemcpyAsync(h->user_F, h->hist_F, (size_t)n * 8, cudaMemcpyDeviceToHost, h->stream));
+    LGF_CK(h, cudaMemcpyAsync(h->user_T, h->hist_T, (size_t)n * 8, cudaMemcpyDeviceToHost, h->stream));
+    LGF_CK(h, cudaStreamSynchronize(h->stream));
+  }
+  if (!(std::isfinite(S.F) && std::isfinite(S.theta)) || S.status == ST_NONFINITE)
+    return fail(h, LGF_E_NONFINITE, "F or theta became non-finite");
+  if (S.theta >= theta_tol) return fail(h, LGF_E_NOTCONV, "max_iter reached before theta < tol");
+  return LGF_OK;
+}
+
+lgf_status lgf_get_transform(lgf_handle h, double* G, int where) {
+  lgf_status s = check_handle(h);
+  if (s != LGF_OK) return s;
+  if (!G || (where != LGF_HOST && where != LGF_DEVICE)) return fail(h, LGF_E_ARG, "bad pointer or location");
+  if (!h->have_links) return fail(h, LGF_E_STATE, "no links set");
+  const Geom& g = h->geom;
+  double* dst = where == LGF_DEVICE ? G : h->stage;
+  if (h->phase == 64 && h->d.G) {
+    LGF_CK(h, (launch_sites_to_aos<double, 3>(g, h->d.G, dst, h->stream)));
+  } else if (h->phase == 32 && h->f.G && (h->flags & LGF_TRACK_G)) {
+    LGF_CK(h, (launch_sites_to_aos<float, 3>(g, h->f.G, dst, h->stream)));
+  } else {
+    return fail(h, LGF_E_STATE, "the handle does not track G (create it with LGF_TRACK_G)");
+  }
+  return copy_out(h, dst, G, (size_t)18 * g.V, where);
+}
+
+lgf_status lgf_get_gauge(lgf_handle h, double* gout, int where) {
+  lgf_status s = check_handle(h);
+  if (s != LGF_OK) return s;
+  if (!gout || (where != LGF_HOST && where != LGF_DEVICE)) return fail(h, LGF_E_ARG, "bad pointer or location");
+  if (!h->have_g) return fail(h, LGF_E_STATE, "no step has been taken");
+  const Geom& g = h->geom;
+  double* dst = where == LGF_DEVICE ? gout : h->stage;
+  if (h->phase == 64) {
+    LGF_CK(h, (launch_sites_to_aos<double, 3>(g, h->d.g, dst, h->stream)));
+  } else if (h->f.grows == 2) {
+    LGF_CK(h, (launch_sites_to_aos<float, 2>(g, h->f.g, dst, h->stream)));
+  } else {
+    LGF_CK(h, (launch_sites_to_aos<float, 3>(g, h->f.g, dst, h->stream)));
+  }
+  return copy_out(h, dst, gout, (size_t)18 * g.V, where);
+}
+
+lgf_status lgf_get_divergence(lgf_handle h, double* D, int where) {
+  lgf_status s = check_handle(h);
+  if (s != LGF_OK) return s;
+  if (!D || (where != LGF_HOST && where != LGF_DEVICE)) return fail(h, LGF_E_ARG, "bad pointer or location");
+  if (!h->have_links) return fail(h, LGF_E_STATE, "no links set");
+  const Geom& g = h->geom;
+  double* dst = where == LGF_DEVICE ? D : h->stage;
+  if (h->phase == 64) LGF_CK(h, launch_delta_to_aos<double>(g, h->d.D, dst, h->stream));
+  else LGF_CK(h, launch_delta_to_aos<float>(g, h->f.D, dst, h->stream));
+  return copy_out(h, dst, D, (size_t)18 * g.V, where);
+}
+
+lgf_status lgf_set_trace(lgf_handle h, double* F_hist, double* theta_hist, int32_t cap) {
+  lgf_status s = check_handle(h);
+  if (s != LGF_OK) return s;
+  if (cap < 0 || (cap > 0 && (!F_hist || !theta_hist))) return fail(h, LGF_E_ARG, "bad trace arguments");
+  LGF_CK(h, cudaStreamSynchronize(h->stream));
+  cudaFree(h->hist_F);
+  cudaFree(h->hist_T);
+  h->hist_F = h->hist_T = nullptr;
+  h->hist_cap = 0;
+  h->user_F = h->user_T = nullptr;
+  if (cap > 0) {
+    LGF_CK(h, dalloc(&h->hist_F, (size_t)cap));
+    LGF_CK(h, dalloc(&h->hist_T, (size_t)cap));
+    h->hist_cap = cap;
+    h->user_F = F_hist;
+    h->user_T = theta_hist;
+  }
+  // the device state must never point at freed history buffers
+  LGF_CK(h, launch_set_state(h->st, 0.0, 0, 0, h->hist_cap, h->hist_F, h->hist_T, h->stream));
+  LGF_CK(h, cudaStreamSynchronize(h->stream));
+  return LGF_OK;
+}
+
+lgf_status lgf_fft4(lgf_handle h, double* data, int32_t nfields, int32_t sign, int where) {
+  lgf_status s = check_handle(h);
+  if (s != LGF_OK) return s;
+  if (!data || nfields != 4 || (sign != -1 && sign != 1) || (where != LGF_HOST && where != LGF_DEVICE))
+    return fail(h, LGF_E_ARG, "bad fft4 arguments");
+  const Geom& g = h->geom;
+  const size_t n = (size_t)4 * 2 * g.V;
+  double* buf = h->stage;
+  if (where == LGF_HOST) LGF_CK(h, cudaMemcpyAsync(buf, data, n * 8, cudaMemcpyHostToDevice, h->stream));
+  else LGF_CK(h, cudaMemcpyAsync(buf, data, n * 8, cudaMemcpyDeviceToDevice, h->stream));
+  if (h->phase == 64) {
+    Lane<double>& L = h->d;
+    LGF_CK(h, cudaMemcpyAsync(L.D, buf, n * 8, cudaMemcpyDeviceToDevice, h->stream));
+    LGF_CK(h, launch_fft_xy<double>(g, L.plan, L.D, L.tw, L.pos, sign, 4, h->stream));
+    LGF_CK(h, launch_fft_zt<double>(g, L.plan, L.D, L.tw, L.pos, L.K, sign, 4, h->stream));
+    LGF_CK(h, cudaMemcpyAsync(buf, L.D, n * 8, cudaMemcpyDeviceToDevice, h->stream));
+  } else {
+    Lane<float>& L = h->f;
+    LGF_CK(h, launch_c2_f64_to_f32(reinterpret_cast<const double2*>(buf), L.D, 4 * g.V, h->stream));
+    LGF_CK(h, launch_fft_xy<float>(g, L.plan, L.D, L.tw, L.pos, sign, 4, h->stream));
+    LGF_CK(h, launch_fft_zt<float>(g, L.plan, L.D, L.tw, L.pos, L.K, sign, 4, h->stream));
+    LGF_CK(h, launch_c2_f32_to_f64(L.D, reinterpret_cast<double2*>(buf), 4 * g.V, h->stream));
+  }
+  s = copy_out(h, buf, data, n, where);
+  if (s != LGF_OK) return s;
+  // the transform used the divergence buffer: restore it from the links
+  if (h->have_links) {
+    s = measure_current(h);
+    if (s != LGF_OK) return s;
+    s = sync_state(h);
+  }
+  return s;
+}
+
+lgf_status lgf_get_phase(lgf_handle h, int32_t* bits) {
+  if (!h || !bits) return LGF_E_ARG;
+  *bits = h->phase;
+  return LGF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,133 @@
+// Shared device helpers of the lgf CUDA library: complex arithmetic, SU(3)
+// row algebra and structure-of-arrays link access.
+//
+// Storage (all fields are structure-of-arrays over lattice sites, site index
+// s = x + Lx*(y + Ly*(z + Lz*t))):
+//   links  : [mu][row][col][s] complex (double2 or float2); ROWS = 3 keeps the
+//            full matrix ("18-real"), ROWS = 2 keeps rows 1-2 ("12-real") and
+//            rebuilds row 3 as (a x b)^* (Sec. 3.2 of arXiv:1206.0675).
+//   g, G   : [row][col][s] complex, same convention without mu.
+//   Delta  : 4 complex fields [f][s]: f0 = Im D11 + i Im D22, f1 = D12,
+//            f2 = D13, f3 = D23 of the traceless anti-Hermitian divergence.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lgf {
+
+template <typename R> struct cplx_of;
+template <> struct cplx_of<double> { using type = double2; };
+template <> struct cplx_of<float> { using type = float2; };
+template <typename R> using C2 = typename cplx_of<R>::type;
+
+template <typename R> __host__ __device__ __forceinline__ C2<R> mkc(R re, R im) {
+  C2<R> z; z.x = re; z.y = im; return z;
+}
+template <typename R> __device__ __forceinline__ C2<R> cadd(C2<R> a, C2<R> b) { return mkc<R>(a.x + b.x, a.y + b.y); }
+template <typename R> __device__ __forceinline__ C2<R> csub(C2<R> a, C2<R> b) { return mkc<R>(a.x - b.x, a.y - b.y); }
+template <typename R> __device__ __forceinline__ C2<R> cconj(C2<R> a) { return mkc<R>(a.x, -a.y); }
+// a * b
+template <typename R> __device__ __forceinline__ C2<R> cmul(C2<R> a, C2<R> b) {
+  return mkc<R>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+template <typename R> __device__ __forceinline__ C2<R> cmulc(C2<R> a, C2<R> b) {
+  return mkc<R>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+// conj(a) * b
+template <typename R> __device__ __forceinline__ C2<R> cconjmul(C2<R> a, C2<R> b) {
+  return mkc<R>(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+// acc + a * b
+template <typename R> __device__ __forceinline__ C2<R> cfma(C2<R> a, C2<R> b, C2<R> acc) {
+  return mkc<R>(fma(a.x, b.x, fma(-a.y, b.y, acc.x)), fma(a.x, b.y, fma(a.y, b.x, acc.y)));
+}
+// acc + a * conj(b)
+template <typename R> __device__ __forceinline__ C2<R> cfmac(C2<R> a, C2<R> b, C2<R> acc) {
+  return mkc<R>(fma(a.x, b.x, fma(a.y, b.y, acc.x)), fma(a.y, b.x, fma(-a.x, b.y, acc.y)));
+}
+template <typename R> __device__ __forceinline__ C2<R> cscale(C2<R> a, R s) { return mkc<R>(a.x * s, a.y * s); }
+template <typename R> __device__ __forceinline__ R cnorm2(C2<R> a) { return fma(a.x, a.x, a.y * a.y); }
+
+template <typename To, typename From> __device__ __forceinline__ C2<To> ccast(C2<From> a) {
+  return mkc<To>((To)a.x, (To)a.y);
+}
+
+// 3x3 complex matrix held in registers.
+template <typename R> struct M3 {
+  C2<R> e[3][3];
+};
+
+// Third row of an SU(3) matrix from its first two: c = (a x b)^*.
+template <typename R> __device__ __forceinline__ void su3_third_row(const C2<R> a[3], const C2<R> b[3], C2<R> c[3]) {
+  // c_j = conj(a_k b_l - a_l b_k) for (j, k, l) cyclic
+  C2<R> t0 = csub<R>(cmul<R>(a[1], b[2]), cmul<R>(a[2], b[1]));
+  C2<R> t1 = csub<R>(cmul<R>(a[2], b[0]), cmul<R>(a[0], b[2]));
+  C2<R> t2 = csub<R>(cmul<R>(a[0], b[1]), cmul<R>(a[1], b[0]));
+  c[0] = cconj<R>(t0);
+  c[1] = cconj<R>(t1);
+  c[2] = cconj<R>(t2);
+}
+
+// Structure-of-arrays matrix field: element (m, r, c) of site s lives at
+// p[((m * ROWS + r) * 3 + c) * V + s]; m is the direction for links, 0 otherwise.
+template <typename R, int ROWS> struct MatField {
+  C2<R>* p;
+  int64_t V;
+  __device__ __forceinline__ int64_t off(int m, int r, int c, int64_t s) const {
+    return ((int64_t)((m * ROWS + r) * 3 + c)) * V + s;
+  }
+  __device__ __forceinline__ void load(int m, int64_t s, M3<R>& M) const {
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) M.e[r][c] = p[off(m, r, c, s)];
+    if (ROWS == 2) su3_third_row<R>(M.e[0], M.e[1], M.e[2]);
+  }
+  __device__ __forceinline__ void load_ro(int m, int64_t s, M3<R>& M) const {
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) M.e[r][c] = __ldg(&p[off(m, r, c, s)]);
+    if (ROWS == 2) su3_third_row<R>(M.e[0], M.e[1], M.e[2]);
+  }
+  // rows 0..1 only (never reconstructs)
+  __device__ __forceinline__ void load_rows01_ro(int m, int64_t s, C2<R> rows[2][3]) const {
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) rows[r][c] = __ldg(&p[off(m, r, c, s)]);
+  }
+  __device__ __forceinline__ void store(int m, int64_t s, const M3<R>& M) const {
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) p[off(m, r, c, s)] = M.e[r][c];
+  }
+};
+
+// Lattice geometry passed by value to every kernel.
+struct Geom {
+  int L[4];        // Lx, Ly, Lz, Lt
+  int64_t V;       // volume
+  int64_t stride[4];  // 1, Lx, Lx*Ly, Lx*Ly*Lz
+};
+
+__device__ __forceinline__ void site_coords(const Geom& g, int64_t s, int c[4]) {
+  int64_t r = s;
+  c[0] = (int)(r % g.L[0]); r /= g.L[0];
+  c[1] = (int)(r % g.L[1]); r /= g.L[1];
+  c[2] = (int)(r % g.L[2]); r /= g.L[2];
+  c[3] = (int)r;
+}
+
+__device__ __forceinline__ int64_t site_back(const Geom& g, int64_t s, const int c[4], int mu) {
+  return c[mu] == 0 ? s + (int64_t)(g.L[mu] - 1) * g.stride[mu] : s - g.stride[mu];
+}
+
+__device__ __forceinline__ int64_t site_fwd(const Geom& g, int64_t s, const int c[4], int mu) {
+  return c[mu] == g.L[mu] - 1 ? s - (int64_t)(g.L[mu] - 1) * g.stride[mu] : s + g.stride[mu];
+}
+
+}  // namespace lgf

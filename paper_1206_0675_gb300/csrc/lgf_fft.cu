@@ -1,0 +1,543 @@
+// 4D Fourier transform of the packed divergence as two plane passes
+// (the "2D + 2D" decomposition of arXiv:1206.0675 Sec. 3.2), written for
+// shared memory instead of cuFFT plus a reorder kernel:
+//
+//   pass A : forward DFT over each (x, y) plane                     [k3 removed]
+//   pass B : forward DFT over (z, t), multiply by the momentum filter,
+//            inverse DFT over (z, t)                                [k4 fused]
+//   pass C : inverse DFT over (x, y), then g(x) = reunitarize(1 + Delta'(x))
+//            in FP64, optionally G <- g G                           [k5 fused]
+//
+// Each 1D transform is an in-place mixed-radix (2, 3, 4, 8) Cooley-Tukey FFT
+// in shared memory (see ct_stage).  Consecutive threads work on neighbouring
+// lines and every line stride is padded by one element, so the butterflies'
+// shared-memory accesses are free of bank conflicts in every direction.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "lgf_internal.h"
+
+namespace lgf {
+
+// ---------------------------------------------------------------------------
+// radix-R DFTs in registers; SIGN = -1 forward (e^{-2 pi i nk/R}), +1 inverse
+// ---------------------------------------------------------------------------
+
+template <typename R, int SIGN> __device__ __forceinline__ C2<R> mul_i(C2<R> a) {
+  // multiply by SIGN * i
+  return SIGN < 0 ? mkc<R>(a.y, -a.x) : mkc<R>(-a.y, a.x);
+}
+
+template <typename R, int RAD, int SIGN> struct DFT;
+
+template <typename R, int SIGN> struct DFT<R, 2, SIGN> {
+  __device__ __forceinline__ static void run(C2<R>* v) {
+    const C2<R> a = v[0], b = v[1];
+    v[0] = cadd<R>(a, b);
+    v[1] = csub<R>(a, b);
+  }
+};
+
+template <typename R, int SIGN> struct DFT<R, 3, SIGN> {
+  __device__ __forceinline__ static void run(C2<R>* v) {
+    const R h = (R)0.5, s3 = (R)0.86602540378443864676372317075294;  // cos(pi/3), sin(pi/3)
+    const C2<R> t1 = cadd<R>(v[1], v[2]);
+    const C2<R> t2 = mkc<R>(fma(-h, t1.x, v[0].x), fma(-h, t1.y, v[0].y));
+    const C2<R> d = csub<R>(v[1], v[2]);
+    const C2<R> t3 = mul_i<R, SIGN>(mkc<R>(s3 * d.x, s3 * d.y));
+    v[0] = cadd<R>(v[0], t1);
+    v[1] = cadd<R>(t2, t3);
+    v[2] = csub<R>(t2, t3);
+  }
+};
+
+template <typename R, int SIGN> struct DFT<R, 4, SIGN> {
+  __device__ __forceinline__ static void run(C2<R>* v) {
+    const C2<R> a = cadd<R>(v[0], v[2]), b = csub<R>(v[0], v[2]);
+    const C2<R> c = cadd<R>(v[1], v[3]), d = mul_i<R, SIGN>(csub<R>(v[1], v[3]));
+    v[0] = cadd<R>(a, c);
+    v[2] = csub<R>(a, c);
+    v[1] = cadd<R>(b, d);
+    v[3] = csub<R>(b, d);
+  }
+};
+
+template <typename R, int SIGN> struct DFT<R, 8, SIGN> {
+  __device__ __forceinline__ static void run(C2<R>* v) {
+    C2<R> e[4] = {v[0], v[2], v[4], v[6]};
+    C2<R> o[4] = {v[1], v[3], v[5], v[7]};
+    DFT<R, 4, SIGN>::run(e);
+    DFT<R, 4, SIGN>::run(o);
+    const R r2 = (R)0.70710678118654752440084436210485;
+    // o[k] *= W8^k, W8 = e^{SIGN 2 pi i / 8}
+    {
+      const C2<R> a = o[1];  // (1 + SIGN i)/sqrt2
+      o[1] = SIGN < 0 ? mkc<R>(r2 * (a.x + a.y), r2 * (a.y - a.x)) : mkc<R>(r2 * (a.x - a.y), r2 * (a.y + a.x));
+    }
+    o[2] = mul_i<R, SIGN>(o[2]);
+    {
+      const C2<R> a = o[3];  // (-1 + SIGN i)/sqrt2
+      o[3] = SIGN < 0 ? mkc<R>(r2 * (a.y - a.x), -r2 * (a.x + a.y)) : mkc<R>(-r2 * (a.x + a.y), r2 * (a.x - a.y));
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      v[k] = cadd<R>(e[k], o[k]);
+      v[k + 4] = csub<R>(e[k], o[k]);
+    }
+  }
+};
+
+// ---------------------------------------------------------------------------
+// in-place mixed-radix Cooley-Tukey stages over a set of lines of a tile
+// ---------------------------------------------------------------------------
+//
+// With radices R_0..R_{m-1} (stage s spans Ns = R_0...R_{s-1}), a butterfly
+// of stage s acts on the R_s elements  g*Ns*R_s + j + r*Ns  (r < R_s) of a
+// line.  Decimation in time (DIT) multiplies input r by W_{Ns R_s}^{j r}
+// before the R_s-point DFT and expects its input in mixed-radix digit-reversed
+// order; decimation in frequency (DIF) runs the stages in reverse, applies
+// the DFT first and the twiddles to the outputs, and leaves its output in
+// digit-reversed order.  The reorder is folded into the global <-> shared
+// copies through the position table pos[n] of each direction, so no
+// separate reorder kernel (k3 of Sec. 3.2) exists.  A butterfly reads and
+// writes only its own elements, so each thread works through its butterflies
+// one at a time and stages are separated by a single __syncthreads.
+
+// Line l starts at (l / inner) * outer_stride + (l % inner) * inner_stride and
+// its elements are es apart.
+struct Lines {
+  int nlines, inner, inner_stride, outer_stride, es;
+};
+
+template <typename R, int RAD, int SIGN, bool DIT>
+__device__ __forceinline__ void ct_stage(C2<R>* __restrict__ tile, const Lines ln, const int N, const int Ns,
+                                         const C2<R>* __restrict__ tw) {
+  const int nbl = N / RAD;
+  const int NB = ln.nlines * nbl;
+  const int tws = N / (Ns * RAD);
+  for (int b = threadIdx.x; b < NB; b += blockDim.x) {
+    const int l = b % ln.nlines, q = b / ln.nlines;
+    const int j = q % Ns, grp = q / Ns;
+    const int base = (l / ln.inner) * ln.outer_stride + (l % ln.inner) * ln.inner_stride +
+                     (grp * Ns * RAD + j) * ln.es;
+    const int step = Ns * ln.es;
+    C2<R> v[RAD];
+#pragma unroll
+    for (int r = 0; r < RAD; ++r) v[r] = tile[base + r * step];
+    if (DIT && j > 0) {
+#pragma unroll
+      for (int r = 1; r < RAD; ++r) {
+        const C2<R> w = tw[j * r * tws];
+        v[r] = SIGN < 0 ? cmul<R>(v[r], w) : cmulc<R>(v[r], w);
+      }
+    }
+    DFT<R, RAD, SIGN>::run(v);
+    if (!DIT && j > 0) {
+#pragma unroll
+      for (int r = 1; r < RAD; ++r) {
+        const C2<R> w = tw[j * r * tws];
+        v[r] = SIGN < 0 ? cmul<R>(v[r], w) : cmulc<R>(v[r], w);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < RAD; ++r) tile[base + r * step] = v[r];
+  }
+  __syncthreads();
+}
+
+template <typename R, int SIGN, bool DIT>
+__device__ __forceinline__ void ct_stage_any(C2<R>* tile, const Lines ln, int N, int Ns, int rad, const C2<R>* tw) {
+  if (rad == 8) ct_stage<R, 8, SIGN, DIT>(tile, ln, N, Ns, tw);
+  else if (rad == 4) ct_stage<R, 4, SIGN, DIT>(tile, ln, N, Ns, tw);
+  else if (rad == 3) ct_stage<R, 3, SIGN, DIT>(tile, ln, N, Ns, tw);
+  else ct_stage<R, 2, SIGN, DIT>(tile, ln, N, Ns, tw);
+}
+
+// DFT of every line: input digit-reversed, output natural.
+template <typename R, int SIGN>
+__device__ __forceinline__ void fft_lines_dit(C2<R>* tile, const Lines ln, const FFTDir& d, const C2<R>* tw) {
+  int Ns = 1;
+  for (int st = 0; st < d.nst; ++st) {
+    ct_stage_any<R, SIGN, true>(tile, ln, d.N, Ns, d.radix[st], tw);
+    Ns *= d.radix[st];
+  }
+}
+
+// DFT of every line: input natural, output digit-reversed.
+template <typename R, int SIGN>
+__device__ __forceinline__ void fft_lines_dif(C2<R>* tile, const Lines ln, const FFTDir& d, const C2<R>* tw) {
+  int Ns = d.N;
+  for (int st = d.nst - 1; st >= 0; --st) {
+    Ns /= d.radix[st];
+    ct_stage_any<R, SIGN, false>(tile, ln, d.N, Ns, d.radix[st], tw);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// shared-memory layout helpers
+// ---------------------------------------------------------------------------
+
+// Shared memory of a pass: twiddles of two directions, position tables of two
+// directions, then the tile.  Returns the tile pointer.
+template <typename R>
+__device__ __forceinline__ C2<R>* setup_smem(unsigned char* raw, const C2<R>* __restrict__ twg,
+                                             const short* __restrict__ posg, int n0, int n1, C2<R>** tw,
+                                             short** pos) {
+  *tw = reinterpret_cast<C2<R>*>(raw);
+  const int twn = (n0 + n1 + 1) & ~1;
+  *pos = reinterpret_cast<short*>(*tw + twn);
+  const int posn = (n0 + n1 + 7) & ~7;  // keeps the tile 16-byte aligned
+  for (int i = threadIdx.x; i < n0 + n1; i += blockDim.x) {
+    (*tw)[i] = __ldg(&twg[i]);
+    (*pos)[i] = __ldg(&posg[i]);
+  }
+  return reinterpret_cast<C2<R>*>(*pos + posn);
+}
+
+template <typename R> __host__ __device__ inline size_t smem_header_bytes(int n0, int n1) {
+  return (size_t)((n0 + n1 + 1) & ~1) * sizeof(C2<R>) + (size_t)((n0 + n1 + 7) & ~7) * sizeof(short);
+}
+
+// ---------------------------------------------------------------------------
+// (x, y) plane pass: one CTA per (z, t) slab and group of fpb fields;
+// digit-reversed load, DIT in x and y, natural store (passes A and, for large
+// planes, C).
+// ---------------------------------------------------------------------------
+
+template <typename R, int SIGN>
+__global__ void __launch_bounds__(512) fft_xy_kernel(Geom g, FFTDir dx, FFTDir dy, C2<R>* __restrict__ data, const C2<R>* __restrict__ twg,
+                              const short* __restrict__ posg, int fpb) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int Lx = g.L[0], Ly = g.L[1];
+  C2<R>* tw;
+  short* pos;
+  C2<R>* tile = setup_smem<R>(smem_raw, twg, posg, Lx, Ly, &tw, &pos);
+  const int RS = Lx + 1, PS = Ly * RS;
+  const int64_t slab = blockIdx.x;
+  const int f0 = blockIdx.y * fpb;
+  const int plane = Lx * Ly;
+  __syncthreads();
+  for (int i = threadIdx.x; i < fpb * plane; i += blockDim.x) {
+    const int f = i / plane, r = i - f * plane, y = r / Lx, x = r - y * Lx;
+    tile[f * PS + pos[Lx + y] * RS + pos[x]] = data[(int64_t)(f0 + f) * g.V + slab * plane + r];
+  }
+  __syncthreads();
+  fft_lines_dit<R, SIGN>(tile, Lines{fpb * Ly, fpb * Ly, RS, 0, 1}, dx, tw);
+  fft_lines_dit<R, SIGN>(tile, Lines{fpb * Lx, Lx, 1, PS, RS}, dy, tw + Lx);
+  for (int i = threadIdx.x; i < fpb * plane; i += blockDim.x) {
+    const int f = i / plane, r = i - f * plane, y = r / Lx, x = r - y * Lx;
+    data[(int64_t)(f0 + f) * g.V + slab * plane + r] = tile[f * PS + y * RS + x];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// (z, t) plane pass with the momentum filter: one CTA per (x-block, y, field)
+// ---------------------------------------------------------------------------
+
+template <typename R>
+__global__ void __launch_bounds__(512) fft_zt_filter_kernel(Geom g, FFTDir dz, FFTDir dt, C2<R>* __restrict__ data,
+                                     const C2<R>* __restrict__ twg, const short* __restrict__ posg,
+                                     const R* __restrict__ K, int xc, int mode) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int Lx = g.L[0], Ly = g.L[1], Lz = g.L[2], Lt = g.L[3];
+  C2<R>* tw;
+  short* pos;
+  C2<R>* tile = setup_smem<R>(smem_raw, twg + Lx + Ly, posg + Lx + Ly, Lz, Lt, &tw, &pos);
+  const int TS = Lz * xc + 1;
+  const int nxb = Lx / xc;
+  const int x0 = (blockIdx.x % nxb) * xc, y = blockIdx.x / nxb;
+  C2<R>* fld = data + (int64_t)blockIdx.y * g.V;
+  const int n = Lz * Lt * xc;
+  const int64_t sxy = (int64_t)y * Lx + x0;
+  const int64_t plane = (int64_t)Lx * Ly;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int xi = i % xc, zt = i / xc, z = zt % Lz, t = zt / Lz;
+    tile[pos[Lz + t] * TS + pos[z] * xc + xi] = fld[(int64_t)zt * plane + sxy + xi];
+  }
+  __syncthreads();
+  const Lines lz{Lt * xc, xc, 1, TS, xc};
+  const Lines lt{Lz * xc, Lz * xc, 1, 0, TS};
+  if (mode == 0) {
+    fft_lines_dit<R, -1>(tile, lz, dz, tw);
+    fft_lines_dit<R, -1>(tile, lt, dt, tw + Lz);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const int xi = i % xc, zt = i / xc, z = zt % Lz, t = zt / Lz;
+      const R k = __ldg(&K[(int64_t)zt * plane + sxy + xi]);
+      C2<R>& e = tile[t * TS + z * xc + xi];
+      e = mkc<R>(e.x * k, e.y * k);
+    }
+    __syncthreads();
+    fft_lines_dif<R, +1>(tile, lt, dt, tw + Lz);
+    fft_lines_dif<R, +1>(tile, lz, dz, tw);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const int xi = i % xc, zt = i / xc, z = zt % Lz, t = zt / Lz;
+      fld[(int64_t)zt * plane + sxy + xi] = tile[pos[Lz + t] * TS + pos[z] * xc + xi];
+    }
+  } else {
+    if (mode < 0) {
+      fft_lines_dit<R, -1>(tile, lz, dz, tw);
+      fft_lines_dit<R, -1>(tile, lt, dt, tw + Lz);
+    } else {
+      fft_lines_dit<R, +1>(tile, lz, dz, tw);
+      fft_lines_dit<R, +1>(tile, lt, dt, tw + Lz);
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const int xi = i % xc, zt = i / xc, z = zt % Lz, t = zt / Lz;
+      fld[(int64_t)zt * plane + sxy + xi] = tile[t * TS + z * xc + xi];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// g(x) = reunitarize(1 + Delta'(x)) in FP64 (Sec. 2 first-order expansion,
+// Gram-Schmidt on rows 1-2, row 3 = (a x b)^* as in Sec. 3.2)
+// ---------------------------------------------------------------------------
+
+// f0 = (Im D11, Im D22), f1 = D12, f2 = D13, f3 = D23 of the filtered field.
+__device__ __forceinline__ void gauge_from_packed(double2 f0, double2 f1, double2 f2, double2 f3, double2 u[3],
+                                                  double2 v[3]) {
+  // row 1 of 1 + X: (1 + i a, b, c)
+  const double a = f0.x, d = f0.y;
+  const double n1 = fma(f2.x, f2.x, fma(f2.y, f2.y, fma(f1.x, f1.x, fma(f1.y, f1.y, fma(a, a, 1.0)))));
+  const double i1 = rsqrt(n1);
+  u[0] = make_double2(i1, a * i1);
+  u[1] = make_double2(f1.x * i1, f1.y * i1);
+  u[2] = make_double2(f2.x * i1, f2.y * i1);
+  // row 2 of 1 + X: (-conj(b), 1 + i d, e)
+  const double2 r0 = make_double2(-f1.x, f1.y), r1 = make_double2(1.0, d), r2 = f3;
+  double2 ip = cconjmul<double>(u[0], r0);
+  ip = cadd<double>(ip, cconjmul<double>(u[1], r1));
+  ip = cadd<double>(ip, cconjmul<double>(u[2], r2));
+  const double2 nip = make_double2(-ip.x, -ip.y);
+  v[0] = cfma<double>(nip, u[0], r0);
+  v[1] = cfma<double>(nip, u[1], r1);
+  v[2] = cfma<double>(nip, u[2], r2);
+  const double n2 = cnorm2<double>(v[0]) + cnorm2<double>(v[1]) + cnorm2<double>(v[2]);
+  const double i2 = rsqrt(n2);
+  v[0] = cscale<double>(v[0], i2);
+  v[1] = cscale<double>(v[1], i2);
+  v[2] = cscale<double>(v[2], i2);
+}
+
+template <typename RG, int GROWS>
+__device__ __forceinline__ void store_gauge(int64_t V, int64_t s, const double2 u[3], const double2 v[3],
+                                            C2<RG>* __restrict__ gf, C2<RG>* __restrict__ Gf) {
+  double2 w[3];
+  const bool need_w = (GROWS == 3) || (Gf != nullptr);
+  if (need_w) su3_third_row<double>(u, v, w);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    gf[(0 * 3 + c) * V + s] = ccast<RG, double>(u[c]);
+    gf[(1 * 3 + c) * V + s] = ccast<RG, double>(v[c]);
+    if (GROWS == 3) gf[(2 * 3 + c) * V + s] = ccast<RG, double>(w[c]);
+  }
+  if (Gf != nullptr) {
+    // G <- g G (full 3x3, precision RG)
+    C2<RG> Go[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) Go[r][c] = Gf[(r * 3 + c) * V + s];
+    const double2* rows[3] = {u, v, w};
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      C2<RG> gr[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) gr[k] = ccast<RG, double>(rows[r][k]);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        C2<RG> acc = cmul<RG>(gr[0], Go[0][c]);
+        acc = cfma<RG>(gr[1], Go[1][c], acc);
+        acc = cfma<RG>(gr[2], Go[2][c], acc);
+        Gf[(r * 3 + c) * V + s] = acc;
+      }
+    }
+  }
+}
+
+template <typename R, typename RG, int GROWS>
+__global__ void __launch_bounds__(512) fft_xy_inv_gauge_kernel(Geom g, FFTDir dx, FFTDir dy, const C2<R>* __restrict__ data,
+                                        const C2<R>* __restrict__ twg, const short* __restrict__ posg,
+                                        C2<RG>* __restrict__ gf, C2<RG>* __restrict__ Gf) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int Lx = g.L[0], Ly = g.L[1];
+  C2<R>* tw;
+  short* pos;
+  C2<R>* tile = setup_smem<R>(smem_raw, twg, posg, Lx, Ly, &tw, &pos);
+  const int RS = Lx + 1, PS = Ly * RS;
+  const int64_t slab = blockIdx.x;
+  const int plane = Lx * Ly;
+  for (int i = threadIdx.x; i < 4 * plane; i += blockDim.x) {
+    const int f = i / plane, r = i - f * plane, y = r / Lx, x = r - y * Lx;
+    tile[f * PS + y * RS + x] = data[(int64_t)f * g.V + slab * plane + r];
+  }
+  __syncthreads();
+  fft_lines_dif<R, +1>(tile, Lines{4 * Ly, 4 * Ly, RS, 0, 1}, dx, tw);
+  fft_lines_dif<R, +1>(tile, Lines{4 * Lx, Lx, 1, PS, RS}, dy, tw + Lx);
+  for (int i = threadIdx.x; i < plane; i += blockDim.x) {
+    const int y = i / Lx, x = i - y * Lx;
+    const int o = pos[Lx + y] * RS + pos[x];
+    double2 u[3], v[3];
+    gauge_from_packed(ccast<double, R>(tile[o]), ccast<double, R>(tile[PS + o]), ccast<double, R>(tile[2 * PS + o]),
+                      ccast<double, R>(tile[3 * PS + o]), u, v);
+    store_gauge<RG, GROWS>(g.V, slab * plane + i, u, v, gf, Gf);
+  }
+}
+
+// Unfused variant for planes whose four fields do not fit in shared memory:
+// the inverse (x, y) transform has already been applied to data.
+template <typename R, typename RG, int GROWS>
+__global__ void gauge_from_delta_kernel(Geom g, const C2<R>* __restrict__ data, C2<RG>* __restrict__ gf,
+                                        C2<RG>* __restrict__ Gf) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= g.V) return;
+  double2 u[3], v[3];
+  gauge_from_packed(ccast<double, R>(data[s]), ccast<double, R>(data[g.V + s]), ccast<double, R>(data[2 * g.V + s]),
+                    ccast<double, R>(data[3 * g.V + s]), u, v);
+  store_gauge<RG, GROWS>(g.V, s, u, v, gf, Gf);
+}
+
+// ---------------------------------------------------------------------------
+// plan and launchers
+// ---------------------------------------------------------------------------
+
+static int radix_schedule(int N, int* radix) {
+  int a = 0, b = 0, n = N;
+  while (n % 2 == 0) { n /= 2; ++a; }
+  while (n % 3 == 0) { n /= 3; ++b; }
+  if (n != 1 || N < 2) return -1;
+  int k = 0;
+  while (a >= 3) { radix[k++] = 8; a -= 3; }
+  if (a == 2) radix[k++] = 4;
+  if (a == 1) radix[k++] = 2;
+  while (b-- > 0) radix[k++] = 3;
+  return k;
+}
+
+// Position of natural index n in the digit-reversed order that the DIT
+// stages expect (and the DIF stages produce) for the given radix sequence.
+static void digit_positions(int N, const int* radix, int nst, short* pos) {
+  if (nst == 0) { pos[0] = 0; return; }
+  const int Rl = radix[nst - 1], Ns = N / Rl;
+  std::vector<short> sub(Ns);
+  digit_positions(Ns, radix, nst - 1, sub.data());
+  for (int n = 0; n < N; ++n) pos[n] = (short)((n % Rl) * Ns + sub[n / Rl]);
+}
+
+void fft_positions(const FFTPlan& p, short* out) {
+  int off = 0;
+  for (int mu = 0; mu < 4; ++mu) {
+    digit_positions(p.d[mu].N, p.d[mu].radix, p.d[mu].nst, out + off);
+    off += p.d[mu].N;
+  }
+}
+
+static int threads_for(int points) {
+  int t = (points + 7) / 8;
+  t = ((t + 31) / 32) * 32;
+  return std::max(64, std::min(512, t));
+}
+
+cudaError_t configure_fft_plan(const int L[4], int real_bytes, FFTPlan* p) {
+  const size_t cb = 2 * (size_t)real_bytes;  // bytes per complex element
+  for (int mu = 0; mu < 4; ++mu) {
+    p->d[mu].N = L[mu];
+    p->d[mu].nst = radix_schedule(L[mu], p->d[mu].radix);
+    if (p->d[mu].nst < 0) return cudaErrorInvalidValue;
+  }
+  const int Lx = L[0], Ly = L[1], Lz = L[2], Lt = L[3];
+  const size_t hxy = (size_t)((Lx + Ly + 1) & ~1) * cb + (size_t)((Lx + Ly + 7) & ~7) * 2;
+  const size_t hzt = (size_t)((Lz + Lt + 1) & ~1) * cb + (size_t)((Lz + Lt + 7) & ~7) * 2;
+  const size_t plane_xy = (size_t)Ly * (Lx + 1) * cb;
+  const size_t budget = 100 * 1024, maxsm = 220 * 1024;
+  p->fpb_xy = 4;
+  while (p->fpb_xy > 1 && p->fpb_xy * plane_xy > budget) p->fpb_xy /= 2;
+  if (plane_xy * p->fpb_xy + hxy > maxsm) return cudaErrorInvalidValue;
+  p->smem_xy = hxy + p->fpb_xy * plane_xy;
+  p->fuse_g = (4 * plane_xy + hxy <= maxsm) ? 1 : 0;
+  p->smem_c = hxy + 4 * plane_xy;
+  int xc = 1;
+  for (int c = 8; c >= 1; c /= 2) {
+    if (Lx % c) continue;
+    if (hzt + (size_t)Lt * (Lz * c + 1) * cb <= budget) { xc = c; break; }
+  }
+  if (xc == 1 && Lx % 2 == 0 && hzt + (size_t)Lt * (Lz * 2 + 1) * cb <= maxsm) xc = 2;
+  p->xc = xc;
+  p->smem_zt = hzt + (size_t)Lt * (Lz * xc + 1) * cb;
+  if (p->smem_zt > maxsm) return cudaErrorInvalidValue;
+  p->threads_xy = threads_for(p->fpb_xy * Lx * Ly);
+  p->threads_zt = threads_for(Lz * Lt * xc);
+  p->threads_c = threads_for(4 * Lx * Ly);
+  return cudaSuccess;
+}
+
+template <typename K> static cudaError_t allow_smem(K kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename R>
+cudaError_t launch_fft_xy(const Geom& g, const FFTPlan& p, C2<R>* data, const C2<R>* tw, const short* pos, int sign,
+                          int nfields, cudaStream_t s) {
+  int fpb = std::min(p.fpb_xy, nfields);
+  while (nfields % fpb) fpb /= 2;
+  const int thr = threads_for(fpb * g.L[0] * g.L[1]);
+  const size_t smem = smem_header_bytes<R>(g.L[0], g.L[1]) + (size_t)fpb * g.L[1] * (g.L[0] + 1) * sizeof(C2<R>);
+  dim3 grid((unsigned)(g.L[2] * g.L[3]), (unsigned)(nfields / fpb));
+  cudaError_t e;
+  if (sign < 0) {
+    if ((e = allow_smem(fft_xy_kernel<R, -1>, smem)) != cudaSuccess) return e;
+    fft_xy_kernel<R, -1><<<grid, thr, smem, s>>>(g, p.d[0], p.d[1], data, tw, pos, fpb);
+  } else {
+    if ((e = allow_smem(fft_xy_kernel<R, +1>, smem)) != cudaSuccess) return e;
+    fft_xy_kernel<R, +1><<<grid, thr, smem, s>>>(g, p.d[0], p.d[1], data, tw, pos, fpb);
+  }
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_fft_zt(const Geom& g, const FFTPlan& p, C2<R>* data, const C2<R>* tw, const short* pos,
+                          const R* K, int mode, int nfields, cudaStream_t s) {
+  const size_t smem = p.smem_zt;
+  dim3 grid((unsigned)(g.L[0] / p.xc * g.L[1]), (unsigned)nfields);
+  cudaError_t e = allow_smem(fft_zt_filter_kernel<R>, smem);
+  if (e != cudaSuccess) return e;
+  fft_zt_filter_kernel<R><<<grid, p.threads_zt, smem, s>>>(g, p.d[2], p.d[3], data, tw, pos, K, p.xc, mode);
+  return cudaGetLastError();
+}
+
+template <typename R, typename RG, int GROWS>
+cudaError_t launch_fft_xy_inv_gauge(const Geom& g, const FFTPlan& p, C2<R>* data, const C2<R>* tw, const short* pos,
+                                    C2<RG>* gfield, C2<RG>* Gfield, cudaStream_t s) {
+  cudaError_t e;
+  if (!p.fuse_g) {
+    if ((e = launch_fft_xy<R>(g, p, data, tw, pos, +1, 4, s)) != cudaSuccess) return e;
+    gauge_from_delta_kernel<R, RG, GROWS><<<(unsigned)((g.V + 127) / 128), 128, 0, s>>>(g, data, gfield, Gfield);
+    return cudaGetLastError();
+  }
+  const size_t smem = p.smem_c;
+  if ((e = allow_smem(fft_xy_inv_gauge_kernel<R, RG, GROWS>, smem)) != cudaSuccess) return e;
+  fft_xy_inv_gauge_kernel<R, RG, GROWS><<<(unsigned)(g.L[2] * g.L[3]), p.threads_c, smem, s>>>(
+      g, p.d[0], p.d[1], data, tw, pos, gfield, Gfield);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_fft_xy<double>(const Geom&, const FFTPlan&, C2<double>*, const C2<double>*, const short*,
+                                           int, int, cudaStream_t);
+template cudaError_t launch_fft_xy<float>(const Geom&, const FFTPlan&, C2<float>*, const C2<float>*, const short*,
+                                          int, int, cudaStream_t);
+template cudaError_t launch_fft_zt<double>(const Geom&, const FFTPlan&, C2<double>*, const C2<double>*, const short*,
+                                           const double*, int, int, cudaStream_t);
+template cudaError_t launch_fft_zt<float>(const Geom&, const FFTPlan&, C2<float>*, const C2<float>*, const short*,
+                                          const float*, int, int, cudaStream_t);
+#define LGF_INST_C(R, RG, GR)                                                                                    \
+  template cudaError_t launch_fft_xy_inv_gauge<R, RG, GR>(const Geom&, const FFTPlan&, C2<R>*, const C2<R>*,      \
+                                                          const short*, C2<RG>*, C2<RG>*, cudaStream_t);
+LGF_INST_C(double, double, 3)
+LGF_INST_C(double, double, 2)
+LGF_INST_C(float, float, 2)
+LGF_INST_C(float, float, 3)
+
+}  // namespace lgf

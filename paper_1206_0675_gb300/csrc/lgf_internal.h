@@ -1,0 +1,132 @@
+// Internal interface between the lgf C-ABI layer (lgf_api.cu) and the
+// kernel translation units.  Not installed; no torch types anywhere.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lgf_common.cuh"
+
+namespace lgf {
+
+// Controller state kept in device memory.  Written by the last CTA of the
+// measurement kernel; read by the host after a fix and by the graph's WHILE
+// condition.
+struct DevState {
+  double F;          // gauge functional of the current links
+  double theta;      // stopping quantity of the current links
+  double F_prev;     // F before the last step
+  double tol;        // loop runs while theta >= tol
+  int iter;          // link updates performed since the counter was reset
+  int max_iter;      // loop stops when iter reaches it
+  int status;        // 0 ok, 1 non-finite F or theta, 2 timeout
+  unsigned int ticket;  // CTA completion counter of the measurement reduction
+  int hist_cap;      // capacity of the history buffers (0 = none)
+  int pad;
+  double* F_hist;    // F after measurement number i (i = iter) if i < hist_cap
+  double* theta_hist;
+};
+
+enum { ST_OK = 0, ST_NONFINITE = 1 };
+
+constexpr int MEASURE_THREADS = 256;
+
+inline int64_t measure_blocks(int64_t V) { return (V + MEASURE_THREADS - 1) / MEASURE_THREADS; }
+
+// ---- lgf_site.cu -------------------------------------------------------
+// Delta, F and theta of the current links (Sec. 2; kernel k2 of Sec. 3.2).
+// count_iter != 0: this measurement follows a link update (iter += 1).
+// use_cond != 0: set the graph conditional to (theta >= tol && iter < max_iter).
+template <typename R, int ROWS>
+cudaError_t launch_measure(const Geom& g, const C2<R>* links, C2<R>* delta, double* partials, DevState* st,
+                           int count_iter, unsigned long long cond_handle, int use_cond, cudaStream_t s);
+
+// U_mu(x) <- g(x) U_mu(x) g^dagger(x + mu^) in place (Sec. 2 eq. 2; kernel k6).
+// Links in precision R with LROWS stored rows; g in precision R with GROWS rows.
+template <typename R, int LROWS, int GROWS>
+cudaError_t launch_update(const Geom& g, C2<R>* links, const C2<R>* gfield, cudaStream_t s);
+
+// AoS FP64 user layout [mu][t][z][y][x][3][3][2] -> SoA links of precision R.
+template <typename R, int ROWS>
+cudaError_t launch_links_from_aos(const Geom& g, const double* aos, C2<R>* links, cudaStream_t s);
+template <typename R, int ROWS>
+cudaError_t launch_links_to_aos(const Geom& g, const C2<R>* links, double* aos, cudaStream_t s);
+// Site matrix field (nmat = 1) SoA <-> AoS, FP64 user layout [t][z][y][x][3][3][2].
+template <typename R, int ROWS>
+cudaError_t launch_sites_to_aos(const Geom& g, const C2<R>* field, double* aos, cudaStream_t s);
+template <typename R, int ROWS>
+cudaError_t launch_sites_from_aos(const Geom& g, const double* aos, C2<R>* field, cudaStream_t s);
+// Packed divergence fields -> 3x3 anti-Hermitian matrices in the site AoS layout.
+template <typename R>
+cudaError_t launch_delta_to_aos(const Geom& g, const C2<R>* delta, double* aos, cudaStream_t s);
+
+// Largest SU(3) defect max(|U U^dag - 1|, |det U - 1|) of an AoS link array,
+// as the bit pattern of a non-negative double (NaN maps to +inf bits).
+cudaError_t launch_su3_defect(const double* aos, int64_t nmat, unsigned long long* out_bits, cudaStream_t s);
+
+// Loop parameters of the controller state (tol, max_iter, history);
+// reset_iter != 0 also zeroes the iteration counter and the status word.
+cudaError_t launch_set_state(DevState* st, double tol, int max_iter, int reset_iter, int hist_cap, double* F_hist,
+                             double* theta_hist, cudaStream_t s);
+
+// Complex array precision conversion (n elements).
+cudaError_t launch_c2_f64_to_f32(const double2* in, float2* out, int64_t n, cudaStream_t s);
+cudaError_t launch_c2_f32_to_f64(const float2* in, double2* out, int64_t n, cudaStream_t s);
+
+// G64 = reunitarize(G32) in FP64 (3-row FP32 site field -> 3-row FP64 site field).
+cudaError_t launch_project_sites_f32_to_f64(const Geom& g, const float2* G32, double2* G64, cudaStream_t s);
+
+// Site field G <- 1.
+template <typename R, int ROWS>
+cudaError_t launch_set_identity(const Geom& g, C2<R>* field, cudaStream_t s);
+
+// Momentum filter table K(k) = alpha * p2max / p2(k) / V with K(0) = 0, stored
+// [kt][kz][ky][kx] in precision R (kernel k1 of Sec. 3.2).
+template <typename R>
+cudaError_t launch_filter_table(const Geom& g, const double* sin2 /* 4 x Lmax: 4 sin^2(pi k/L) */, int lmax,
+                                double alpha, double p2max, int plain_sd, R* K, cudaStream_t s);
+
+// ---- lgf_fft.cu ---------------------------------------------------------
+// Radix schedule of one lattice direction.
+struct FFTDir {
+  int N;
+  int nst;
+  int radix[8];
+};
+
+struct FFTPlan {
+  FFTDir d[4];
+  int xc;          // consecutive x columns per CTA in the (z,t) pass
+  int fpb_xy;      // fields per CTA in the (x,y) passes (1, 2 or 4)
+  int threads_xy;
+  int threads_zt;
+  int threads_c;
+  size_t smem_xy;
+  size_t smem_zt;
+  size_t smem_c;   // pass C (needs all 4 fields when fused with g)
+  int fuse_g;      // pass C computes g directly (4 fields fit in shared memory)
+};
+
+// Twiddle tables W_N^m = exp(-2 pi i m / N), m < N, for the four directions,
+// concatenated at offsets 0, Lx, Lx+Ly, Lx+Ly+Lz (FP64 and FP32 copies).
+// pos: digit-reversal position tables of the four directions (fft_positions).
+template <typename R>
+cudaError_t launch_fft_xy(const Geom& g, const FFTPlan& p, C2<R>* data, const C2<R>* tw, const short* pos, int sign,
+                          int nfields, cudaStream_t s);
+// mode 0: forward (z,t) DFT, multiply by K, inverse (z,t) DFT (pass B);
+// mode -1 / +1: forward / inverse (z,t) DFT only (K unused).
+template <typename R>
+cudaError_t launch_fft_zt(const Geom& g, const FFTPlan& p, C2<R>* data, const C2<R>* tw, const short* pos,
+                          const R* K, int mode, int nfields, cudaStream_t s);
+// Inverse (x,y) transform fused with g(x) = reunitarize(1 + Delta'(x)) in FP64;
+// g stored with GROWS rows in precision RG; optional G <- g G (precision RG2 with 3 rows).
+template <typename R, typename RG, int GROWS>
+cudaError_t launch_fft_xy_inv_gauge(const Geom& g, const FFTPlan& p, C2<R>* data, const C2<R>* tw, const short* pos,
+                                    C2<RG>* gfield, C2<RG>* Gfield, cudaStream_t s);
+
+cudaError_t configure_fft_plan(const int L[4], int real_bytes, FFTPlan* p);
+// Digit-reversal position tables of the four directions, concatenated
+// (Lx + Ly + Lz + Lt entries).
+void fft_positions(const FFTPlan& p, short* out);
+
+}  // namespace lgf

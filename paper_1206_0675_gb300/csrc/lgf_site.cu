@@ -1,0 +1,496 @@
+// Site-local kernels of FA steepest-descent Landau gauge fixing:
+//   * measure  : Delta(x), F and theta with a deterministic FP64 reduction
+//                (arXiv:1206.0675 Sec. 2 and kernel k2 of Sec. 3.2),
+//   * update   : U_mu(x) -> g(x) U_mu(x) g^dagger(x + mu^) (Sec. 2 eq. 2, kernel k6),
+//   * layout conversion, SU(3) validation, the momentum filter table (k1).
+// One thread per lattice site; link arrays are structure-of-arrays so that a
+// warp touches 32 consecutive sites of one matrix element per load.
+#include <cmath>
+
+#include "lgf_internal.h"
+
+namespace lgf {
+
+// ---------------------------------------------------------------------------
+// measure: Delta, F, theta
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block sum of two values in a fixed order; result valid in thread 0.
+__device__ __forceinline__ void block_sum2(double& a, double& b) {
+  __shared__ double sa[32], sb[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  a = warp_sum(a);
+  b = warp_sum(b);
+  if (lane == 0) { sa[warp] = a; sb[warp] = b; }
+  __syncthreads();
+  if (warp == 0) {
+    a = lane < nw ? sa[lane] : 0.0;
+    b = lane < nw ? sb[lane] : 0.0;
+    a = warp_sum(a);
+    b = warp_sum(b);
+  }
+  __syncthreads();
+}
+
+template <typename R, int ROWS>
+__global__ void __launch_bounds__(MEASURE_THREADS)
+measure_kernel(Geom g, MatField<R, ROWS> U, C2<R>* __restrict__ delta, double* __restrict__ partials,
+               DevState* __restrict__ st, int count_iter, unsigned long long cond, int use_cond) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double fsum = 0.0, tsum = 0.0;
+  if (s < g.V) {
+    int c[4];
+    site_coords(g, s, c);
+    // W = sum_mu [U_mu(x - mu^) - U_mu(x)]; only the entries that enter its
+    // traceless anti-Hermitian part are accumulated.
+    R im0 = 0, im1 = 0, im2 = 0;           // Im W_ii
+    C2<R> w01 = mkc<R>(0, 0), w02 = mkc<R>(0, 0), w12 = mkc<R>(0, 0);  // W_ij - conj(W_ji)
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+      M3<R> u;
+      U.load_ro(mu, s, u);
+      fsum += (double)u.e[0][0].x + (double)u.e[1][1].x + (double)u.e[2][2].x;
+      im0 -= u.e[0][0].y; im1 -= u.e[1][1].y; im2 -= u.e[2][2].y;
+      w01 = csub<R>(w01, csub<R>(u.e[0][1], cconj<R>(u.e[1][0])));
+      w02 = csub<R>(w02, csub<R>(u.e[0][2], cconj<R>(u.e[2][0])));
+      w12 = csub<R>(w12, csub<R>(u.e[1][2], cconj<R>(u.e[2][1])));
+      M3<R> b;
+      U.load_ro(mu, site_back(g, s, c, mu), b);
+      im0 += b.e[0][0].y; im1 += b.e[1][1].y; im2 += b.e[2][2].y;
+      w01 = cadd<R>(w01, csub<R>(b.e[0][1], cconj<R>(b.e[1][0])));
+      w02 = cadd<R>(w02, csub<R>(b.e[0][2], cconj<R>(b.e[2][0])));
+      w12 = cadd<R>(w12, csub<R>(b.e[1][2], cconj<R>(b.e[2][1])));
+    }
+    const R tr = (im0 + im1 + im2) * (R)(1.0 / 3.0);
+    const R a0 = im0 - tr, a1 = im1 - tr, a2 = im2 - tr;
+    const C2<R> d01 = cscale<R>(w01, (R)0.5), d02 = cscale<R>(w02, (R)0.5), d12 = cscale<R>(w12, (R)0.5);
+    delta[s] = mkc<R>(a0, a1);
+    delta[g.V + s] = d01;
+    delta[2 * g.V + s] = d02;
+    delta[3 * g.V + s] = d12;
+    // ||Delta_A||_F^2 in FP64
+    const double da0 = a0, da1 = a1, da2 = a2;
+    tsum = da0 * da0 + da1 * da1 + da2 * da2 +
+           2.0 * ((double)d01.x * d01.x + (double)d01.y * d01.y + (double)d02.x * d02.x + (double)d02.y * d02.y +
+                  (double)d12.x * d12.x + (double)d12.y * d12.y);
+  }
+  block_sum2(fsum, tsum);
+  __shared__ int is_last;
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = fsum;
+    partials[2 * blockIdx.x + 1] = tsum;
+    __threadfence();
+    const unsigned int t = atomicAdd(&st->ticket, 1u);
+    is_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  // Final sum over the per-CTA partials in a fixed order (independent of
+  // which CTA finished last), so the result is bit-reproducible.
+  double f = 0.0, t = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+    f += __ldcg(&partials[2 * i]);
+    t += __ldcg(&partials[2 * i + 1]);
+  }
+  block_sum2(f, t);
+  if (threadIdx.x == 0) {
+    const double Vd = (double)g.V;
+    const double F = f / (12.0 * Vd);
+    const double th = 4.0 * t / (3.0 * Vd);
+    int it = st->iter;
+    if (count_iter) {
+      it += 1;
+      st->iter = it;
+      st->F_prev = st->F;
+    }
+    st->F = F;
+    st->theta = th;
+    if (it < st->hist_cap) {
+      st->F_hist[it] = F;
+      st->theta_hist[it] = th;
+    }
+    const bool finite = isfinite(F) && isfinite(th);
+    if (!finite) st->status = ST_NONFINITE;
+    st->ticket = 0u;
+    if (use_cond) {
+      cudaGraphConditionalHandle h = (cudaGraphConditionalHandle)cond;
+      cudaGraphSetConditional(h, (finite && th >= st->tol && it < st->max_iter) ? 1u : 0u);
+    }
+  }
+}
+
+template <typename R, int ROWS>
+cudaError_t launch_measure(const Geom& g, const C2<R>* links, C2<R>* delta, double* partials, DevState* st,
+                           int count_iter, unsigned long long cond_handle, int use_cond, cudaStream_t s) {
+  MatField<R, ROWS> U{const_cast<C2<R>*>(links), g.V};
+  const int64_t nb = measure_blocks(g.V);
+  measure_kernel<R, ROWS><<<(unsigned)nb, MEASURE_THREADS, 0, s>>>(g, U, delta, partials, st, count_iter, cond_handle,
+                                                                   use_cond);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// update: U_mu(x) <- g(x) U_mu(x) g^dagger(x + mu^)
+// ---------------------------------------------------------------------------
+
+constexpr int UPDATE_THREADS = 128;
+
+template <typename R, int LROWS, int GROWS>
+__global__ void __launch_bounds__(UPDATE_THREADS)
+update_kernel(Geom g, MatField<R, LROWS> U, MatField<R, GROWS> Gf) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= g.V) return;
+  int c[4];
+  site_coords(g, s, c);
+  C2<R> gx[2][3];
+  Gf.load_rows01_ro(0, s, gx);  // rows 1-2 of g(x) are all the product needs
+#pragma unroll 1
+  for (int mu = 0; mu < 4; ++mu) {
+    M3<R> u;
+    U.load(mu, s, u);
+    M3<R> h;
+    Gf.load_ro(0, site_fwd(g, s, c, mu), h);
+    // T = g(x)[rows 0,1] * U
+    C2<R> T[2][3];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        C2<R> acc = cmul<R>(gx[i][0], u.e[0][j]);
+        acc = cfma<R>(gx[i][1], u.e[1][j], acc);
+        T[i][j] = cfma<R>(gx[i][2], u.e[2][j], acc);
+      }
+    // rows 0,1 of T h^dagger; row 2 = (row0 x row1)^* (the result is in SU(3))
+    M3<R> o;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        C2<R> acc = cmulc<R>(T[i][0], h.e[j][0]);
+        acc = cfmac<R>(T[i][1], h.e[j][1], acc);
+        o.e[i][j] = cfmac<R>(T[i][2], h.e[j][2], acc);
+      }
+    if (LROWS == 3) su3_third_row<R>(o.e[0], o.e[1], o.e[2]);
+    U.store(mu, s, o);
+  }
+}
+
+template <typename R, int LROWS, int GROWS>
+cudaError_t launch_update(const Geom& g, C2<R>* links, const C2<R>* gfield, cudaStream_t s) {
+  MatField<R, LROWS> U{links, g.V};
+  MatField<R, GROWS> Gf{const_cast<C2<R>*>(gfield), g.V};
+  const int64_t nb = (g.V + UPDATE_THREADS - 1) / UPDATE_THREADS;
+  update_kernel<R, LROWS, GROWS><<<(unsigned)nb, UPDATE_THREADS, 0, s>>>(g, U, Gf);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// layout conversion
+// ---------------------------------------------------------------------------
+
+constexpr int CONV_THREADS = 256;
+
+// nmat matrices per site field: links use nmat = 4 (mu), site fields nmat = 1.
+template <typename R, int ROWS>
+__global__ void from_aos_kernel(int64_t V, int nmat, const double2* __restrict__ aos, MatField<R, ROWS> F) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= V * nmat) return;
+  const int m = (int)(i / V);
+  const int64_t s = i - (int64_t)m * V;
+  const double2* src = aos + i * 9;
+#pragma unroll
+  for (int r = 0; r < ROWS; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double2 v = __ldg(&src[r * 3 + c]);
+      F.p[F.off(m, r, c, s)] = mkc<R>((R)v.x, (R)v.y);
+    }
+}
+
+template <typename R, int ROWS>
+__global__ void to_aos_kernel(int64_t V, int nmat, MatField<R, ROWS> F, double2* __restrict__ aos) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= V * nmat) return;
+  const int m = (int)(i / V);
+  const int64_t s = i - (int64_t)m * V;
+  M3<R> M;
+  F.load_ro(m, s, M);
+  double2* dst = aos + i * 9;
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) dst[r * 3 + c] = make_double2((double)M.e[r][c].x, (double)M.e[r][c].y);
+}
+
+template <typename R, int ROWS>
+cudaError_t launch_links_from_aos(const Geom& g, const double* aos, C2<R>* links, cudaStream_t s) {
+  MatField<R, ROWS> F{links, g.V};
+  const int64_t n = 4 * g.V;
+  from_aos_kernel<R, ROWS><<<(unsigned)((n + CONV_THREADS - 1) / CONV_THREADS), CONV_THREADS, 0, s>>>(
+      g.V, 4, reinterpret_cast<const double2*>(aos), F);
+  return cudaGetLastError();
+}
+
+template <typename R, int ROWS>
+cudaError_t launch_links_to_aos(const Geom& g, const C2<R>* links, double* aos, cudaStream_t s) {
+  MatField<R, ROWS> F{const_cast<C2<R>*>(links), g.V};
+  const int64_t n = 4 * g.V;
+  to_aos_kernel<R, ROWS><<<(unsigned)((n + CONV_THREADS - 1) / CONV_THREADS), CONV_THREADS, 0, s>>>(
+      g.V, 4, F, reinterpret_cast<double2*>(aos));
+  return cudaGetLastError();
+}
+
+template <typename R, int ROWS>
+cudaError_t launch_sites_to_aos(const Geom& g, const C2<R>* field, double* aos, cudaStream_t s) {
+  MatField<R, ROWS> F{const_cast<C2<R>*>(field), g.V};
+  to_aos_kernel<R, ROWS><<<(unsigned)((g.V + CONV_THREADS - 1) / CONV_THREADS), CONV_THREADS, 0, s>>>(
+      g.V, 1, F, reinterpret_cast<double2*>(aos));
+  return cudaGetLastError();
+}
+
+template <typename R, int ROWS>
+cudaError_t launch_sites_from_aos(const Geom& g, const double* aos, C2<R>* field, cudaStream_t s) {
+  MatField<R, ROWS> F{field, g.V};
+  from_aos_kernel<R, ROWS><<<(unsigned)((g.V + CONV_THREADS - 1) / CONV_THREADS), CONV_THREADS, 0, s>>>(
+      g.V, 1, reinterpret_cast<const double2*>(aos), F);
+  return cudaGetLastError();
+}
+
+template <typename R>
+__global__ void delta_to_aos_kernel(int64_t V, const C2<R>* __restrict__ d, double2* __restrict__ aos) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= V) return;
+  const C2<R> f0 = d[s], f1 = d[V + s], f2 = d[2 * V + s], f3 = d[3 * V + s];
+  const double a0 = f0.x, a1 = f0.y, a2 = -(a0 + a1);
+  double2* o = aos + s * 9;
+  o[0] = make_double2(0.0, a0);
+  o[1] = make_double2(f1.x, f1.y);
+  o[2] = make_double2(f2.x, f2.y);
+  o[3] = make_double2(-(double)f1.x, (double)f1.y);
+  o[4] = make_double2(0.0, a1);
+  o[5] = make_double2(f3.x, f3.y);
+  o[6] = make_double2(-(double)f2.x, (double)f2.y);
+  o[7] = make_double2(-(double)f3.x, (double)f3.y);
+  o[8] = make_double2(0.0, a2);
+}
+
+template <typename R>
+cudaError_t launch_delta_to_aos(const Geom& g, const C2<R>* delta, double* aos, cudaStream_t s) {
+  delta_to_aos_kernel<R><<<(unsigned)((g.V + CONV_THREADS - 1) / CONV_THREADS), CONV_THREADS, 0, s>>>(
+      g.V, delta, reinterpret_cast<double2*>(aos));
+  return cudaGetLastError();
+}
+
+template <typename R, int ROWS>
+__global__ void identity_kernel(int64_t V, MatField<R, ROWS> F) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= V) return;
+#pragma unroll
+  for (int r = 0; r < ROWS; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) F.p[F.off(0, r, c, s)] = mkc<R>(r == c ? (R)1 : (R)0, (R)0);
+}
+
+template <typename R, int ROWS>
+cudaError_t launch_set_identity(const Geom& g, C2<R>* field, cudaStream_t s) {
+  MatField<R, ROWS> F{field, g.V};
+  identity_kernel<R, ROWS><<<(unsigned)((g.V + CONV_THREADS - 1) / CONV_THREADS), CONV_THREADS, 0, s>>>(g.V, F);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// SU(3) validation of user links
+// ---------------------------------------------------------------------------
+
+__global__ void su3_defect_kernel(const double2* __restrict__ aos, int64_t nmat, unsigned long long* out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double d = 0.0;
+  if (i < nmat) {
+    double2 m[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) m[r][c] = __ldg(&aos[i * 9 + r * 3 + c]);
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        double2 acc = mkc<double>(0.0, 0.0);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) acc = cfmac<double>(m[r][k], m[c][k], acc);
+        if (r == c) acc.x -= 1.0;
+        d = fmax(d, fmax(fabs(acc.x), fabs(acc.y)));
+      }
+    double2 cr[3];
+    su3_third_row<double>(m[0], m[1], cr);  // conj(r0 x r1)
+    // det = r2 . (r0 x r1) = sum_j r2_j conj(cr_j)
+    double2 det = mkc<double>(0.0, 0.0);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) det = cfmac<double>(m[2][j], cr[j], det);
+    d = fmax(d, sqrt((det.x - 1.0) * (det.x - 1.0) + det.y * det.y));
+    bool finite = true;
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) finite = finite && isfinite(m[r][c].x) && isfinite(m[r][c].y);
+    if (!finite || !isfinite(d)) d = INFINITY;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) d = fmax(d, __shfl_down_sync(0xffffffffu, d, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(d));
+}
+
+cudaError_t launch_su3_defect(const double* aos, int64_t nmat, unsigned long long* out_bits, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(out_bits, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  su3_defect_kernel<<<(unsigned)((nmat + CONV_THREADS - 1) / CONV_THREADS), CONV_THREADS, 0, s>>>(
+      reinterpret_cast<const double2*>(aos), nmat, out_bits);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// momentum filter table (kernel k1 of Sec. 3.2)
+// ---------------------------------------------------------------------------
+
+template <typename R>
+__global__ void filter_table_kernel(Geom g, const double* __restrict__ sin2, int lmax, double alpha, double p2max,
+                                    int plain_sd, R* __restrict__ K) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= g.V) return;
+  int c[4];
+  site_coords(g, s, c);
+  const double p2 = sin2[3 * lmax + c[3]] + sin2[2 * lmax + c[2]] + sin2[lmax + c[1]] + sin2[c[0]];
+  double k = 0.0;
+  if (s != 0) k = plain_sd ? alpha / (double)g.V : alpha * p2max / (p2 * (double)g.V);
+  K[s] = (R)k;
+}
+
+template <typename R>
+cudaError_t launch_filter_table(const Geom& g, const double* sin2, int lmax, double alpha, double p2max, int plain_sd,
+                                R* K, cudaStream_t s) {
+  filter_table_kernel<R><<<(unsigned)((g.V + CONV_THREADS - 1) / CONV_THREADS), CONV_THREADS, 0, s>>>(
+      g, sin2, lmax, alpha, p2max, plain_sd, K);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// controller state, precision conversion, FP64 projection of G
+// ---------------------------------------------------------------------------
+
+__global__ void set_state_kernel(DevState* st, double tol, int max_iter, int reset_iter, int hist_cap, double* Fh,
+                                 double* Th) {
+  st->tol = tol;
+  st->max_iter = max_iter;
+  if (reset_iter) {
+    st->iter = 0;
+    st->status = ST_OK;
+  }
+  st->hist_cap = hist_cap;
+  st->F_hist = Fh;
+  st->theta_hist = Th;
+  if (hist_cap > 0 && reset_iter) {
+    Fh[0] = st->F;
+    Th[0] = st->theta;
+  }
+}
+
+cudaError_t launch_set_state(DevState* st, double tol, int max_iter, int reset_iter, int hist_cap, double* F_hist,
+                             double* theta_hist, cudaStream_t s) {
+  set_state_kernel<<<1, 1, 0, s>>>(st, tol, max_iter, reset_iter, hist_cap, F_hist, theta_hist);
+  return cudaGetLastError();
+}
+
+__global__ void c2_f64_to_f32_kernel(const double2* __restrict__ in, float2* __restrict__ out, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = make_float2((float)in[i].x, (float)in[i].y);
+}
+
+__global__ void c2_f32_to_f64_kernel(const float2* __restrict__ in, double2* __restrict__ out, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = make_double2((double)in[i].x, (double)in[i].y);
+}
+
+cudaError_t launch_c2_f64_to_f32(const double2* in, float2* out, int64_t n, cudaStream_t s) {
+  c2_f64_to_f32_kernel<<<(unsigned)((n + CONV_THREADS - 1) / CONV_THREADS), CONV_THREADS, 0, s>>>(in, out, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_c2_f32_to_f64(const float2* in, double2* out, int64_t n, cudaStream_t s) {
+  c2_f32_to_f64_kernel<<<(unsigned)((n + CONV_THREADS - 1) / CONV_THREADS), CONV_THREADS, 0, s>>>(in, out, n);
+  return cudaGetLastError();
+}
+
+// Gram-Schmidt projection of rows 1-2 to SU(3) in FP64, row 3 = (a x b)^*.
+__global__ void project_sites_kernel(int64_t V, const float2* __restrict__ in, double2* __restrict__ out) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= V) return;
+  double2 a[3], b[3], c[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const float2 x = in[(0 * 3 + j) * V + s], y = in[(1 * 3 + j) * V + s];
+    a[j] = make_double2(x.x, x.y);
+    b[j] = make_double2(y.x, y.y);
+  }
+  const double ia = rsqrt(cnorm2<double>(a[0]) + cnorm2<double>(a[1]) + cnorm2<double>(a[2]));
+#pragma unroll
+  for (int j = 0; j < 3; ++j) a[j] = cscale<double>(a[j], ia);
+  double2 ip = cconjmul<double>(a[0], b[0]);
+  ip = cadd<double>(ip, cconjmul<double>(a[1], b[1]));
+  ip = cadd<double>(ip, cconjmul<double>(a[2], b[2]));
+  const double2 nip = make_double2(-ip.x, -ip.y);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) b[j] = cfma<double>(nip, a[j], b[j]);
+  const double ib = rsqrt(cnorm2<double>(b[0]) + cnorm2<double>(b[1]) + cnorm2<double>(b[2]));
+#pragma unroll
+  for (int j = 0; j < 3; ++j) b[j] = cscale<double>(b[j], ib);
+  su3_third_row<double>(a, b, c);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    out[(0 * 3 + j) * V + s] = a[j];
+    out[(1 * 3 + j) * V + s] = b[j];
+    out[(2 * 3 + j) * V + s] = c[j];
+  }
+}
+
+cudaError_t launch_project_sites_f32_to_f64(const Geom& g, const float2* G32, double2* G64, cudaStream_t s) {
+  project_sites_kernel<<<(unsigned)((g.V + CONV_THREADS - 1) / CONV_THREADS), CONV_THREADS, 0, s>>>(g.V, G32, G64);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// explicit instantiations
+// ---------------------------------------------------------------------------
+
+#define LGF_INST_R_ROWS(R, ROWS)                                                                                     \
+  template cudaError_t launch_measure<R, ROWS>(const Geom&, const C2<R>*, C2<R>*, double*, DevState*, int,           \
+                                               unsigned long long, int, cudaStream_t);                              \
+  template cudaError_t launch_links_from_aos<R, ROWS>(const Geom&, const double*, C2<R>*, cudaStream_t);            \
+  template cudaError_t launch_links_to_aos<R, ROWS>(const Geom&, const C2<R>*, double*, cudaStream_t);              \
+  template cudaError_t launch_sites_to_aos<R, ROWS>(const Geom&, const C2<R>*, double*, cudaStream_t);              \
+  template cudaError_t launch_sites_from_aos<R, ROWS>(const Geom&, const double*, C2<R>*, cudaStream_t);            \
+  template cudaError_t launch_set_identity<R, ROWS>(const Geom&, C2<R>*, cudaStream_t);
+
+LGF_INST_R_ROWS(double, 3)
+LGF_INST_R_ROWS(double, 2)
+LGF_INST_R_ROWS(float, 3)
+LGF_INST_R_ROWS(float, 2)
+
+template cudaError_t launch_update<double, 3, 3>(const Geom&, C2<double>*, const C2<double>*, cudaStream_t);
+template cudaError_t launch_update<double, 2, 3>(const Geom&, C2<double>*, const C2<double>*, cudaStream_t);
+template cudaError_t launch_update<float, 2, 2>(const Geom&, C2<float>*, const C2<float>*, cudaStream_t);
+template cudaError_t launch_update<float, 3, 3>(const Geom&, C2<float>*, const C2<float>*, cudaStream_t);
+template cudaError_t launch_delta_to_aos<double>(const Geom&, const C2<double>*, double*, cudaStream_t);
+template cudaError_t launch_delta_to_aos<float>(const Geom&, const C2<float>*, double*, cudaStream_t);
+template cudaError_t launch_filter_table<double>(const Geom&, const double*, int, double, double, int, double*,
+                                                 cudaStream_t);
+template cudaError_t launch_filter_table<float>(const Geom&, const double*, int, double, double, int, float*,
+                                                cudaStream_t);
+
+}  // namespace lgf

@@ -1,0 +1,290 @@
+"""ctypes binding of the lgf C-ABI (include/lgf.h).
+
+Argument marshalling only: every step of the gauge-fixing path runs in the
+CUDA kernels of ``liblgf.so``.  There is no CPU fallback; loading fails with
+a clear error when the library has not been built.
+
+Two layers:
+
+* module-level functions with the C names (``lgf_create``, ``lgf_set_links``,
+  ...) that take and return plain integers / pointers, and
+* ``Lattice``, a small owner object that marshals numpy arrays (host) and
+  torch CUDA tensors (device) into those calls.
+
+Host arrays are complex128 of shape ``(4, Lt, Lz, Ly, Lx, 3, 3)`` for links
+and ``(Lt, Lz, Ly, Lx, 3, 3)`` for site fields, i.e. the library's FP64 user
+layout ``[mu][t][z][y][x][row][col][re, im]``.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblgf.so")
+
+LGF_OK, LGF_E_ARG, LGF_E_NOMEM, LGF_E_CUDA, LGF_E_STATE, LGF_E_NONFINITE, LGF_E_NOTCONV, LGF_E_TIMEOUT, \
+    LGF_E_UNSUPPORTED = range(9)
+LGF_FP64, LGF_FP32, LGF_MIXED = 0, 1, 2
+LGF_STORE18, LGF_STORE12, LGF_TRACK_G, LGF_PLAIN_SD = 0, 1, 2, 8
+LGF_HOST, LGF_DEVICE = 0, 1
+
+_c_int_p = ctypes.POINTER(ctypes.c_int32)
+_c_dbl_p = ctypes.POINTER(ctypes.c_double)
+
+# (name, restype, argtypes) for every entry point of include/lgf.h
+SIGNATURES = [
+    ("lgf_create", ctypes.c_int, [ctypes.POINTER(ctypes.c_int32), ctypes.c_int, ctypes.c_uint32, ctypes.c_void_p,
+                                  ctypes.POINTER(ctypes.c_void_p)]),
+    ("lgf_destroy", ctypes.c_int, [ctypes.c_void_p]),
+    ("lgf_set_links", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    ("lgf_get_links", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    ("lgf_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
+    ("lgf_measure", ctypes.c_int, [ctypes.c_void_p, _c_dbl_p, _c_dbl_p]),
+    ("lgf_fix", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int32, ctypes.c_double, _c_int_p,
+                               _c_dbl_p, _c_dbl_p]),
+    ("lgf_get_transform", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    ("lgf_get_gauge", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    ("lgf_get_divergence", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    ("lgf_set_trace", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
+    ("lgf_fft4", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int]),
+    ("lgf_get_phase", ctypes.c_int, [ctypes.c_void_p, _c_int_p]),
+    ("lgf_status_string", ctypes.c_char_p, [ctypes.c_int]),
+    ("lgf_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
+]
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load liblgf.so (once).  Raises RuntimeError if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build the CUDA library first "
+                           "(python -m paper_1206_0675_gb300.build)")
+    lib = ctypes.CDLL(path)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class LgfError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        lib = load_library()
+        msg = f"{where}: {lib.lgf_status_string(status).decode()}"
+        if detail:
+            msg += f" ({detail})"
+        super().__init__(msg)
+        self.status = status
+
+
+# --- thin C-name wrappers ---------------------------------------------------
+
+def lgf_create(extents, prec: int, flags: int, stream: int = 0) -> int:
+    lib = load_library()
+    ext = (ctypes.c_int32 * 4)(*[int(e) for e in extents])
+    h = ctypes.c_void_p()
+    st = lib.lgf_create(ext, int(prec), ctypes.c_uint32(flags), ctypes.c_void_p(stream or None), ctypes.byref(h))
+    if st != LGF_OK:
+        raise LgfError(st, "lgf_create")
+    return h.value
+
+
+def _check(h, st, where, allow=()):
+    if st != LGF_OK and st not in allow:
+        detail = load_library().lgf_last_error(ctypes.c_void_p(h)).decode(errors="replace")
+        raise LgfError(st, where, detail)
+    return st
+
+
+def lgf_destroy(h: int) -> None:
+    load_library().lgf_destroy(ctypes.c_void_p(h))
+
+
+def lgf_set_links(h: int, ptr: int, where: int) -> None:
+    _check(h, load_library().lgf_set_links(ctypes.c_void_p(h), ctypes.c_void_p(ptr), where), "lgf_set_links")
+
+
+def lgf_get_links(h: int, ptr: int, where: int) -> None:
+    _check(h, load_library().lgf_get_links(ctypes.c_void_p(h), ctypes.c_void_p(ptr), where), "lgf_get_links")
+
+
+def lgf_step(h: int, alpha: float) -> None:
+    _check(h, load_library().lgf_step(ctypes.c_void_p(h), float(alpha)), "lgf_step")
+
+
+def lgf_measure(h: int) -> tuple[float, float]:
+    F, th = ctypes.c_double(), ctypes.c_double()
+    _check(h, load_library().lgf_measure(ctypes.c_void_p(h), ctypes.byref(F), ctypes.byref(th)), "lgf_measure")
+    return F.value, th.value
+
+
+def lgf_fix(h: int, theta_tol: float, max_iter: int, alpha: float) -> tuple[int, float, float, int]:
+    """Returns (iters, F, theta, status); status is LGF_OK or LGF_E_NOTCONV."""
+    it, F, th = ctypes.c_int32(), ctypes.c_double(), ctypes.c_double()
+    st = load_library().lgf_fix(ctypes.c_void_p(h), float(theta_tol), int(max_iter), float(alpha), ctypes.byref(it),
+                                ctypes.byref(F), ctypes.byref(th))
+    _check(h, st, "lgf_fix", allow=(LGF_E_NOTCONV,))
+    return it.value, F.value, th.value, st
+
+
+def lgf_get_transform(h: int, ptr: int, where: int) -> None:
+    _check(h, load_library().lgf_get_transform(ctypes.c_void_p(h), ctypes.c_void_p(ptr), where),
+           "lgf_get_transform")
+
+
+def lgf_get_gauge(h: int, ptr: int, where: int) -> None:
+    _check(h, load_library().lgf_get_gauge(ctypes.c_void_p(h), ctypes.c_void_p(ptr), where), "lgf_get_gauge")
+
+
+def lgf_get_divergence(h: int, ptr: int, where: int) -> None:
+    _check(h, load_library().lgf_get_divergence(ctypes.c_void_p(h), ctypes.c_void_p(ptr), where),
+           "lgf_get_divergence")
+
+
+def lgf_set_trace(h: int, f_ptr: int, t_ptr: int, cap: int) -> None:
+    _check(h, load_library().lgf_set_trace(ctypes.c_void_p(h), ctypes.c_void_p(f_ptr), ctypes.c_void_p(t_ptr),
+                                           int(cap)), "lgf_set_trace")
+
+
+def lgf_fft4(h: int, ptr: int, nfields: int, sign: int, where: int) -> None:
+    _check(h, load_library().lgf_fft4(ctypes.c_void_p(h), ctypes.c_void_p(ptr), int(nfields), int(sign), where),
+           "lgf_fft4")
+
+
+def lgf_get_phase(h: int) -> int:
+    b = ctypes.c_int32()
+    _check(h, load_library().lgf_get_phase(ctypes.c_void_p(h), ctypes.byref(b)), "lgf_get_phase")
+    return b.value
+
+
+# --- marshalling helpers ----------------------------------------------------
+
+_PREC = {"fp64": LGF_FP64, "fp32": LGF_FP32, "mixed": LGF_MIXED}
+
+
+def _host_buffer(arr: np.ndarray, shape) -> np.ndarray:
+    a = np.ascontiguousarray(arr, dtype=np.complex128)
+    if a.shape != tuple(shape):
+        raise ValueError(f"expected shape {tuple(shape)}, got {a.shape}")
+    return a
+
+
+def _is_torch_cuda(x) -> bool:
+    return type(x).__module__.startswith("torch") and getattr(x, "is_cuda", False)
+
+
+class Lattice:
+    """One lattice configuration on the GPU (owns an lgf handle)."""
+
+    def __init__(self, extents, precision: str = "fp64", store12: bool = False, track_G: bool = False,
+                 plain_sd: bool = False, stream: int | None = None):
+        self.extents = tuple(int(e) for e in extents)
+        lx, ly, lz, lt = self.extents
+        self.link_shape = (4, lt, lz, ly, lx, 3, 3)
+        self.site_shape = (lt, lz, ly, lx, 3, 3)
+        flags = (LGF_STORE12 if store12 else 0) | (LGF_TRACK_G if track_G else 0) | (LGF_PLAIN_SD if plain_sd else 0)
+        if stream is None:
+            try:
+                import torch
+                stream = torch.cuda.current_stream().cuda_stream
+            except Exception:
+                stream = 0
+        self.handle = lgf_create(self.extents, _PREC[precision], flags, stream)
+        self._trace = None
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lgf_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # links -------------------------------------------------------------------
+    def set_links(self, U) -> None:
+        """U: complex128 numpy array (host) or a CUDA torch tensor (complex128 or float64 [...,2])."""
+        if _is_torch_cuda(U):
+            if not U.is_contiguous():
+                raise ValueError("device links must be contiguous")
+            lgf_set_links(self.handle, U.data_ptr(), LGF_DEVICE)
+        else:
+            a = _host_buffer(U, self.link_shape)
+            lgf_set_links(self.handle, a.ctypes.data, LGF_HOST)
+
+    def get_links(self, out=None):
+        if out is not None and _is_torch_cuda(out):
+            lgf_get_links(self.handle, out.data_ptr(), LGF_DEVICE)
+            return out
+        a = np.empty(self.link_shape, dtype=np.complex128) if out is None else out
+        lgf_get_links(self.handle, a.ctypes.data, LGF_HOST)
+        return a
+
+    def _site_out(self, fn, out):
+        if out is not None and _is_torch_cuda(out):
+            fn(self.handle, out.data_ptr(), LGF_DEVICE)
+            return out
+        a = np.empty(self.site_shape, dtype=np.complex128) if out is None else out
+        fn(self.handle, a.ctypes.data, LGF_HOST)
+        return a
+
+    def get_transform(self, out=None):
+        return self._site_out(lgf_get_transform, out)
+
+    def get_gauge(self, out=None):
+        return self._site_out(lgf_get_gauge, out)
+
+    def get_divergence(self, out=None):
+        return self._site_out(lgf_get_divergence, out)
+
+    # algorithm ---------------------------------------------------------------
+    def step(self, alpha: float = 0.08) -> None:
+        lgf_step(self.handle, alpha)
+
+    def measure(self) -> tuple[float, float]:
+        return lgf_measure(self.handle)
+
+    def fix(self, theta_tol: float = 1e-15, max_iter: int = 10000, alpha: float = 0.08):
+        """Returns (iters, F, theta, converged)."""
+        it, F, th, st = lgf_fix(self.handle, theta_tol, max_iter, alpha)
+        return it, F, th, st == LGF_OK
+
+    def set_trace(self, cap: int):
+        """Record F and theta of every measurement of the next fix(); returns the (F, theta) arrays."""
+        if cap <= 0:
+            lgf_set_trace(self.handle, 0, 0, 0)
+            self._trace = None
+            return None
+        Fh = np.zeros(cap)
+        Th = np.zeros(cap)
+        lgf_set_trace(self.handle, Fh.ctypes.data, Th.ctypes.data, cap)
+        self._trace = (Fh, Th)
+        return self._trace
+
+    def fft4(self, data: np.ndarray, sign: int = -1) -> np.ndarray:
+        """The library's 4D DFT of 4 complex fields, shape (4, Lt, Lz, Ly, Lx), host arrays."""
+        lx, ly, lz, lt = self.extents
+        a = _host_buffer(data, (4, lt, lz, ly, lx)).copy()
+        lgf_fft4(self.handle, a.ctypes.data, 4, sign, LGF_HOST)
+        return a
+
+    @property
+    def phase(self) -> int:
+        return lgf_get_phase(self.handle)
