@@ -1,0 +1,380 @@
+#!/usr/bin/env python
+"""Benchmark of Fourier-accelerated steepest-descent Landau gauge fixing.
+
+Workload: a 32^4 SU(3) lattice built as U_mu(x) = h(x) exp(i eps sum_a c_a
+lambda_a/2) h^dag(x+mu) (eps = 1.0, Haar h, seed = rank), alpha = 0.08.
+One "step" is one body of Algorithm 1 (4D FFT of the divergence, filter,
+inverse FFT, g = reunitarize(1 + Delta'), link update, measurement of Delta,
+F and theta) in plain FP64 with 18-real links, run through the C-ABI.
+
+Printed: one JSON line with iterations/s (the headline), site updates/s,
+per-kernel times, the roofline of the dominant kernel, the FP32 12-real
+rate, the wall time to theta < 1e-15 of plain FP64 and of the mixed
+FP32 -> FP64 mode, an end-to-end figure through host buffers, the CPU
+oracle's rate on the host cores, and the SM clocks seen while timing.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lgf|reference]
+
+With --impl reference the CPU oracle (plain FP64 numpy) is timed on the
+same workload and metric instead.  Multi-GPU runs (torchrun) are replicas:
+each rank fixes its own lattice, no data moves between GPUs.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import resource
+import shutil
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1206_0675_gb300 import accounting, fields  # noqa: E402
+
+EXT = (32, 32, 32, 32)
+EPS = 1.0
+ALPHA = 0.08
+TOL = 1e-15
+METRIC = "FA-SD iters/s at 32^4 (plain FP64, 18-real links)"
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+# FP64 pipe of a GB300: 152 SMs x 2 FP64 instructions per clock x 2070 MHz;
+# counted as FMA-equivalents (2 flops per FP64 instruction).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+
+
+# DRAM bytes (read + write) per launch from the committed ncu capture of the
+# FP64 update kernel at 32^4 (profiles/update_kernel_fp64_32x4.md), valid only
+# while the kernel's sources are unchanged (sha256 prefixes of the files).
+NCU_TRAFFIC = {
+    "update": {"bytes": 772.115712e6 + 579.595264e6,
+               "sources": {"paper_1206_0675_gb300/csrc/lgf_site.cu": "8ea91052234455c8",
+                           "paper_1206_0675_gb300/csrc/lgf_common.cuh": "9033a8a14b8a51a5"}},
+}
+
+
+def ncu_traffic(kernel):
+    import hashlib
+    rec = NCU_TRAFFIC.get(kernel)
+    if rec is None:
+        return None
+    for path, h in rec["sources"].items():
+        with open(os.path.join(ROOT, path), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest()[:16] != h:
+                return None
+    return rec["bytes"]
+
+
+def workload_desc():
+    return (f"SU(3) {EXT[0]}^4 periodic lattice, U_mu(x)=h(x) exp(i eps sum_a c_a lambda_a/2) h^dag(x+mu), "
+            f"eps={EPS}, c_a~N(0,1), Haar h, seed=rank; plain FA-SD alpha={ALPHA}")
+
+
+def peaks():
+    try:
+        with open(PEAKS_PATH) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.lines: list[str] = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        exe = shutil.which("nvidia-smi")
+        if exe is None:
+            return
+        self.proc = subprocess.Popen([exe, f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                      "-i", str(self.gpu), "-lms", "100"], stdout=subprocess.PIPE,
+                                     stderr=subprocess.DEVNULL, text=True)
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        time.sleep(0.3)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (cpu_baseline leg and --impl reference)
+# ---------------------------------------------------------------------------
+
+def oracle_iterations(U, n):
+    """n bodies of Algorithm 1 with the CPU oracle; returns (seconds, cores used)."""
+    from oracle import lgf_oracle as O
+    K = O.fa_filter(EXT, ALPHA)
+    _, _, D = O.measure(U)
+    r0 = resource.getrusage(resource.RUSAGE_SELF)
+    t0 = time.perf_counter()
+    for _ in range(n):
+        U, _ = O.fa_step(U, ALPHA, K, D)
+        _, _, D = O.measure(U)
+    dt = time.perf_counter() - t0
+    r1 = resource.getrusage(resource.RUSAGE_SELF)
+    cpu = (r1.ru_utime - r0.ru_utime) + (r1.ru_stime - r0.ru_stime)
+    return dt, max(1, int(round(cpu / dt))), U
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    U = fields.random_links(EXT, EPS, 0)
+    # one warm-up body sizes the run so that it ends within a few minutes
+    t1, _, U = oracle_iterations(U, 1)
+    budget = 150.0
+    W = min(args.warmup, max(0, int(budget * 0.1 / t1)))
+    K = max(1, min(args.steps, int(budget / t1)))
+    if W:
+        _, _, U = oracle_iterations(U, W)
+    dt, cores, _ = oracle_iterations(U, K)
+    value = K / dt
+    sample = (f"{K} oracle bodies of Algorithm 1 (FFT, filter, IFFT, g, update, measure) on the 32^4 field, "
+              f"after {W + 1} warm-up bodies")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world,
+        "steps": K, "warmup": W + 1, "ms_per_step": 1e3 * dt / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_desc(), "lattice": list(EXT), "precision": "fp64", "storage": "18-real",
+                   "engine": "CPU oracle (numpy FP64)"},
+        "cpu_baseline": {"value": value, "unit": "iters/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def time_steps(torch, lat, K):
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(K):
+        lat.step(ALPHA)
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def run_lgf(args, rank, world, local_rank):
+    import torch
+    from paper_1206_0675_gb300 import lgf
+
+    torch.cuda.set_device(local_rank)
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+
+    V = int(np.prod(EXT))
+    U = fields.random_links(EXT, EPS, rank)
+    hbm_peak, peak_kind = peaks()
+
+    # ---- plain FP64, 18-real: the headline --------------------------------
+    lat = lgf.Lattice(EXT, "fp64")
+    lat.set_links(U)
+    for _ in range(args.warmup):
+        lat.step(ALPHA)
+    torch.cuda.synchronize()
+    lat.set_timing(True)
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    if dist:
+        tdist.barrier()
+    torch.cuda.synchronize()
+    ms = time_steps(torch, lat, args.steps)
+    clocks = sampler.stop()
+    kms, nsteps = lat.get_timing()
+    lat.set_timing(False)
+    if dist:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    value = world * args.steps / (ms / 1e3)
+
+    ops = accounting.fp64_ops_per_site(EXT, rows=3)
+    byt = accounting.bytes_per_site(8, 3, 3, k_bytes=8)
+    per_kernel = {}
+    for name, t_ms in zip(accounting.KERNELS, kms):
+        per_kernel[name] = {
+            "ms": t_ms,
+            "fp64_tflops": 2 * ops[name] * V / (t_ms * 1e-3) / 1e12 if t_ms > 0 else None,
+            "gbs": byt[name] * V / (t_ms * 1e-3) / 1e9 if t_ms > 0 else None,
+        }
+    dom = max(accounting.KERNELS, key=lambda k: per_kernel[k]["ms"])
+    achieved = per_kernel[dom]["fp64_tflops"]
+    roofline = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": ncu_traffic(dom),
+                "note": "FP64 pipe: every FP64 instruction counted as one FMA (2 flops); peak = 152 SMs x 2 "
+                        "FP64 inst/clk x 2070 MHz; per-launch time from CUDA events on the launching stream"}
+    b_alg = accounting.survey_b_alg(8, 3)
+    step_hbm = {"b_alg_bytes_per_site": b_alg, "achieved_gbs": b_alg * V / (ms_step * 1e-3) / 1e9,
+                "peak_gbs": hbm_peak, "peak_kind": peak_kind,
+                "frac": b_alg * V / (ms_step * 1e-3) / 1e9 / hbm_peak,
+                "schedule_bytes_per_site": sum(byt.values())}
+
+    # ---- end to end through host buffers ----------------------------------
+    pinned = torch.from_numpy(U).pin_memory()
+    Ke = min(args.steps, 20)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(Ke):
+        lat.set_links(pinned)
+        lat.step(ALPHA)
+        lat.measure()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": world * Ke / e2e_s, "unit": "iters/s", "h2d_bytes_per_step": int(U.nbytes),
+           "d2h_bytes_per_step": 16,
+           "note": "per step: lgf_set_links from pinned host memory (H2D copy, SU(3) check, layout conversion, "
+                   "measurement), lgf_step, lgf_measure (D2H of F and theta)"}
+    lat.close()
+    del pinned
+
+    # ---- FP32 12-real rate --------------------------------------------------
+    lat32 = lgf.Lattice(EXT, "fp32", store12=True)
+    lat32.set_links(U)
+    for _ in range(args.warmup):
+        lat32.step(ALPHA)
+    lat32.set_timing(True)
+    ms32 = time_steps(torch, lat32, args.steps)
+    kms32, _ = lat32.get_timing()
+    lat32.close()
+    b32 = accounting.bytes_per_site(4, 2, 2, k_bytes=4)
+    ops32 = accounting.fp32_path_fp64_ops_per_site()
+    fp32 = {"iters_per_s": args.steps / (ms32 / 1e3), "ms_per_step": ms32 / args.steps,
+            "per_kernel": {k: {"ms": t, "gbs": b32[k] * V / (t * 1e-3) / 1e9 if t > 0 else None,
+                               "fp64_tflops": 2 * ops32[k] * V / (t * 1e-3) / 1e12 if t > 0 else None}
+                           for k, t in zip(accounting.KERNELS, kms32)},
+            "hbm_frac_b_alg": accounting.survey_b_alg(4, 2) * V / (ms32 / args.steps * 1e-3) / 1e9 / hbm_peak}
+
+    # ---- time to theta < 1e-15: plain FP64 vs mixed -------------------------
+    ttt = None
+    if not args.no_tol:
+        ttt = {"tol": TOL, "field": f"32^4 eps={EPS} seed={rank}"}
+        for mode, kw in (("fp64_18", dict(precision="fp64")), ("mixed_12", dict(precision="mixed", store12=True))):
+            L2 = lgf.Lattice(EXT, **kw)
+            L2.set_links(U)
+            L2.fix(TOL, 1, ALPHA)           # builds the loop graph
+            L2.set_links(U)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            it, F, th, conv = L2.fix(TOL, args.max_iter, ALPHA)
+            torch.cuda.synchronize()
+            ttt[mode] = {"seconds": time.perf_counter() - t0, "iters": it, "F": F, "theta": th, "converged": conv}
+            L2.close()
+        ttt["speedup_mixed"] = ttt["fp64_18"]["seconds"] / ttt["mixed_12"]["seconds"]
+
+    # ---- CPU oracle on the host cores (rank 0, N = 1 only) ------------------
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        dt, cores, _ = oracle_iterations(U, args.cpu_iters)
+        cpu = {"value": args.cpu_iters / dt, "unit": "iters/s", "cores": cores, "kind": "oracle",
+               "sample": f"{args.cpu_iters} oracle bodies of Algorithm 1 on the same 32^4 field (numpy FP64)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_desc(), "lattice": list(EXT), "precision": "fp64",
+                       "storage": "18-real", "alpha": ALPHA, "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "no flush needed: each step streams 604 MB of links (> 129 MB L2)"},
+            "site_updates_per_s": value * V,
+            "per_kernel": per_kernel, "roofline": roofline, "step_hbm": step_hbm, "fp32_12": fp32,
+            "time_to_tol": ttt, "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
+            "gpu_launches": 5 * args.steps,
+            "paper_context": {"c2070_dp_ms_per_iter_12real_tex": 61.16, "c2070_dp_ms_per_iter_18real_tex": 100.65,
+                              "note": "derived from the paper's Table 2 (real beta=5.8-6.2 configurations)"},
+        }
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="lgf", choices=["lgf", "reference"])
+    ap.add_argument("--max-iter", type=int, default=20000)
+    ap.add_argument("--cpu-iters", type=int, default=3)
+    ap.add_argument("--no-tol", action="store_true", help="skip the time-to-threshold runs")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        # the CPU oracle runs on rank 0 only; other ranks exit without work
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(local_rank)
+        tdist.init_process_group("nccl")
+    try:
+        run_lgf(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as tdist
+            tdist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

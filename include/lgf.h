@@ -157,6 +157,19 @@ lgf_status lgf_set_trace(lgf_handle h, double* F_hist, double* theta_hist, int32
  * against the defining sum.  Synchronises. */
 lgf_status lgf_fft4(lgf_handle h, double* data, int32_t nfields, int32_t sign, int where);
 
+/* Per-kernel timing of lgf_step.  enable != 0 starts recording CUDA events
+ * on the handle's stream around each of the five kernels of every
+ * subsequent lgf_step (not inside lgf_fix's graph) and clears the
+ * accumulators; enable = 0 stops.  Synchronises. */
+lgf_status lgf_set_timing(lgf_handle h, int32_t enable);
+
+/* Mean device time in milliseconds of each kernel of the lgf_step calls
+ * since timing was enabled: ms[0] pass A (forward (x,y) DFT), ms[1] pass B
+ * ((z,t) DFT, filter, inverse), ms[2] pass C (inverse (x,y) DFT and g),
+ * ms[3] link update, ms[4] measurement; nkernels <= 5 entries are written.
+ * nsteps (may be NULL) receives the number of steps averaged.  Synchronises. */
+lgf_status lgf_get_timing(lgf_handle h, double* ms, int32_t nkernels, int32_t* nsteps);
+
 /* Phase of an LGF_MIXED handle: 32 while in the FP32 phase, 64 after the
  * switch (FP64 and FP32 handles report their fixed precision). */
 lgf_status lgf_get_phase(lgf_handle h, int32_t* bits);

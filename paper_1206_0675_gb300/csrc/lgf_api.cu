@@ -38,6 +38,17 @@ template <typename R> struct Lane {
   bool active = false;
 };
 
+// Per-kernel CUDA-event timing of lgf_step (ring of in-flight steps).
+struct TimingRing {
+  static constexpr int kSlots = 64, kEv = 6;  // events bracket the 5 kernels of one step
+  cudaEvent_t ev[kSlots][kEv] = {};
+  bool pending[kSlots] = {};
+  int next = 0;
+  double sum_ms[kEv - 1] = {};
+  long steps = 0;
+  bool enabled = false;
+};
+
 }  // namespace
 
 struct lgf_ctx {
@@ -69,6 +80,7 @@ struct lgf_ctx {
   int hist_cap = 0;
   double* user_F = nullptr;
   double* user_T = nullptr;
+  TimingRing timing;
 };
 
 namespace {
@@ -161,36 +173,73 @@ template <typename R> cudaError_t enqueue_measure(lgf_ctx* h, Lane<R>& L, int co
 // Gauge-transform step of a lane given the divergence in L.D (from the last
 // measurement), followed by the next measurement: FFT passes A, B, C(+g),
 // update, measure.
-template <typename R> cudaError_t enqueue_body(lgf_ctx* h, Lane<R>& L, unsigned long long cond, int use_cond,
-                                                cudaStream_t s);
+// Kernel k of the body: 0 pass A, 1 pass B, 2 pass C (+g), 3 update, 4 measure.
+template <typename R> cudaError_t enqueue_kernel(lgf_ctx* h, Lane<R>& L, int k, unsigned long long cond,
+                                                  int use_cond, cudaStream_t s);
 
-template <> cudaError_t enqueue_body<double>(lgf_ctx* h, Lane<double>& L, unsigned long long cond, int use_cond,
-                                             cudaStream_t s) {
+template <> cudaError_t enqueue_kernel<double>(lgf_ctx* h, Lane<double>& L, int k, unsigned long long cond,
+                                               int use_cond, cudaStream_t s) {
   const Geom& g = h->geom;
-  cudaError_t e;
-  if ((e = launch_fft_xy<double>(g, L.plan, L.D, L.tw, L.pos, -1, 4, s)) != cudaSuccess) return e;
-  if ((e = launch_fft_zt<double>(g, L.plan, L.D, L.tw, L.pos, L.K, 0, 4, s)) != cudaSuccess) return e;
-  if ((e = launch_fft_xy_inv_gauge<double, double, 3>(g, L.plan, L.D, L.tw, L.pos, L.g, L.G, s)) != cudaSuccess) return e;
-  if (L.rows == 3) e = launch_update<double, 3, 3>(g, L.U, L.g, s);
-  else e = launch_update<double, 2, 3>(g, L.U, L.g, s);
-  if (e != cudaSuccess) return e;
-  return enqueue_measure<double>(h, L, 1, cond, use_cond, s);
+  switch (k) {
+    case 0: return launch_fft_xy<double>(g, L.plan, L.D, L.tw, L.pos, -1, 4, s);
+    case 1: return launch_fft_zt<double>(g, L.plan, L.D, L.tw, L.pos, L.K, 0, 4, s);
+    case 2: return launch_fft_xy_inv_gauge<double, double, 3>(g, L.plan, L.D, L.tw, L.pos, L.g, L.G, s);
+    case 3: return L.rows == 3 ? launch_update<double, 3, 3>(g, L.U, L.g, s) : launch_update<double, 2, 3>(g, L.U, L.g, s);
+    default: return enqueue_measure<double>(h, L, 1, cond, use_cond, s);
+  }
 }
 
-template <> cudaError_t enqueue_body<float>(lgf_ctx* h, Lane<float>& L, unsigned long long cond, int use_cond,
-                                            cudaStream_t s) {
+template <> cudaError_t enqueue_kernel<float>(lgf_ctx* h, Lane<float>& L, int k, unsigned long long cond,
+                                              int use_cond, cudaStream_t s) {
   const Geom& g = h->geom;
-  cudaError_t e;
-  if ((e = launch_fft_xy<float>(g, L.plan, L.D, L.tw, L.pos, -1, 4, s)) != cudaSuccess) return e;
-  if ((e = launch_fft_zt<float>(g, L.plan, L.D, L.tw, L.pos, L.K, 0, 4, s)) != cudaSuccess) return e;
-  if (L.grows == 2) {
-    if ((e = launch_fft_xy_inv_gauge<float, float, 2>(g, L.plan, L.D, L.tw, L.pos, L.g, L.G, s)) != cudaSuccess) return e;
-    if ((e = launch_update<float, 2, 2>(g, L.U, L.g, s)) != cudaSuccess) return e;
-  } else {
-    if ((e = launch_fft_xy_inv_gauge<float, float, 3>(g, L.plan, L.D, L.tw, L.pos, L.g, L.G, s)) != cudaSuccess) return e;
-    if ((e = launch_update<float, 3, 3>(g, L.U, L.g, s)) != cudaSuccess) return e;
+  switch (k) {
+    case 0: return launch_fft_xy<float>(g, L.plan, L.D, L.tw, L.pos, -1, 4, s);
+    case 1: return launch_fft_zt<float>(g, L.plan, L.D, L.tw, L.pos, L.K, 0, 4, s);
+    case 2:
+      return L.grows == 2 ? launch_fft_xy_inv_gauge<float, float, 2>(g, L.plan, L.D, L.tw, L.pos, L.g, L.G, s)
+                          : launch_fft_xy_inv_gauge<float, float, 3>(g, L.plan, L.D, L.tw, L.pos, L.g, L.G, s);
+    case 3: return L.grows == 2 ? launch_update<float, 2, 2>(g, L.U, L.g, s) : launch_update<float, 3, 3>(g, L.U, L.g, s);
+    default: return enqueue_measure<float>(h, L, 1, cond, use_cond, s);
   }
-  return enqueue_measure<float>(h, L, 1, cond, use_cond, s);
+}
+
+cudaError_t timing_collect(TimingRing& T, int slot) {
+  if (!T.pending[slot]) return cudaSuccess;
+  cudaError_t e = cudaEventSynchronize(T.ev[slot][TimingRing::kEv - 1]);
+  if (e != cudaSuccess) return e;
+  for (int k = 0; k < TimingRing::kEv - 1; ++k) {
+    float ms = 0.f;
+    e = cudaEventElapsedTime(&ms, T.ev[slot][k], T.ev[slot][k + 1]);
+    if (e != cudaSuccess) return e;
+    T.sum_ms[k] += ms;
+  }
+  T.steps += 1;
+  T.pending[slot] = false;
+  return cudaSuccess;
+}
+
+// Gauge-transform step of a lane given the divergence in L.D (from the last
+// measurement), followed by the next measurement: FFT passes A, B, C(+g),
+// update, measure.  With timing enabled (and outside graph capture) every
+// kernel is bracketed by CUDA events on the launching stream.
+template <typename R> cudaError_t enqueue_body(lgf_ctx* h, Lane<R>& L, unsigned long long cond, int use_cond,
+                                                cudaStream_t s) {
+  TimingRing& T = h->timing;
+  const bool timed = T.enabled && !use_cond;
+  int slot = 0;
+  cudaError_t e;
+  if (timed) {
+    slot = T.next;
+    T.next = (T.next + 1) % TimingRing::kSlots;
+    if ((e = timing_collect(T, slot)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(T.ev[slot][0], s)) != cudaSuccess) return e;
+  }
+  for (int k = 0; k < 5; ++k) {
+    if ((e = enqueue_kernel<R>(h, L, k, cond, use_cond, s)) != cudaSuccess) return e;
+    if (timed && (e = cudaEventRecord(T.ev[slot][k + 1], s)) != cudaSuccess) return e;
+  }
+  if (timed) T.pending[slot] = true;
+  return cudaSuccess;
 }
 
 // Build (once) the graph  WHILE(cond) { body }  for a lane.
@@ -320,6 +369,9 @@ lgf_status lgf_destroy(lgf_handle h) {
   if (h->st_host) cudaFreeHost(h->st_host);
   if (h->defect_host) cudaFreeHost(h->defect_host);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  for (int i = 0; i < TimingRing::kSlots; ++i)
+    for (int k = 0; k < TimingRing::kEv; ++k)
+      if (h->timing.ev[i][k]) cudaEventDestroy(h->timing.ev[i][k]);
   delete h;
   return LGF_OK;
 }
@@ -645,6 +697,35 @@ lgf_status lgf_fft4(lgf_handle h, double* data, int32_t nfields, int32_t sign, i
     s = sync_state(h);
   }
   return s;
+}
+
+lgf_status lgf_set_timing(lgf_handle h, int32_t enable) {
+  lgf_status s = check_handle(h);
+  if (s != LGF_OK) return s;
+  TimingRing& T = h->timing;
+  LGF_CK(h, cudaStreamSynchronize(h->stream));
+  if (enable && !T.ev[0][0]) {
+    for (int i = 0; i < TimingRing::kSlots; ++i)
+      for (int k = 0; k < TimingRing::kEv; ++k) LGF_CK(h, cudaEventCreate(&T.ev[i][k]));
+  }
+  for (int i = 0; i < TimingRing::kSlots; ++i) T.pending[i] = false;
+  for (int k = 0; k < TimingRing::kEv - 1; ++k) T.sum_ms[k] = 0.0;
+  T.steps = 0;
+  T.next = 0;
+  T.enabled = enable != 0;
+  return LGF_OK;
+}
+
+lgf_status lgf_get_timing(lgf_handle h, double* ms, int32_t nkernels, int32_t* nsteps) {
+  lgf_status s = check_handle(h);
+  if (s != LGF_OK) return s;
+  if (!ms || nkernels < 1 || nkernels > 5) return fail(h, LGF_E_ARG, "bad timing arguments");
+  TimingRing& T = h->timing;
+  LGF_CK(h, cudaStreamSynchronize(h->stream));
+  for (int i = 0; i < TimingRing::kSlots; ++i) LGF_CK(h, timing_collect(T, i));
+  for (int k = 0; k < nkernels; ++k) ms[k] = T.steps ? T.sum_ms[k] / (double)T.steps : 0.0;
+  if (nsteps) *nsteps = (int32_t)T.steps;
+  return LGF_OK;
 }
 
 lgf_status lgf_get_phase(lgf_handle h, int32_t* bits) {

@@ -52,6 +52,8 @@ SIGNATURES = [
     ("lgf_set_trace", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
     ("lgf_fft4", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int]),
     ("lgf_get_phase", ctypes.c_int, [ctypes.c_void_p, _c_int_p]),
+    ("lgf_set_timing", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    ("lgf_get_timing", ctypes.c_int, [ctypes.c_void_p, _c_dbl_p, ctypes.c_int32, _c_int_p]),
     ("lgf_status_string", ctypes.c_char_p, [ctypes.c_int]),
     ("lgf_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
 ]
@@ -166,6 +168,17 @@ def lgf_get_phase(h: int) -> int:
     return b.value
 
 
+def lgf_set_timing(h: int, enable: bool) -> None:
+    _check(h, load_library().lgf_set_timing(ctypes.c_void_p(h), 1 if enable else 0), "lgf_set_timing")
+
+
+def lgf_get_timing(h: int) -> tuple[list[float], int]:
+    ms = (ctypes.c_double * 5)()
+    n = ctypes.c_int32()
+    _check(h, load_library().lgf_get_timing(ctypes.c_void_p(h), ms, 5, ctypes.byref(n)), "lgf_get_timing")
+    return list(ms), n.value
+
+
 # --- marshalling helpers ----------------------------------------------------
 
 _PREC = {"fp64": LGF_FP64, "fp32": LGF_FP32, "mixed": LGF_MIXED}
@@ -180,6 +193,17 @@ def _host_buffer(arr: np.ndarray, shape) -> np.ndarray:
 
 def _is_torch_cuda(x) -> bool:
     return type(x).__module__.startswith("torch") and getattr(x, "is_cuda", False)
+
+
+def _is_torch_cpu(x) -> bool:
+    return type(x).__module__.startswith("torch") and not getattr(x, "is_cuda", True)
+
+
+def _torch_host_ptr(t, nbytes: int) -> int:
+    """Pointer of a contiguous CPU torch tensor (e.g. pinned) holding nbytes of FP64 data."""
+    if not t.is_contiguous() or t.numel() * t.element_size() != nbytes:
+        raise ValueError(f"host tensor must be contiguous with {nbytes} bytes")
+    return t.data_ptr()
 
 
 class Lattice:
@@ -225,6 +249,9 @@ class Lattice:
             if not U.is_contiguous():
                 raise ValueError("device links must be contiguous")
             lgf_set_links(self.handle, U.data_ptr(), LGF_DEVICE)
+        elif _is_torch_cpu(U):
+            nbytes = 16 * int(np.prod(self.link_shape))
+            lgf_set_links(self.handle, _torch_host_ptr(U, nbytes), LGF_HOST)
         else:
             a = _host_buffer(U, self.link_shape)
             lgf_set_links(self.handle, a.ctypes.data, LGF_HOST)
@@ -284,6 +311,13 @@ class Lattice:
         a = _host_buffer(data, (4, lt, lz, ly, lx)).copy()
         lgf_fft4(self.handle, a.ctypes.data, 4, sign, LGF_HOST)
         return a
+
+    def set_timing(self, enable: bool = True) -> None:
+        lgf_set_timing(self.handle, enable)
+
+    def get_timing(self) -> tuple[list[float], int]:
+        """Mean ms per kernel [pass A, pass B, pass C+g, update, measure] and the step count."""
+        return lgf_get_timing(self.handle)
 
     @property
     def phase(self) -> int:
