@@ -174,6 +174,36 @@ lgf_status lgf_get_timing(lgf_handle h, double* ms, int32_t nkernels, int32_t* n
  * switch (FP64 and FP32 handles report their fixed precision). */
 lgf_status lgf_get_phase(lgf_handle h, int32_t* bits);
 
+/* Largest lattice (sites) lgf_measure_static accepts. */
+#define LGF_STATIC_MAX_SITES 16777216
+
+/* Measurement of Delta_A, F and theta that allocates nothing.  The paper has
+ * no counterpart: this exists for callers that must not allocate device
+ * memory where they measure -- e.g. a host application whose device memory
+ * is owned entirely by its own pool allocator, or monitoring code between
+ * the steps of a time-critical loop, where cudaMalloc/cudaFree could fail or
+ * synchronise the device.  The computation is the one lgf_measure and
+ * lgf_get_divergence perform, without a handle.
+ * extents: {Lx, Ly, Lz, Lt}, each 2^a 3^b in [2, 128], and at most
+ *   LGF_STATIC_MAX_SITES sites in total (else LGF_E_UNSUPPORTED; nothing is
+ *   launched).
+ * U: device pointer, FP64 links in the user layout (4*V*18 doubles, read only).
+ * D: device pointer to V*18 doubles receiving Delta_A in the site layout, or
+ *   NULL to skip it.
+ * F_theta: device pointer to 2 doubles receiving F and theta.
+ * cuda_stream: a cudaStream_t or NULL; the work is enqueued there and the
+ *   call returns without synchronising.
+ * Scratch: a fixed 1 MB device array inside the library (one per device,
+ *   held until the process exits) that every call on a device shares.  Calls
+ *   whose kernels may overlap on the GPU (other streams, other host threads)
+ *   race on it and must be serialised by the caller.  The first call on each
+ *   device looks up the array's device address, so make that first call
+ *   before any stream capture begins.  No cudaMalloc, cudaFree or other
+ *   allocating routine is called.
+ * Returns LGF_OK, LGF_E_ARG (NULL pointers), LGF_E_UNSUPPORTED or LGF_E_CUDA. */
+lgf_status lgf_measure_static(const int32_t extents[4], const double* U, double* D, double* F_theta,
+                              void* cuda_stream);
+
 /* Human-readable name of a status code (static string). */
 const char* lgf_status_string(lgf_status s);
 

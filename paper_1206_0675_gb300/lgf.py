@@ -54,6 +54,8 @@ SIGNATURES = [
     ("lgf_get_phase", ctypes.c_int, [ctypes.c_void_p, _c_int_p]),
     ("lgf_set_timing", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     ("lgf_get_timing", ctypes.c_int, [ctypes.c_void_p, _c_dbl_p, ctypes.c_int32, _c_int_p]),
+    ("lgf_measure_static", ctypes.c_int, [ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_void_p]),
     ("lgf_status_string", ctypes.c_char_p, [ctypes.c_int]),
     ("lgf_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
 ]
@@ -177,6 +179,16 @@ def lgf_get_timing(h: int) -> tuple[list[float], int]:
     n = ctypes.c_int32()
     _check(h, load_library().lgf_get_timing(ctypes.c_void_p(h), ms, 5, ctypes.byref(n)), "lgf_get_timing")
     return list(ms), n.value
+
+
+LGF_STATIC_MAX_SITES = 16777216
+
+
+def lgf_measure_static(extents, u_ptr: int, d_ptr: int, f_theta_ptr: int, stream: int = 0) -> int:
+    """Allocation-free measurement (device pointers only); returns the lgf_status code."""
+    ext = (ctypes.c_int32 * 4)(*[int(e) for e in extents])
+    return load_library().lgf_measure_static(ext, ctypes.c_void_p(u_ptr or None), ctypes.c_void_p(d_ptr or None),
+                                             ctypes.c_void_p(f_theta_ptr or None), ctypes.c_void_p(stream or None))
 
 
 # --- marshalling helpers ----------------------------------------------------
