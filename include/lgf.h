@@ -77,6 +77,7 @@ enum {
   LGF_STORE18 = 0,        /* keep all three rows of each link (18 reals) */
   LGF_STORE12 = 1 << 0,   /* keep rows 1-2 (12 reals), rebuild row 3 = (a x b)^* (Sec. 3.2) */
   LGF_TRACK_G = 1 << 1,   /* accumulate G(x) = g_k(x)...g_1(x) for lgf_get_transform */
+  LGF_LEARNED = 1 << 2,   /* multiply the filter by the learned per-mode multiplier (lgf_load_preconditioner) */
   LGF_PLAIN_SD = 1 << 3   /* plain steepest descent: filter K(k) = alpha (no Fourier acceleration) */
 };
 
@@ -110,8 +111,10 @@ lgf_status lgf_get_links(lgf_handle h, double* U, int where);
 
 /* One body of Algorithm 1: 4D FFT of Delta, filter K(k) (alpha given here),
  * inverse FFT, g = reunitarize(1 + Delta'), U -> g U g^dag(x+mu), then the
- * measurement of Delta, F and theta.  Asynchronous (enqueued on the stream).
- * In LGF_MIXED mode the step runs in the phase the handle is in. */
+ * measurement of Delta, F and theta.  Asynchronous (enqueued on the stream),
+ * except with LGF_LEARNED, where it synchronises to redo a rejected step
+ * with the plain filter.  In LGF_MIXED mode the step runs in the phase the
+ * handle is in. */
 lgf_status lgf_step(lgf_handle h, double alpha);
 
 /* F and theta of the current links (Sec. 2, eq. 3 and the theta formula).
@@ -169,6 +172,71 @@ lgf_status lgf_set_timing(lgf_handle h, int32_t enable);
  * ms[3] link update, ms[4] measurement; nkernels <= 5 entries are written.
  * nsteps (may be NULL) receives the number of steps averaged.  Synchronises. */
 lgf_status lgf_get_timing(lgf_handle h, double* ms, int32_t nkernels, int32_t* nsteps);
+/* (ms[5], with nkernels = 6: the learned extras -- undo of a rejected step,
+ * its re-measurement and the network inference -- of LGF_LEARNED handles.) */
+
+/* ---- learned per-mode multiplier (an addition; the paper has no learned part) ----
+ *
+ * With LGF_LEARNED every step multiplies the filter by m(k) in [0.25, 1.25],
+ * predicted for each momentum class (modes with the same per-direction
+ * p2_mu = 4 sin^2(pi k_mu / L_mu)) by a network 6 -> 64 -> 64 -> 64 -> 1
+ * (ReLU hidden layers, m = softplus(z)) with BF16 weights and FP32
+ * accumulation on the tensor cores.  Features of a mode:
+ *   (p2_x/4, p2_y/4, p2_z/4, p2_t/4, -floor(2 log10 theta)/32, min(iter/10000, 1))
+ * where theta and iter are those of the links the step starts from.  A step
+ * that lowers F is undone and redone with the plain filter; theta (of the
+ * plain definition) decides convergence.
+ *
+ * Parameter layout (8833 numbers, rows [out][in]):
+ *   W1[64][6] @0, b1[64] @384, W2[64][64] @448, b2[64] @4544,
+ *   W3[64][64] @4608, b3[64] @8704, w4[64] @8768, b4 @8832. */
+#define LGF_MLP_NPARAM 8833
+
+/* Load BF16 network parameters (n_w must be LGF_MLP_NPARAM) into the
+ * handle; where = LGF_HOST or LGF_DEVICE.  Synchronises. */
+lgf_status lgf_load_preconditioner(lgf_handle h, const uint16_t* bf16_w, size_t n_w, int where);
+
+/* Number of learned steps that were rejected (F did not increase) and redone
+ * with the plain filter during the last lgf_fix. */
+lgf_status lgf_get_fallbacks(lgf_handle h, int32_t* n);
+
+/* Mode log (training data).  enable != 0 makes every subsequent lgf_step
+ * also accumulate, for each theta bucket b and momentum class c, the sums
+ *   Re<D^_{k+1}, D^_k>, |D^_k|^2, count, iteration fraction of step k
+ * over the modes of the class, D^ being the 4D Fourier transform of the
+ * packed divergence (b = clamp(4 - 2 floor(2 log10 theta_k)/2, 0, 39)).
+ * Enabling clears the sums.  Synchronises. */
+lgf_status lgf_set_mode_log(lgf_handle h, int32_t enable);
+
+/* Copy the mode-log sums out: n must be 40 * nclass * 4 doubles, laid out
+ * [b][c][4] with nclass = prod_mu (L_mu/2 + 1) and
+ * c = ((f_t H_z + f_z) H_y + f_y) H_x + f_x, f_mu = min(k_mu, L_mu - k_mu),
+ * H_mu = L_mu/2 + 1.  out is a host pointer.  Synchronises. */
+lgf_status lgf_get_mode_log(lgf_handle h, double* out, int64_t n);
+
+/* Network inference on the tensor cores for arbitrary feature rows
+ * (device pointers): X[n][6] FP32 features, P[8833] BF16 parameters,
+ * m[n] = softplus(z) FP32 out (unclamped).  Enqueued on cuda_stream. */
+lgf_status lgf_mlp_eval(const uint16_t* P, const float* X, int64_t n, float* m, void* cuda_stream);
+
+/* Loss L = (1/n) sum_i w_i (log m_i - y_i)^2 over all rows and its gradient
+ * with respect to the FP32 parameters (device pointers: P[8833], X[n][6],
+ * Y[n], W[n], grad[8833]); *loss on the host.  Synchronises. */
+lgf_status lgf_mlp_loss_grad(const float* P, const float* X, const float* Y, const float* W, int64_t n, float* grad,
+                             double* loss, void* cuda_stream);
+
+/* Adam training of the FP32 parameters P (device, in place) on minibatches of
+ * `batch` rows drawn by a counter-based hash of (seed, step, row): `steps`
+ * updates with learning rate lr, moments in adam[2 * 8833] (device, zero for
+ * a fresh start), t0 = number of updates done before (bias correction).
+ * loss_hist (host, may be NULL) receives the minibatch loss of every
+ * update.  Synchronises. */
+lgf_status lgf_mlp_train(float* P, float* adam, const float* X, const float* Y, const float* W, int64_t n,
+                         int32_t batch, int32_t steps, float lr, uint64_t seed, int32_t t0, double* loss_hist,
+                         void* cuda_stream);
+
+/* FP32 -> BF16 (round to nearest even) of the 8833 parameters (device). */
+lgf_status lgf_mlp_to_bf16(const float* P, uint16_t* out, void* cuda_stream);
 
 /* Phase of an LGF_MIXED handle: 32 while in the FP32 phase, 64 after the
  * switch (FP64 and FP32 handles report their fixed precision). */

@@ -12,6 +12,7 @@
 
 #include "../../include/lgf.h"
 #include "lgf_internal.h"
+#include "lgf_mlp.h"
 
 using namespace lgf;
 
@@ -36,15 +37,25 @@ template <typename R> struct Lane {
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
   bool active = false;
+  // learned multiplier and mode log
+  float* mtab = nullptr;   // multiplier per momentum class
+  float* p2f = nullptr;    // per-direction p2 tables for the network features
+  MlpGeom mg{};
+  C2<R>* Dlog = nullptr;   // Fourier-space divergence of the current / previous step (mode log)
+  C2<R>* Dprev = nullptr;
 };
 
 // Per-kernel CUDA-event timing of lgf_step (ring of in-flight steps).
+// Categories: 0 pass A, 1 pass B, 2 pass C, 3 update, 4 measure, 5 learned
+// extras (undo of a rejected step, its re-measurement, network inference).
 struct TimingRing {
-  static constexpr int kSlots = 64, kEv = 6;  // events bracket the 5 kernels of one step
-  cudaEvent_t ev[kSlots][kEv] = {};
+  static constexpr int kSlots = 64, kMaxK = 8, kCat = 6;
+  cudaEvent_t ev[kSlots][kMaxK + 1] = {};
+  int cat[kSlots][kMaxK] = {};
+  int nk[kSlots] = {};
   bool pending[kSlots] = {};
   int next = 0;
-  double sum_ms[kEv - 1] = {};
+  double sum_ms[kCat] = {};
   long steps = 0;
   bool enabled = false;
 };
@@ -81,6 +92,12 @@ struct lgf_ctx {
   double* user_F = nullptr;
   double* user_T = nullptr;
   TimingRing timing;
+  bool learned = false;           // LGF_LEARNED
+  uint16_t* mlp_w = nullptr;      // BF16 network parameters (device)
+  bool logging = false;           // per-mode statistics of every lgf_step
+  bool log_primed = false;
+  LogState* ls = nullptr;
+  double* stats = nullptr;        // [MLP_NBUCKET][nclass][4]
 };
 
 namespace {
@@ -117,6 +134,7 @@ template <typename R> void free_lane(Lane<R>& L) {
   if (L.exec) cudaGraphExecDestroy(L.exec);
   if (L.graph) cudaGraphDestroy(L.graph);
   cudaFree(L.U); cudaFree(L.g); cudaFree(L.D); cudaFree(L.K); cudaFree(L.tw); cudaFree(L.pos); cudaFree(L.G);
+  cudaFree(L.mtab); cudaFree(L.p2f); cudaFree(L.Dlog); cudaFree(L.Dprev);
   L = Lane<R>();
 }
 
@@ -149,6 +167,24 @@ template <typename R> lgf_status alloc_lane(lgf_ctx* h, Lane<R>& L, int rows, in
   fft_positions(L.plan, pos.data());
   LGF_CK(h, dalloc(&L.pos, (size_t)nt));
   LGF_CK(h, cudaMemcpy(L.pos, pos.data(), nt * sizeof(short), cudaMemcpyHostToDevice));
+  // momentum classes and their per-direction p2 = 4 sin^2(pi f / L), f <= L/2
+  std::vector<float> p2;
+  L.mg.nclass = 1;
+  for (int mu = 0; mu < 4; ++mu) {
+    const int N = h->geom.L[mu];
+    L.mg.H[mu] = N / 2 + 1;
+    L.mg.off[mu] = (int)p2.size();
+    L.mg.nclass *= L.mg.H[mu];
+    for (int f = 0; f <= N / 2; ++f) {
+      const double sv = std::sin(M_PI * (double)f / (double)N);
+      p2.push_back((float)(4.0 * sv * sv));
+    }
+  }
+  L.mg.m_lo = 0.25f;
+  L.mg.m_hi = 1.25f;
+  LGF_CK(h, dalloc(&L.p2f, p2.size()));
+  LGF_CK(h, cudaMemcpy(L.p2f, p2.data(), p2.size() * sizeof(float), cudaMemcpyHostToDevice));
+  if (h->learned) LGF_CK(h, dalloc(&L.mtab, (size_t)L.mg.nclass));
   L.active = true;
   return LGF_OK;
 }
@@ -164,16 +200,40 @@ template <typename R> lgf_status ensure_filter(lgf_ctx* h, Lane<R>& L, double al
 
 // Measurement of the current links of a lane.
 template <typename R> cudaError_t enqueue_measure(lgf_ctx* h, Lane<R>& L, int count_iter,
-                                                   unsigned long long cond, int use_cond, cudaStream_t s) {
+                                                   unsigned long long cond, int use_cond, cudaStream_t s,
+                                                   int only_if_revert = 0) {
   if (L.rows == 3)
-    return launch_measure<R, 3>(h->geom, L.U, L.D, h->partials, h->st, count_iter, cond, use_cond, s);
-  return launch_measure<R, 2>(h->geom, L.U, L.D, h->partials, h->st, count_iter, cond, use_cond, s);
+    return launch_measure<R, 3>(h->geom, L.U, L.D, h->partials, h->st, count_iter, cond, use_cond, s,
+                                only_if_revert);
+  return launch_measure<R, 2>(h->geom, L.U, L.D, h->partials, h->st, count_iter, cond, use_cond, s, only_if_revert);
 }
 
 // Gauge-transform step of a lane given the divergence in L.D (from the last
 // measurement), followed by the next measurement: FFT passes A, B, C(+g),
 // update, measure.
-// Kernel k of the body: 0 pass A, 1 pass B, 2 pass C (+g), 3 update, 4 measure.
+// The kernels of one body, in order, with their timing category.  Plain:
+// pass A, pass B, pass C (+g), update, measure.  Learned: undo of a rejected
+// step, its re-measurement and the network inference come first (each does
+// nothing unless it has work), then the plain sequence with the multiplier.
+enum { K_A = 0, K_B, K_C, K_UPD, K_MEAS, K_REVERT, K_RESTORE, K_MLP };
+
+template <typename R> int body_kernels(const lgf_ctx* h, int* ks) {
+  int n = 0;
+  if (h->learned) {
+    ks[n++] = K_REVERT;
+    ks[n++] = K_RESTORE;
+    ks[n++] = K_MLP;
+  }
+  ks[n++] = K_A;
+  ks[n++] = K_B;
+  ks[n++] = K_C;
+  ks[n++] = K_UPD;
+  ks[n++] = K_MEAS;
+  return n;
+}
+
+inline int kernel_category(int k) { return k <= K_MEAS ? k : 5; }
+
 template <typename R> cudaError_t enqueue_kernel(lgf_ctx* h, Lane<R>& L, int k, unsigned long long cond,
                                                   int use_cond, cudaStream_t s);
 
@@ -181,11 +241,17 @@ template <> cudaError_t enqueue_kernel<double>(lgf_ctx* h, Lane<double>& L, int 
                                                int use_cond, cudaStream_t s) {
   const Geom& g = h->geom;
   switch (k) {
-    case 0: return launch_fft_xy<double>(g, L.plan, L.D, L.tw, L.pos, -1, 4, s);
-    case 1: return launch_fft_zt<double>(g, L.plan, L.D, L.tw, L.pos, L.K, 0, 4, s);
-    case 2: return launch_fft_xy_inv_gauge<double, double, 3>(g, L.plan, L.D, L.tw, L.pos, L.g, L.G, s);
-    case 3: return L.rows == 3 ? launch_update<double, 3, 3>(g, L.U, L.g, s) : launch_update<double, 2, 3>(g, L.U, L.g, s);
-    default: return enqueue_measure<double>(h, L, 1, cond, use_cond, s);
+    case K_A: return launch_fft_xy<double>(g, L.plan, L.D, L.tw, L.pos, -1, 4, s);
+    case K_B: return launch_fft_zt<double>(g, L.plan, L.D, L.tw, L.pos, L.K, 0, 4, s, L.mtab, &h->st->use_m);
+    case K_C: return launch_fft_xy_inv_gauge<double, double, 3>(g, L.plan, L.D, L.tw, L.pos, L.g, L.G, s);
+    case K_UPD:
+      return L.rows == 3 ? launch_update<double, 3, 3>(g, L.U, L.g, s) : launch_update<double, 2, 3>(g, L.U, L.g, s);
+    case K_MEAS: return enqueue_measure<double>(h, L, 1, cond, use_cond, s);
+    case K_REVERT:
+      return L.rows == 3 ? launch_revert<double, 3, 3>(g, L.U, L.g, L.G, h->st, s)
+                         : launch_revert<double, 2, 3>(g, L.U, L.g, L.G, h->st, s);
+    case K_RESTORE: return enqueue_measure<double>(h, L, -1, 0, 0, s, 1);
+    default: return launch_mlp_multiplier(h->mlp_w, L.mg, L.p2f, h->st, L.mtab, s);
   }
 }
 
@@ -193,25 +259,30 @@ template <> cudaError_t enqueue_kernel<float>(lgf_ctx* h, Lane<float>& L, int k,
                                               int use_cond, cudaStream_t s) {
   const Geom& g = h->geom;
   switch (k) {
-    case 0: return launch_fft_xy<float>(g, L.plan, L.D, L.tw, L.pos, -1, 4, s);
-    case 1: return launch_fft_zt<float>(g, L.plan, L.D, L.tw, L.pos, L.K, 0, 4, s);
-    case 2:
+    case K_A: return launch_fft_xy<float>(g, L.plan, L.D, L.tw, L.pos, -1, 4, s);
+    case K_B: return launch_fft_zt<float>(g, L.plan, L.D, L.tw, L.pos, L.K, 0, 4, s, L.mtab, &h->st->use_m);
+    case K_C:
       return L.grows == 2 ? launch_fft_xy_inv_gauge<float, float, 2>(g, L.plan, L.D, L.tw, L.pos, L.g, L.G, s)
                           : launch_fft_xy_inv_gauge<float, float, 3>(g, L.plan, L.D, L.tw, L.pos, L.g, L.G, s);
-    case 3: return L.grows == 2 ? launch_update<float, 2, 2>(g, L.U, L.g, s) : launch_update<float, 3, 3>(g, L.U, L.g, s);
-    default: return enqueue_measure<float>(h, L, 1, cond, use_cond, s);
+    case K_UPD: return L.grows == 2 ? launch_update<float, 2, 2>(g, L.U, L.g, s) : launch_update<float, 3, 3>(g, L.U, L.g, s);
+    case K_MEAS: return enqueue_measure<float>(h, L, 1, cond, use_cond, s);
+    case K_REVERT:
+      return L.grows == 2 ? launch_revert<float, 2, 2>(g, L.U, L.g, L.G, h->st, s)
+                          : launch_revert<float, 3, 3>(g, L.U, L.g, L.G, h->st, s);
+    case K_RESTORE: return enqueue_measure<float>(h, L, -1, 0, 0, s, 1);
+    default: return launch_mlp_multiplier(h->mlp_w, L.mg, L.p2f, h->st, L.mtab, s);
   }
 }
 
 cudaError_t timing_collect(TimingRing& T, int slot) {
   if (!T.pending[slot]) return cudaSuccess;
-  cudaError_t e = cudaEventSynchronize(T.ev[slot][TimingRing::kEv - 1]);
+  cudaError_t e = cudaEventSynchronize(T.ev[slot][T.nk[slot]]);
   if (e != cudaSuccess) return e;
-  for (int k = 0; k < TimingRing::kEv - 1; ++k) {
+  for (int k = 0; k < T.nk[slot]; ++k) {
     float ms = 0.f;
     e = cudaEventElapsedTime(&ms, T.ev[slot][k], T.ev[slot][k + 1]);
     if (e != cudaSuccess) return e;
-    T.sum_ms[k] += ms;
+    T.sum_ms[T.cat[slot][k]] += ms;
   }
   T.steps += 1;
   T.pending[slot] = false;
@@ -234,11 +305,19 @@ template <typename R> cudaError_t enqueue_body(lgf_ctx* h, Lane<R>& L, unsigned 
     if ((e = timing_collect(T, slot)) != cudaSuccess) return e;
     if ((e = cudaEventRecord(T.ev[slot][0], s)) != cudaSuccess) return e;
   }
-  for (int k = 0; k < 5; ++k) {
-    if ((e = enqueue_kernel<R>(h, L, k, cond, use_cond, s)) != cudaSuccess) return e;
-    if (timed && (e = cudaEventRecord(T.ev[slot][k + 1], s)) != cudaSuccess) return e;
+  int ks[TimingRing::kMaxK];
+  const int nk = body_kernels<R>(h, ks);
+  for (int i = 0; i < nk; ++i) {
+    if ((e = enqueue_kernel<R>(h, L, ks[i], cond, use_cond, s)) != cudaSuccess) return e;
+    if (timed) {
+      T.cat[slot][i] = kernel_category(ks[i]);
+      if ((e = cudaEventRecord(T.ev[slot][i + 1], s)) != cudaSuccess) return e;
+    }
   }
-  if (timed) T.pending[slot] = true;
+  if (timed) {
+    T.nk[slot] = nk;
+    T.pending[slot] = true;
+  }
   return cudaSuccess;
 }
 
@@ -330,6 +409,62 @@ template <typename R> lgf_status run_loop(lgf_ctx* h, Lane<R>& L, double tol, in
   return sync_state(h);
 }
 
+// Mode log of one step: D^ of the divergence just measured, compared with the
+// one of the previous step.
+template <typename R> cudaError_t log_modes(lgf_ctx* h, Lane<R>& L, bool prime_only) {
+  const Geom& g = h->geom;
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(L.Dlog, L.D, sizeof(C2<R>) * 4 * g.V, cudaMemcpyDeviceToDevice, h->stream)) != cudaSuccess)
+    return e;
+  if ((e = launch_fft_xy<R>(g, L.plan, L.Dlog, L.tw, L.pos, -1, 4, h->stream)) != cudaSuccess) return e;
+  if ((e = launch_fft_zt<R>(g, L.plan, L.Dlog, L.tw, L.pos, L.K, -1, 4, h->stream)) != cudaSuccess) return e;
+  if (!prime_only && (e = launch_mode_log<R>(g, L.mg, L.Dlog, L.Dprev, h->ls, h->stats, h->stream)) != cudaSuccess)
+    return e;
+  if ((e = launch_log_state_update(h->ls, h->st, h->stream)) != cudaSuccess) return e;
+  std::swap(L.Dlog, L.Dprev);
+  return cudaSuccess;
+}
+
+template <typename R> lgf_status step_lane(lgf_ctx* h, Lane<R>& L, double alpha) {
+  lgf_status s = ensure_filter<R>(h, L, alpha);
+  if (s != LGF_OK) return s;
+  cudaError_t e;
+  if (h->logging && !h->log_primed) {
+    if ((e = log_modes<R>(h, L, true)) != cudaSuccess) return fail_cuda(h, e, "mode log");
+    h->log_primed = true;
+  }
+  if ((e = enqueue_body<R>(h, L, 0, 0, h->stream)) != cudaSuccess) return fail_cuda(h, e, "lgf_step");
+  if (h->learned) {
+    // a rejected learned step is undone and redone with the plain filter now
+    if ((s = sync_state(h)) != LGF_OK) return s;
+    if (h->st_host->revert && (e = enqueue_body<R>(h, L, 0, 0, h->stream)) != cudaSuccess)
+      return fail_cuda(h, e, "lgf_step redo");
+  }
+  if (h->logging && (e = log_modes<R>(h, L, false)) != cudaSuccess) return fail_cuda(h, e, "mode log");
+  return LGF_OK;
+}
+
+struct MlpScratch {
+  float* part_g = nullptr;
+  double* part_l = nullptr;
+  float* grad = nullptr;
+  double* loss = nullptr;
+  int nb = 0;
+  cudaError_t alloc(int nblocks, int nloss, cudaStream_t s) {
+    nb = nblocks;
+    cudaError_t e = cudaMallocAsync((void**)&part_g, sizeof(float) * (size_t)nb * MLP_NPARAM, s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&part_l, sizeof(double) * nb, s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&grad, sizeof(float) * MLP_NPARAM, s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&loss, sizeof(double) * (size_t)(nloss > 0 ? nloss : 1), s);
+    return e;
+  }
+  void release(cudaStream_t s) {
+    if (part_g) cudaFreeAsync(part_g, s);
+    if (part_l) cudaFreeAsync(part_l, s);
+    if (grad) cudaFreeAsync(grad, s);
+    if (loss) cudaFreeAsync(loss, s);
+  }
+};
 }  // namespace
 
 // ===========================================================================
@@ -370,8 +505,9 @@ lgf_status lgf_destroy(lgf_handle h) {
   if (h->defect_host) cudaFreeHost(h->defect_host);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   for (int i = 0; i < TimingRing::kSlots; ++i)
-    for (int k = 0; k < TimingRing::kEv; ++k)
+    for (int k = 0; k <= TimingRing::kMaxK; ++k)
       if (h->timing.ev[i][k]) cudaEventDestroy(h->timing.ev[i][k]);
+  cudaFree(h->mlp_w); cudaFree(h->ls); cudaFree(h->stats);
   delete h;
   return LGF_OK;
 }
@@ -381,7 +517,7 @@ lgf_status lgf_create(const int32_t extents[4], lgf_precision prec, uint32_t fla
   if (!extents || !out) return LGF_E_ARG;
   *out = nullptr;
   if (prec != LGF_FP64 && prec != LGF_FP32 && prec != LGF_MIXED) return LGF_E_ARG;
-  if (flags & ~(uint32_t)(LGF_STORE12 | LGF_TRACK_G | LGF_PLAIN_SD)) return LGF_E_ARG;
+  if (flags & ~(uint32_t)(LGF_STORE12 | LGF_TRACK_G | LGF_PLAIN_SD | LGF_LEARNED)) return LGF_E_ARG;
   for (int mu = 0; mu < 4; ++mu)
     if (!extent_ok(extents[mu])) return LGF_E_UNSUPPORTED;
   lgf_ctx* h = new (std::nothrow) lgf_ctx();
@@ -389,6 +525,7 @@ lgf_status lgf_create(const int32_t extents[4], lgf_precision prec, uint32_t fla
   try {
     h->prec = prec;
     h->flags = flags;
+    h->learned = (flags & LGF_LEARNED) != 0;
     h->stream = (cudaStream_t)cuda_stream;
     if (cudaGetDevice(&h->device) != cudaSuccess) { delete h; return LGF_E_CUDA; }
     Geom& g = h->geom;
@@ -530,15 +667,9 @@ lgf_status lgf_step(lgf_handle h, double alpha) {
   if (s != LGF_OK) return s;
   if (!h->have_links) return fail(h, LGF_E_STATE, "no links set");
   if (!std::isfinite(alpha)) return fail(h, LGF_E_ARG, "alpha must be finite");
-  cudaError_t e;
-  if (h->phase == 64) {
-    if ((s = ensure_filter<double>(h, h->d, alpha)) != LGF_OK) return s;
-    e = enqueue_body<double>(h, h->d, 0, 0, h->stream);
-  } else {
-    if ((s = ensure_filter<float>(h, h->f, alpha)) != LGF_OK) return s;
-    e = enqueue_body<float>(h, h->f, 0, 0, h->stream);
-  }
-  if (e != cudaSuccess) return fail_cuda(h, e, "lgf_step");
+  if (h->learned && !h->mlp_w) return fail(h, LGF_E_STATE, "LGF_LEARNED handle without a loaded preconditioner");
+  s = h->phase == 64 ? step_lane<double>(h, h->d, alpha) : step_lane<float>(h, h->f, alpha);
+  if (s != LGF_OK) return s;
   h->have_g = true;
   return LGF_OK;
 }
@@ -562,6 +693,7 @@ lgf_status lgf_fix(lgf_handle h, double theta_tol, int32_t max_iter, double alph
   if (s != LGF_OK) return s;
   if (!h->have_links) return fail(h, LGF_E_STATE, "no links set");
   if (!(theta_tol >= 0.0) || max_iter < 0 || !std::isfinite(alpha)) return fail(h, LGF_E_ARG, "bad fix arguments");
+  if (h->learned && !h->mlp_w) return fail(h, LGF_E_STATE, "LGF_LEARNED handle without a loaded preconditioner");
   if (h->phase == 32) {
     if ((s = ensure_filter<float>(h, h->f, alpha)) != LGF_OK) return s;
     const double tol1 = h->prec == LGF_MIXED ? std::max(theta_tol, kSwitchTheta) : theta_tol;
@@ -706,10 +838,10 @@ lgf_status lgf_set_timing(lgf_handle h, int32_t enable) {
   LGF_CK(h, cudaStreamSynchronize(h->stream));
   if (enable && !T.ev[0][0]) {
     for (int i = 0; i < TimingRing::kSlots; ++i)
-      for (int k = 0; k < TimingRing::kEv; ++k) LGF_CK(h, cudaEventCreate(&T.ev[i][k]));
+      for (int k = 0; k <= TimingRing::kMaxK; ++k) LGF_CK(h, cudaEventCreate(&T.ev[i][k]));
   }
   for (int i = 0; i < TimingRing::kSlots; ++i) T.pending[i] = false;
-  for (int k = 0; k < TimingRing::kEv - 1; ++k) T.sum_ms[k] = 0.0;
+  for (int k = 0; k < TimingRing::kCat; ++k) T.sum_ms[k] = 0.0;
   T.steps = 0;
   T.next = 0;
   T.enabled = enable != 0;
@@ -719,13 +851,122 @@ lgf_status lgf_set_timing(lgf_handle h, int32_t enable) {
 lgf_status lgf_get_timing(lgf_handle h, double* ms, int32_t nkernels, int32_t* nsteps) {
   lgf_status s = check_handle(h);
   if (s != LGF_OK) return s;
-  if (!ms || nkernels < 1 || nkernels > 5) return fail(h, LGF_E_ARG, "bad timing arguments");
+  if (!ms || nkernels < 1 || nkernels > TimingRing::kCat) return fail(h, LGF_E_ARG, "bad timing arguments");
   TimingRing& T = h->timing;
   LGF_CK(h, cudaStreamSynchronize(h->stream));
   for (int i = 0; i < TimingRing::kSlots; ++i) LGF_CK(h, timing_collect(T, i));
   for (int k = 0; k < nkernels; ++k) ms[k] = T.steps ? T.sum_ms[k] / (double)T.steps : 0.0;
   if (nsteps) *nsteps = (int32_t)T.steps;
   return LGF_OK;
+}
+
+lgf_status lgf_load_preconditioner(lgf_handle h, const uint16_t* w, size_t n_w, int where) {
+  lgf_status s = check_handle(h);
+  if (s != LGF_OK) return s;
+  if (!w || n_w != (size_t)MLP_NPARAM || (where != LGF_HOST && where != LGF_DEVICE))
+    return fail(h, LGF_E_ARG, "expected 8833 BF16 parameters");
+  if (!h->mlp_w) LGF_CK(h, dalloc(&h->mlp_w, (size_t)MLP_NPARAM));
+  LGF_CK(h, cudaMemcpyAsync(h->mlp_w, w, (size_t)MLP_NPARAM * 2,
+                            where == LGF_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, h->stream));
+  LGF_CK(h, cudaStreamSynchronize(h->stream));
+  return LGF_OK;
+}
+
+lgf_status lgf_get_fallbacks(lgf_handle h, int32_t* n) {
+  lgf_status s = check_handle(h);
+  if (s != LGF_OK) return s;
+  if (!n) return fail(h, LGF_E_ARG, "null pointer");
+  if ((s = sync_state(h)) != LGF_OK) return s;
+  *n = h->st_host->n_fallback;
+  return LGF_OK;
+}
+
+lgf_status lgf_set_mode_log(lgf_handle h, int32_t enable) {
+  lgf_status s = check_handle(h);
+  if (s != LGF_OK) return s;
+  LGF_CK(h, cudaStreamSynchronize(h->stream));
+  h->logging = false;
+  h->log_primed = false;
+  if (!enable) return LGF_OK;
+  const int64_t V = h->geom.V;
+  const int64_t nclass = h->phase == 64 ? h->d.mg.nclass : h->f.mg.nclass;
+  if (!h->stats) LGF_CK(h, dalloc(&h->stats, (size_t)MLP_NBUCKET * nclass * 4));
+  if (!h->ls) LGF_CK(h, dalloc(&h->ls, 1));
+  if (h->phase == 64 && !h->d.Dlog) {
+    LGF_CK(h, dalloc(&h->d.Dlog, (size_t)4 * V));
+    LGF_CK(h, dalloc(&h->d.Dprev, (size_t)4 * V));
+  }
+  if (h->phase == 32 && !h->f.Dlog) {
+    LGF_CK(h, dalloc(&h->f.Dlog, (size_t)4 * V));
+    LGF_CK(h, dalloc(&h->f.Dprev, (size_t)4 * V));
+  }
+  LGF_CK(h, cudaMemsetAsync(h->stats, 0, sizeof(double) * MLP_NBUCKET * nclass * 4, h->stream));
+  LGF_CK(h, cudaMemsetAsync(h->ls, 0, sizeof(LogState), h->stream));
+  LGF_CK(h, cudaStreamSynchronize(h->stream));
+  h->logging = true;
+  return LGF_OK;
+}
+
+lgf_status lgf_get_mode_log(lgf_handle h, double* out, int64_t n) {
+  lgf_status s = check_handle(h);
+  if (s != LGF_OK) return s;
+  const int64_t nclass = h->phase == 64 ? h->d.mg.nclass : h->f.mg.nclass;
+  if (!out || !h->stats || n != (int64_t)MLP_NBUCKET * nclass * 4)
+    return fail(h, LGF_E_ARG, "mode log not enabled or wrong size");
+  LGF_CK(h, cudaMemcpyAsync(out, h->stats, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
+  LGF_CK(h, cudaStreamSynchronize(h->stream));
+  return LGF_OK;
+}
+
+lgf_status lgf_mlp_eval(const uint16_t* P, const float* X, int64_t n, float* m, void* cuda_stream) {
+  if (!P || !X || !m || n < 0) return LGF_E_ARG;
+  if (n == 0) return LGF_OK;
+  return launch_mlp_eval(P, X, n, m, (cudaStream_t)cuda_stream) == cudaSuccess ? LGF_OK : LGF_E_CUDA;
+}
+
+
+lgf_status lgf_mlp_loss_grad(const float* P, const float* X, const float* Y, const float* W, int64_t n, float* grad,
+                             double* loss, void* cuda_stream) {
+  if (!P || !X || !Y || !W || !grad || n <= 0) return LGF_E_ARG;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  MlpScratch sc;
+  const int nb = (int)std::min<int64_t>((n + 63) / 64, 304);
+  cudaError_t e = sc.alloc(nb, 1, s);
+  if (e == cudaSuccess)
+    e = launch_mlp_grad(P, X, Y, W, n, 0, 0, 0, 1.f / (float)n, sc.part_g, sc.part_l, nb, grad, sc.loss, s);
+  double l = 0.0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&l, sc.loss, sizeof(double), cudaMemcpyDeviceToHost, s);
+  sc.release(s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? LGF_E_NOMEM : LGF_E_CUDA;
+  if (loss) *loss = l;
+  return LGF_OK;
+}
+
+lgf_status lgf_mlp_train(float* P, float* adam, const float* X, const float* Y, const float* W, int64_t n,
+                         int32_t batch, int32_t steps, float lr, uint64_t seed, int32_t t0, double* loss_hist,
+                         void* cuda_stream) {
+  if (!P || !adam || !X || !Y || !W || n <= 0 || batch <= 0 || steps < 0 || !(lr > 0.f) || t0 < 0) return LGF_E_ARG;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  MlpScratch sc;
+  const int nb = (int)std::min<int64_t>((batch + 63) / 64, 304);
+  cudaError_t e = sc.alloc(nb, steps, s);
+  for (int i = 0; i < steps && e == cudaSuccess; ++i) {
+    e = launch_mlp_grad(P, X, Y, W, n, batch, seed, t0 + i, 1.f / (float)batch, sc.part_g, sc.part_l, nb, sc.grad,
+                        sc.loss + i, s);
+    if (e == cudaSuccess) e = launch_adam(P, adam, adam + MLP_NPARAM, sc.grad, lr, t0 + i + 1, s);
+  }
+  if (e == cudaSuccess && loss_hist && steps > 0)
+    e = cudaMemcpyAsync(loss_hist, sc.loss, sizeof(double) * steps, cudaMemcpyDeviceToHost, s);
+  sc.release(s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? LGF_E_NOMEM : LGF_E_CUDA;
+  return LGF_OK;
+}
+
+lgf_status lgf_mlp_to_bf16(const float* P, uint16_t* out, void* cuda_stream) {
+  if (!P || !out) return LGF_E_ARG;
+  return launch_f32_to_bf16(P, out, MLP_NPARAM, (cudaStream_t)cuda_stream) == cudaSuccess ? LGF_OK : LGF_E_CUDA;
 }
 
 lgf_status lgf_get_phase(lgf_handle h, int32_t* bits) {

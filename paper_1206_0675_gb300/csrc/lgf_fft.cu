@@ -238,7 +238,8 @@ __global__ void __launch_bounds__(512) fft_xy_kernel(Geom g, FFTDir dx, FFTDir d
 template <typename R>
 __global__ void __launch_bounds__(512) fft_zt_filter_kernel(Geom g, FFTDir dz, FFTDir dt, C2<R>* __restrict__ data,
                                      const C2<R>* __restrict__ twg, const short* __restrict__ posg,
-                                     const R* __restrict__ K, int xc, int mode) {
+                                     const R* __restrict__ K, int xc, int mode, const float* __restrict__ mtab,
+                                     int4 H, const int* __restrict__ use_m) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int Lx = g.L[0], Ly = g.L[1], Lz = g.L[2], Lt = g.L[3];
   C2<R>* tw;
@@ -262,9 +263,17 @@ __global__ void __launch_bounds__(512) fft_zt_filter_kernel(Geom g, FFTDir dz, F
   if (mode == 0) {
     fft_lines_dit<R, -1>(tile, lz, dz, tw);
     fft_lines_dit<R, -1>(tile, lt, dt, tw + Lz);
+    // learned multiplier of the momentum class (f_mu = min(k_mu, L_mu - k_mu))
+    const bool learned = mtab != nullptr && *use_m != 0;
+    const int fy = min(y, Ly - y);
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       const int xi = i % xc, zt = i / xc, z = zt % Lz, t = zt / Lz;
-      const R k = __ldg(&K[(int64_t)zt * plane + sxy + xi]);
+      R k = __ldg(&K[(int64_t)zt * plane + sxy + xi]);
+      if (learned) {
+        const int kx = x0 + xi;
+        const int fx = min(kx, Lx - kx), fz = min(z, Lz - z), ft = min(t, Lt - t);
+        k *= (R)__ldg(&mtab[((ft * H.z + fz) * H.y + fy) * H.x + fx]);
+      }
       C2<R>& e = tile[t * TS + z * xc + xi];
       e = mkc<R>(e.x * k, e.y * k);
     }
@@ -499,12 +508,14 @@ cudaError_t launch_fft_xy(const Geom& g, const FFTPlan& p, C2<R>* data, const C2
 
 template <typename R>
 cudaError_t launch_fft_zt(const Geom& g, const FFTPlan& p, C2<R>* data, const C2<R>* tw, const short* pos,
-                          const R* K, int mode, int nfields, cudaStream_t s) {
+                          const R* K, int mode, int nfields, cudaStream_t s, const float* mtab, const int* use_m) {
   const size_t smem = p.smem_zt;
   dim3 grid((unsigned)(g.L[0] / p.xc * g.L[1]), (unsigned)nfields);
   cudaError_t e = allow_smem(fft_zt_filter_kernel<R>, smem);
   if (e != cudaSuccess) return e;
-  fft_zt_filter_kernel<R><<<grid, p.threads_zt, smem, s>>>(g, p.d[2], p.d[3], data, tw, pos, K, p.xc, mode);
+  const int4 H = make_int4(g.L[0] / 2 + 1, g.L[1] / 2 + 1, g.L[2] / 2 + 1, g.L[3] / 2 + 1);
+  fft_zt_filter_kernel<R><<<grid, p.threads_zt, smem, s>>>(g, p.d[2], p.d[3], data, tw, pos, K, p.xc, mode, mtab, H,
+                                                           use_m);
   return cudaGetLastError();
 }
 
@@ -529,9 +540,9 @@ template cudaError_t launch_fft_xy<double>(const Geom&, const FFTPlan&, C2<doubl
 template cudaError_t launch_fft_xy<float>(const Geom&, const FFTPlan&, C2<float>*, const C2<float>*, const short*,
                                           int, int, cudaStream_t);
 template cudaError_t launch_fft_zt<double>(const Geom&, const FFTPlan&, C2<double>*, const C2<double>*, const short*,
-                                           const double*, int, int, cudaStream_t);
+                                           const double*, int, int, cudaStream_t, const float*, const int*);
 template cudaError_t launch_fft_zt<float>(const Geom&, const FFTPlan&, C2<float>*, const C2<float>*, const short*,
-                                          const float*, int, int, cudaStream_t);
+                                          const float*, int, int, cudaStream_t, const float*, const int*);
 #define LGF_INST_C(R, RG, GR)                                                                                    \
   template cudaError_t launch_fft_xy_inv_gauge<R, RG, GR>(const Geom&, const FFTPlan&, C2<R>*, const C2<R>*,      \
                                                           const short*, C2<RG>*, C2<RG>*, cudaStream_t);

@@ -22,7 +22,9 @@ struct DevState {
   int status;        // 0 ok, 1 non-finite F or theta, 2 timeout
   unsigned int ticket;  // CTA completion counter of the measurement reduction
   int hist_cap;      // capacity of the history buffers (0 = none)
-  int pad;
+  int use_m;         // the running step multiplies the filter by the learned table
+  int revert;        // the last learned step lowered F: undo it and redo it with the plain filter
+  int n_fallback;    // learned steps rejected since the counter was reset
   double* F_hist;    // F after measurement number i (i = iter) if i < hist_cap
   double* theta_hist;
 };
@@ -37,9 +39,21 @@ inline int64_t measure_blocks(int64_t V) { return (V + MEASURE_THREADS - 1) / ME
 // Delta, F and theta of the current links (Sec. 2; kernel k2 of Sec. 3.2).
 // count_iter != 0: this measurement follows a link update (iter += 1).
 // use_cond != 0: set the graph conditional to (theta >= tol && iter < max_iter).
+// count_iter = -1: this measurement follows the undo of a rejected step (iter -= 1).
+// only_if_revert != 0: do nothing unless an undo is pending (st->revert).
+// After a counted step that used the learned table (st->use_m) and lowered F,
+// st->revert is set and the WHILE condition stays true so that the next
+// body undoes the step and redoes it with the plain filter.
 template <typename R, int ROWS>
 cudaError_t launch_measure(const Geom& g, const C2<R>* links, C2<R>* delta, double* partials, DevState* st,
-                           int count_iter, unsigned long long cond_handle, int use_cond, cudaStream_t s);
+                           int count_iter, unsigned long long cond_handle, int use_cond, cudaStream_t s,
+                           int only_if_revert = 0);
+
+// Undo of the last update when st->revert is set: U_mu(x) <- g^dag(x) U_mu(x)
+// g(x + mu^) and, when G is given (3 rows, precision R), G <- g^dag G.
+template <typename R, int LROWS, int GROWS>
+cudaError_t launch_revert(const Geom& g, C2<R>* links, const C2<R>* gfield, C2<R>* Gacc, const DevState* st,
+                          cudaStream_t s);
 
 // U_mu(x) <- g(x) U_mu(x) g^dagger(x + mu^) in place (Sec. 2 eq. 2; kernel k6).
 // Links in precision R with LROWS stored rows; g in precision R with GROWS rows.
@@ -115,9 +129,12 @@ cudaError_t launch_fft_xy(const Geom& g, const FFTPlan& p, C2<R>* data, const C2
                           int nfields, cudaStream_t s);
 // mode 0: forward (z,t) DFT, multiply by K, inverse (z,t) DFT (pass B);
 // mode -1 / +1: forward / inverse (z,t) DFT only (K unused).
+// mtab (may be NULL): learned multiplier per momentum class, applied when
+// *use_m != 0 (mode 0 only).
 template <typename R>
 cudaError_t launch_fft_zt(const Geom& g, const FFTPlan& p, C2<R>* data, const C2<R>* tw, const short* pos,
-                          const R* K, int mode, int nfields, cudaStream_t s);
+                          const R* K, int mode, int nfields, cudaStream_t s, const float* mtab = nullptr,
+                          const int* use_m = nullptr);
 // Inverse (x,y) transform fused with g(x) = reunitarize(1 + Delta'(x)) in FP64;
 // g stored with GROWS rows in precision RG; optional G <- g G (precision RG2 with 3 rows).
 template <typename R, typename RG, int GROWS>

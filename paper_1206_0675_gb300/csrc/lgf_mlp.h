@@ -1,0 +1,58 @@
+// Learned multiplier: network layout and launchers (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lgf_internal.h"
+
+namespace lgf {
+
+// 6 -> 64 -> 64 -> 64 -> 1, flat parameter layout (row-major [out][in]):
+constexpr int MLP_NIN = 6, MLP_NH = 64;
+constexpr int MLP_OFF_W1 = 0, MLP_OFF_B1 = 384, MLP_OFF_W2 = 448, MLP_OFF_B2 = 4544;
+constexpr int MLP_OFF_W3 = 4608, MLP_OFF_B3 = 8704, MLP_OFF_W4 = 8768, MLP_OFF_B4 = 8832;
+constexpr int MLP_NPARAM = 8833;
+constexpr float MLP_ITER_SCALE = 10000.f;  // iter_frac = min(iter / 10000, 1)
+constexpr int MLP_NBUCKET = 40;            // theta buckets of the mode log
+
+// Momentum classes of a lattice: f_mu = min(k_mu, L_mu - k_mu) in [0, L/2];
+// class = ((ft H2 + fz) H1 + fy) H0 + fx with H_mu = L_mu/2 + 1.
+struct MlpGeom {
+  int H[4];
+  int off[4];      // offsets of the per-direction p2 tables
+  int64_t nclass;
+  float m_lo, m_hi;
+};
+
+// bucket index of the mode log: b = clamp(4 - 2 * bucket(theta), 0, 39)
+// with bucket(theta) = floor(2 log10 theta) / 2.
+__host__ __device__ inline int mlp_bucket_index(double theta) {
+  if (!(theta > 0.0)) return MLP_NBUCKET - 1;
+  const double b = floor(2.0 * log10(theta)) * 0.5;
+  int i = (int)(4.0 - 2.0 * b);
+  return i < 0 ? 0 : (i >= MLP_NBUCKET ? MLP_NBUCKET - 1 : i);
+}
+
+cudaError_t launch_mlp_eval(const uint16_t* P, const float* X, int64_t n, float* out, cudaStream_t s);
+cudaError_t launch_mlp_multiplier(const uint16_t* P, const MlpGeom& mg, const float* p2, DevState* st, float* mtab,
+                                  cudaStream_t s);
+size_t mlp_train_smem();
+cudaError_t launch_mlp_grad(const float* P, const float* X, const float* Y, const float* Wt, int64_t n, int64_t batch,
+                            uint64_t seed, int step, float inv_sw, float* part_g, double* part_l, int nblocks,
+                            float* grad, double* loss, cudaStream_t s);
+cudaError_t launch_adam(float* P, float* mom, float* vel, const float* grad, float lr, int t, cudaStream_t s);
+cudaError_t launch_f32_to_bf16(const float* in, uint16_t* out, int n, cudaStream_t s);
+
+// Per-mode statistics of consecutive Fourier-space divergences (see lgf_mlp.cu).
+struct LogState {
+  double theta_prev;
+  int iter_prev;
+  int have_prev;
+};
+template <typename R>
+cudaError_t launch_mode_log(const Geom& g, const MlpGeom& mg, const C2<R>* cur, const C2<R>* prev,
+                            const LogState* ls, double* stats, cudaStream_t s);
+cudaError_t launch_log_state_update(LogState* ls, const DevState* st, cudaStream_t s);
+
+}  // namespace lgf

@@ -41,7 +41,8 @@ __device__ __forceinline__ void block_sum2(double& a, double& b) {
 template <typename R, int ROWS>
 __global__ void __launch_bounds__(MEASURE_THREADS)
 measure_kernel(Geom g, MatField<R, ROWS> U, C2<R>* __restrict__ delta, double* __restrict__ partials,
-               DevState* __restrict__ st, int count_iter, unsigned long long cond, int use_cond) {
+               DevState* __restrict__ st, int count_iter, unsigned long long cond, int use_cond, int only_if_revert) {
+  if (only_if_revert && !st->revert) return;
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double fsum = 0.0, tsum = 0.0;
   if (s < g.V) {
@@ -105,10 +106,20 @@ measure_kernel(Geom g, MatField<R, ROWS> U, C2<R>* __restrict__ delta, double* _
     const double F = f / (12.0 * Vd);
     const double th = 4.0 * t / (3.0 * Vd);
     int it = st->iter;
-    if (count_iter) {
+    int revert = 0;
+    if (count_iter > 0) {
       it += 1;
       st->iter = it;
       st->F_prev = st->F;
+      // a learned step that lowered F is undone and redone with the plain filter
+      if (st->use_m && F < st->F) {
+        revert = 1;
+        st->n_fallback += 1;
+      }
+      st->revert = revert;
+    } else if (count_iter < 0) {
+      it -= 1;
+      st->iter = it;
     }
     st->F = F;
     st->theta = th;
@@ -121,18 +132,19 @@ measure_kernel(Geom g, MatField<R, ROWS> U, C2<R>* __restrict__ delta, double* _
     st->ticket = 0u;
     if (use_cond) {
       cudaGraphConditionalHandle h = (cudaGraphConditionalHandle)cond;
-      cudaGraphSetConditional(h, (finite && th >= st->tol && it < st->max_iter) ? 1u : 0u);
+      cudaGraphSetConditional(h, (finite && ((th >= st->tol && it < st->max_iter) || revert)) ? 1u : 0u);
     }
   }
 }
 
 template <typename R, int ROWS>
 cudaError_t launch_measure(const Geom& g, const C2<R>* links, C2<R>* delta, double* partials, DevState* st,
-                           int count_iter, unsigned long long cond_handle, int use_cond, cudaStream_t s) {
+                           int count_iter, unsigned long long cond_handle, int use_cond, cudaStream_t s,
+                           int only_if_revert) {
   MatField<R, ROWS> U{const_cast<C2<R>*>(links), g.V};
   const int64_t nb = measure_blocks(g.V);
   measure_kernel<R, ROWS><<<(unsigned)nb, MEASURE_THREADS, 0, s>>>(g, U, delta, partials, st, count_iter, cond_handle,
-                                                                   use_cond);
+                                                                   use_cond, only_if_revert);
   return cudaGetLastError();
 }
 
@@ -188,6 +200,73 @@ cudaError_t launch_update(const Geom& g, C2<R>* links, const C2<R>* gfield, cuda
   MatField<R, GROWS> Gf{const_cast<C2<R>*>(gfield), g.V};
   const int64_t nb = (g.V + UPDATE_THREADS - 1) / UPDATE_THREADS;
   update_kernel<R, LROWS, GROWS><<<(unsigned)nb, UPDATE_THREADS, 0, s>>>(g, U, Gf);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// undo of a rejected step: U_mu(x) <- g^dag(x) U_mu(x) g(x + mu^), G <- g^dag G
+// ---------------------------------------------------------------------------
+
+template <typename R, int LROWS, int GROWS>
+__global__ void __launch_bounds__(UPDATE_THREADS)
+revert_kernel(Geom g, MatField<R, LROWS> U, MatField<R, GROWS> Gf, MatField<R, 3> Gacc, const DevState* st) {
+  if (!st->revert) return;
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= g.V) return;
+  int c[4];
+  site_coords(g, s, c);
+  M3<R> gx;
+  Gf.load_ro(0, s, gx);
+#pragma unroll 1
+  for (int mu = 0; mu < 4; ++mu) {
+    M3<R> u, h;
+    U.load(mu, s, u);
+    Gf.load_ro(0, site_fwd(g, s, c, mu), h);
+    // T = (g^dag U)[rows 0,1]: T_ij = sum_k conj(g_ki) U_kj
+    C2<R> T[2][3];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        C2<R> acc = cconjmul<R>(gx.e[0][i], u.e[0][j]);
+        acc = cadd<R>(acc, cconjmul<R>(gx.e[1][i], u.e[1][j]));
+        T[i][j] = cadd<R>(acc, cconjmul<R>(gx.e[2][i], u.e[2][j]));
+      }
+    M3<R> o;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        C2<R> acc = cmul<R>(T[i][0], h.e[0][j]);
+        acc = cfma<R>(T[i][1], h.e[1][j], acc);
+        o.e[i][j] = cfma<R>(T[i][2], h.e[2][j], acc);
+      }
+    su3_third_row<R>(o.e[0], o.e[1], o.e[2]);
+    U.store(mu, s, o);
+  }
+  if (Gacc.p != nullptr) {
+    M3<R> G0, G1;
+    Gacc.load(0, s, G0);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        C2<R> acc = cconjmul<R>(gx.e[0][i], G0.e[0][j]);
+        acc = cadd<R>(acc, cconjmul<R>(gx.e[1][i], G0.e[1][j]));
+        G1.e[i][j] = cadd<R>(acc, cconjmul<R>(gx.e[2][i], G0.e[2][j]));
+      }
+    Gacc.store(0, s, G1);
+  }
+}
+
+template <typename R, int LROWS, int GROWS>
+cudaError_t launch_revert(const Geom& g, C2<R>* links, const C2<R>* gfield, C2<R>* Gacc, const DevState* st,
+                          cudaStream_t s) {
+  MatField<R, LROWS> U{links, g.V};
+  MatField<R, GROWS> Gf{const_cast<C2<R>*>(gfield), g.V};
+  MatField<R, 3> Ga{Gacc, g.V};
+  const int64_t nb = (g.V + UPDATE_THREADS - 1) / UPDATE_THREADS;
+  revert_kernel<R, LROWS, GROWS><<<(unsigned)nb, UPDATE_THREADS, 0, s>>>(g, U, Gf, Ga, st);
   return cudaGetLastError();
 }
 
@@ -391,6 +470,9 @@ __global__ void set_state_kernel(DevState* st, double tol, int max_iter, int res
   if (reset_iter) {
     st->iter = 0;
     st->status = ST_OK;
+    st->revert = 0;
+    st->use_m = 0;
+    st->n_fallback = 0;
   }
   st->hist_cap = hist_cap;
   st->F_hist = Fh;
@@ -470,7 +552,7 @@ cudaError_t launch_project_sites_f32_to_f64(const Geom& g, const float2* G32, do
 
 #define LGF_INST_R_ROWS(R, ROWS)                                                                                     \
   template cudaError_t launch_measure<R, ROWS>(const Geom&, const C2<R>*, C2<R>*, double*, DevState*, int,           \
-                                               unsigned long long, int, cudaStream_t);                              \
+                                               unsigned long long, int, cudaStream_t, int);                         \
   template cudaError_t launch_links_from_aos<R, ROWS>(const Geom&, const double*, C2<R>*, cudaStream_t);            \
   template cudaError_t launch_links_to_aos<R, ROWS>(const Geom&, const C2<R>*, double*, cudaStream_t);              \
   template cudaError_t launch_sites_to_aos<R, ROWS>(const Geom&, const C2<R>*, double*, cudaStream_t);              \
@@ -482,6 +564,14 @@ LGF_INST_R_ROWS(double, 2)
 LGF_INST_R_ROWS(float, 3)
 LGF_INST_R_ROWS(float, 2)
 
+template cudaError_t launch_revert<double, 3, 3>(const Geom&, C2<double>*, const C2<double>*, C2<double>*,
+                                                 const DevState*, cudaStream_t);
+template cudaError_t launch_revert<double, 2, 3>(const Geom&, C2<double>*, const C2<double>*, C2<double>*,
+                                                 const DevState*, cudaStream_t);
+template cudaError_t launch_revert<float, 2, 2>(const Geom&, C2<float>*, const C2<float>*, C2<float>*,
+                                                const DevState*, cudaStream_t);
+template cudaError_t launch_revert<float, 3, 3>(const Geom&, C2<float>*, const C2<float>*, C2<float>*,
+                                                const DevState*, cudaStream_t);
 template cudaError_t launch_update<double, 3, 3>(const Geom&, C2<double>*, const C2<double>*, cudaStream_t);
 template cudaError_t launch_update<double, 2, 3>(const Geom&, C2<double>*, const C2<double>*, cudaStream_t);
 template cudaError_t launch_update<float, 2, 2>(const Geom&, C2<float>*, const C2<float>*, cudaStream_t);

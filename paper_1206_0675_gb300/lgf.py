@@ -29,7 +29,9 @@ LIB_PATH = os.path.join(_HERE, "liblgf.so")
 LGF_OK, LGF_E_ARG, LGF_E_NOMEM, LGF_E_CUDA, LGF_E_STATE, LGF_E_NONFINITE, LGF_E_NOTCONV, LGF_E_TIMEOUT, \
     LGF_E_UNSUPPORTED = range(9)
 LGF_FP64, LGF_FP32, LGF_MIXED = 0, 1, 2
-LGF_STORE18, LGF_STORE12, LGF_TRACK_G, LGF_PLAIN_SD = 0, 1, 2, 8
+LGF_STORE18, LGF_STORE12, LGF_TRACK_G, LGF_LEARNED, LGF_PLAIN_SD = 0, 1, 2, 4, 8
+LGF_MLP_NPARAM = 8833
+MLP_NBUCKET = 40
 LGF_HOST, LGF_DEVICE = 0, 1
 
 _c_int_p = ctypes.POINTER(ctypes.c_int32)
@@ -56,6 +58,18 @@ SIGNATURES = [
     ("lgf_get_timing", ctypes.c_int, [ctypes.c_void_p, _c_dbl_p, ctypes.c_int32, _c_int_p]),
     ("lgf_measure_static", ctypes.c_int, [ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_void_p]),
+    ("lgf_load_preconditioner", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int]),
+    ("lgf_get_fallbacks", ctypes.c_int, [ctypes.c_void_p, _c_int_p]),
+    ("lgf_set_mode_log", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    ("lgf_get_mode_log", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
+    ("lgf_mlp_eval", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                    ctypes.c_void_p]),
+    ("lgf_mlp_loss_grad", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_int64, ctypes.c_void_p, _c_dbl_p, ctypes.c_void_p]),
+    ("lgf_mlp_train", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
+                                     ctypes.c_uint64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
+    ("lgf_mlp_to_bf16", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("lgf_status_string", ctypes.c_char_p, [ctypes.c_int]),
     ("lgf_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
 ]
@@ -184,6 +198,56 @@ def lgf_get_timing(h: int) -> tuple[list[float], int]:
 LGF_STATIC_MAX_SITES = 16777216
 
 
+def lgf_load_preconditioner(h: int, ptr: int, n: int, where: int) -> None:
+    _check(h, load_library().lgf_load_preconditioner(ctypes.c_void_p(h), ctypes.c_void_p(ptr), n, where),
+           "lgf_load_preconditioner")
+
+
+def lgf_get_fallbacks(h: int) -> int:
+    n = ctypes.c_int32()
+    _check(h, load_library().lgf_get_fallbacks(ctypes.c_void_p(h), ctypes.byref(n)), "lgf_get_fallbacks")
+    return n.value
+
+
+def lgf_set_mode_log(h: int, enable: bool) -> None:
+    _check(h, load_library().lgf_set_mode_log(ctypes.c_void_p(h), 1 if enable else 0), "lgf_set_mode_log")
+
+
+def lgf_get_mode_log(h: int, ptr: int, n: int) -> None:
+    _check(h, load_library().lgf_get_mode_log(ctypes.c_void_p(h), ctypes.c_void_p(ptr), n), "lgf_get_mode_log")
+
+
+def _stat(st: int, where: str) -> None:
+    if st != LGF_OK:
+        raise LgfError(st, where)
+
+
+def lgf_mlp_eval(p_ptr: int, x_ptr: int, n: int, m_ptr: int, stream: int = 0) -> None:
+    _stat(load_library().lgf_mlp_eval(ctypes.c_void_p(p_ptr), ctypes.c_void_p(x_ptr), n, ctypes.c_void_p(m_ptr),
+                                      ctypes.c_void_p(stream or None)), "lgf_mlp_eval")
+
+
+def lgf_mlp_loss_grad(p_ptr, x_ptr, y_ptr, w_ptr, n, g_ptr, stream=0) -> float:
+    loss = ctypes.c_double()
+    _stat(load_library().lgf_mlp_loss_grad(*(ctypes.c_void_p(v) for v in (p_ptr, x_ptr, y_ptr, w_ptr)), n,
+                                           ctypes.c_void_p(g_ptr), ctypes.byref(loss),
+                                           ctypes.c_void_p(stream or None)), "lgf_mlp_loss_grad")
+    return loss.value
+
+
+def lgf_mlp_train(p_ptr, adam_ptr, x_ptr, y_ptr, w_ptr, n, batch, steps, lr, seed, t0=0, stream=0) -> np.ndarray:
+    hist = np.zeros(max(steps, 1))
+    _stat(load_library().lgf_mlp_train(*(ctypes.c_void_p(v) for v in (p_ptr, adam_ptr, x_ptr, y_ptr, w_ptr)), n,
+                                       batch, steps, ctypes.c_float(lr), ctypes.c_uint64(seed), t0,
+                                       hist.ctypes.data, ctypes.c_void_p(stream or None)), "lgf_mlp_train")
+    return hist[:steps]
+
+
+def lgf_mlp_to_bf16(p_ptr: int, out_ptr: int, stream: int = 0) -> None:
+    _stat(load_library().lgf_mlp_to_bf16(ctypes.c_void_p(p_ptr), ctypes.c_void_p(out_ptr),
+                                         ctypes.c_void_p(stream or None)), "lgf_mlp_to_bf16")
+
+
 def lgf_measure_static(extents, u_ptr: int, d_ptr: int, f_theta_ptr: int, stream: int = 0) -> int:
     """Allocation-free measurement (device pointers only); returns the lgf_status code."""
     ext = (ctypes.c_int32 * 4)(*[int(e) for e in extents])
@@ -222,12 +286,14 @@ class Lattice:
     """One lattice configuration on the GPU (owns an lgf handle)."""
 
     def __init__(self, extents, precision: str = "fp64", store12: bool = False, track_G: bool = False,
-                 plain_sd: bool = False, stream: int | None = None):
+                 plain_sd: bool = False, learned: bool = False, stream: int | None = None):
         self.extents = tuple(int(e) for e in extents)
         lx, ly, lz, lt = self.extents
         self.link_shape = (4, lt, lz, ly, lx, 3, 3)
         self.site_shape = (lt, lz, ly, lx, 3, 3)
-        flags = (LGF_STORE12 if store12 else 0) | (LGF_TRACK_G if track_G else 0) | (LGF_PLAIN_SD if plain_sd else 0)
+        self.nclass = int(np.prod([e // 2 + 1 for e in self.extents]))
+        flags = ((LGF_STORE12 if store12 else 0) | (LGF_TRACK_G if track_G else 0) | (LGF_PLAIN_SD if plain_sd else 0)
+                 | (LGF_LEARNED if learned else 0))
         if stream is None:
             try:
                 import torch
@@ -330,6 +396,28 @@ class Lattice:
     def get_timing(self) -> tuple[list[float], int]:
         """Mean ms per kernel [pass A, pass B, pass C+g, update, measure] and the step count."""
         return lgf_get_timing(self.handle)
+
+    def load_preconditioner(self, weights_bf16) -> None:
+        """weights_bf16: uint16 numpy array (host) or CUDA tensor (int16/uint16/bfloat16) of 8833 values."""
+        if _is_torch_cuda(weights_bf16):
+            lgf_load_preconditioner(self.handle, weights_bf16.data_ptr(), LGF_MLP_NPARAM, LGF_DEVICE)
+        else:
+            w = np.ascontiguousarray(weights_bf16, dtype=np.uint16)
+            if w.size != LGF_MLP_NPARAM:
+                raise ValueError("expected 8833 BF16 parameters")
+            lgf_load_preconditioner(self.handle, w.ctypes.data, LGF_MLP_NPARAM, LGF_HOST)
+
+    def fallbacks(self) -> int:
+        return lgf_get_fallbacks(self.handle)
+
+    def set_mode_log(self, enable: bool = True) -> None:
+        lgf_set_mode_log(self.handle, enable)
+
+    def get_mode_log(self) -> np.ndarray:
+        """Sums [bucket][class][4] = (Re<D^_{k+1}, D^_k>, |D^_k|^2, count, iter_frac)."""
+        out = np.zeros((MLP_NBUCKET, self.nclass, 4))
+        lgf_get_mode_log(self.handle, out.ctypes.data, out.size)
+        return out
 
     @property
     def phase(self) -> int:

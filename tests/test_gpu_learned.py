@@ -1,0 +1,216 @@
+"""The learned multiplier on the GPU against its CPU oracle (oracle/lgf_mlp_oracle.py).
+
+* tensor-core inference (BF16 weights, FP32 accumulation) vs the oracle's
+  BF16-emulating forward pass;
+* training gradients vs the oracle's hand-written backward pass (which is
+  itself checked against finite differences in test_mlp_oracle.py);
+* the learned step with a constant multiplier and the F-monotonicity
+  fallback vs the FA oracle driven the same way;
+* the mode log (training data) vs the same sums formed from the oracle's
+  Fourier-space divergence.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import lgf_mlp_oracle as M
+from oracle import lgf_oracle as O
+from paper_1206_0675_gb300 import fields, lgf
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    assert torch.cuda.is_available()
+    lgf.load_library()
+    return torch
+
+
+def random_params(seed):
+    rng = np.random.default_rng(seed)
+    p = M.init_params(seed)
+    p[M.OFF_W4:M.OFF_B4] = rng.standard_normal(64) * 0.3
+    p[M.OFF_B1:M.OFF_W2] = rng.standard_normal(64) * 0.1
+    p[M.OFF_B2:M.OFF_W3] = rng.standard_normal(64) * 0.1
+    p[M.OFF_B3:M.OFF_W4] = rng.standard_normal(64) * 0.1
+    p[M.OFF_B4] = 0.2
+    return p
+
+
+def bf16_bits(p):
+    return (M.bf16_round(p).astype(np.float32).view(np.uint32) >> 16).astype(np.uint16)
+
+
+def gpu_eval(torch, bits, X):
+    Pb = torch.from_numpy(bits.view(np.int16).copy()).cuda()
+    Xd = torch.tensor(X, dtype=torch.float32).cuda()
+    m = torch.empty(X.shape[0], dtype=torch.float32, device="cuda")
+    lgf.lgf_mlp_eval(Pb.data_ptr(), Xd.data_ptr(), X.shape[0], m.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    return m.cpu().numpy().astype(np.float64)
+
+
+def test_inference_matches_bf16_oracle(torch):
+    rng = np.random.default_rng(0)
+    p = random_params(0)
+    X = rng.random((1000 + 13, 6))  # ragged tail: not a multiple of the 16-row tile
+    m_gpu = gpu_eval(torch, bf16_bits(p), X)
+    m_ref, _ = M.forward(M.bf16_round(p), X, bf16=True)
+    err = np.abs(m_gpu - m_ref) / m_ref
+    assert np.median(err) < 1e-4
+    assert np.max(err) < 1e-2
+
+
+def test_gradient_matches_oracle(torch):
+    rng = np.random.default_rng(1)
+    p = random_params(1).astype(np.float32)
+    n = 777
+    X = rng.random((n, 6)).astype(np.float32)
+    Y = (rng.standard_normal(n) * 0.2).astype(np.float32)
+    W = rng.random(n) + 0.2
+    W = (W / W.mean()).astype(np.float32)
+    loss_ref, g_ref = M.loss_and_grad(p.astype(np.float64), X.astype(np.float64), Y.astype(np.float64),
+                                      W.astype(np.float64))
+    dev = torch.device("cuda")
+    Pd, Xd, Yd, Wd = (torch.from_numpy(a).to(dev) for a in (p, X, Y, W))
+    g = torch.empty(M.NPARAM, dtype=torch.float32, device=dev)
+    loss = lgf.lgf_mlp_loss_grad(Pd.data_ptr(), Xd.data_ptr(), Yd.data_ptr(), Wd.data_ptr(), n, g.data_ptr(),
+                                 torch.cuda.current_stream().cuda_stream)
+    g = g.cpu().numpy().astype(np.float64)
+    assert abs(loss - loss_ref) < 1e-5 * loss_ref
+    assert np.max(np.abs(g - g_ref)) < 1e-4 * np.max(np.abs(g_ref))
+
+
+def test_training_reduces_loss(torch):
+    rng = np.random.default_rng(2)
+    n = 20000
+    X = rng.random((n, 6)).astype(np.float32)
+    Y = (0.15 * np.sin(3 * X[:, 0]) - 0.1 * X[:, 4] + 0.05 * X[:, 5]).astype(np.float32)
+    W = np.ones(n, dtype=np.float32)
+    dev = torch.device("cuda")
+    Pd = torch.from_numpy(M.init_params(3).astype(np.float32)).to(dev)
+    adam = torch.zeros(2 * M.NPARAM, dtype=torch.float32, device=dev)
+    Xd, Yd, Wd = (torch.from_numpy(a).to(dev) for a in (X, Y, W))
+    st = torch.cuda.current_stream().cuda_stream
+    g = torch.empty(M.NPARAM, dtype=torch.float32, device=dev)
+    l0 = lgf.lgf_mlp_loss_grad(Pd.data_ptr(), Xd.data_ptr(), Yd.data_ptr(), Wd.data_ptr(), n, g.data_ptr(), st)
+    hist = lgf.lgf_mlp_train(Pd.data_ptr(), adam.data_ptr(), Xd.data_ptr(), Yd.data_ptr(), Wd.data_ptr(), n, 1024,
+                             600, 1e-3, 11, 0, st)
+    l1 = lgf.lgf_mlp_loss_grad(Pd.data_ptr(), Xd.data_ptr(), Yd.data_ptr(), Wd.data_ptr(), n, g.data_ptr(), st)
+    assert hist.shape == (600,) and np.all(np.isfinite(hist))
+    assert l1 < 0.1 * l0
+    # the oracle agrees on the trained network's loss
+    lo, _ = M.loss_and_grad(Pd.cpu().numpy().astype(np.float64), X.astype(np.float64), Y.astype(np.float64),
+                            W.astype(np.float64))
+    assert abs(lo - l1) < 1e-4 * lo + 1e-9
+
+
+def constant_multiplier_bits(z0):
+    p = np.zeros(M.NPARAM)
+    p[M.OFF_B4] = z0
+    return bf16_bits(p)
+
+
+def oracle_learned_fix(U, K, m, n_steps):
+    """Algorithm 1 with filter K*m and the fallback: a step that lowers F is redone with K."""
+    F, th, D = O.measure(U)
+    Fs, ths, nf = [F], [th], 0
+    for _ in range(n_steps):
+        Un, _ = O.fa_step(U, 0.08, K * m, D)
+        Fn, thn, Dn = O.measure(Un)
+        if Fn < F:
+            nf += 1
+            Un, _ = O.fa_step(U, 0.08, K, D)
+            Fn, thn, Dn = O.measure(Un)
+        U, F, th, D = Un, Fn, thn, Dn
+        Fs.append(F)
+        ths.append(th)
+    return np.array(Fs), np.array(ths), nf
+
+
+@pytest.mark.parametrize("alpha_scale,z0", [(1.0, 0.7), (1.6, 3.0)])
+def test_learned_constant_multiplier_and_fallback_match_oracle(torch, alpha_scale, z0):
+    """z0 = 0.7: m = softplus(0.7) = 1.10, no fallback.  z0 = 3: m clamps to 1.25 and,
+    with alpha scaled by 1.6, steps overshoot and are redone with the plain filter."""
+    ext = (6, 4, 8, 4)
+    alpha = 0.08 * alpha_scale
+    U = fields.random_links(ext, eps=0.9, seed=21)
+    bits = constant_multiplier_bits(z0)
+    m = float(np.clip(gpu_eval(torch, bits, np.zeros((1, 6)))[0], 0.25, 1.25))
+    n = 30
+    with lgf.Lattice(ext, "fp64", learned=True) as lat:
+        lat.load_preconditioner(bits)
+        lat.set_links(U)
+        Fh, Th = lat.set_trace(n + 1)
+        it, F, th, conv = lat.fix(0.0, n, alpha)
+        nf = lat.fallbacks()
+    K = O.fa_filter(ext, alpha)
+    Fo, tho, nfo = oracle_learned_fix(U, K, m, n)
+    assert it == n
+    assert nf == nfo
+    if z0 > 1:
+        assert nf > 0
+    assert np.max(np.abs(Fh - Fo) / np.abs(Fo)) < 1e-11
+    assert np.max(np.abs(Th - tho) / tho) < 1e-9
+
+
+def test_learned_step_api_redoes_rejected_steps(torch):
+    ext = (4, 4, 4, 6)
+    U = fields.random_links(ext, eps=0.9, seed=5)
+    bits = constant_multiplier_bits(3.0)
+    with lgf.Lattice(ext, "fp64", learned=True) as lat:
+        lat.load_preconditioner(bits)
+        lat.set_links(U)
+        F_prev = lat.measure()[0]
+        for _ in range(10):
+            lat.step(0.13)
+            F, _ = lat.measure()
+            assert F >= F_prev  # every accepted step raises F
+            F_prev = F
+
+
+def packed_hat(D):
+    """Fourier transforms of the four packed divergence fields from the oracle's 3x3 Delta_A."""
+    Dh = O.fft4(D)
+    return np.stack([-1j * Dh[..., 0, 0] + Dh[..., 1, 1], Dh[..., 0, 1], Dh[..., 0, 2], Dh[..., 1, 2]])
+
+
+def test_mode_log_matches_oracle(torch):
+    ext = (6, 4, 4, 6)
+    steps = 3
+    U = fields.random_links(ext, eps=0.8, seed=2)
+    with lgf.Lattice(ext, "fp64") as lat:
+        lat.set_links(U)
+        lat.set_mode_log(True)
+        for _ in range(steps):
+            lat.step(0.08)
+        stats = lat.get_mode_log()
+    lx, ly, lz, lt = ext
+    H = [L // 2 + 1 for L in ext]
+    t, z, y, x = np.meshgrid(range(lt), range(lz), range(ly), range(lx), indexing="ij")
+    f = [np.minimum(c, L - c) for c, L in ((x, lx), (y, ly), (z, lz), (t, lt))]
+    cls = ((f[3] * H[2] + f[2]) * H[1] + f[1]) * H[0] + f[0]
+    nclass = int(np.prod(H))
+    ref = np.zeros_like(stats)
+    Ucur = U
+    F, th, D = O.measure(Ucur)
+    prev = packed_hat(D)
+    for k in range(steps):
+        b = int(np.clip(4 - 2 * np.floor(2 * np.log10(th)) / 2, 0, 39))
+        Ucur, _ = O.fa_step(Ucur, 0.08, D=D)
+        F, th_new, D = O.measure(Ucur)
+        cur = packed_hat(D)
+        num = np.sum(np.real(np.conj(prev) * cur), axis=0)
+        den = np.sum(np.abs(prev) ** 2, axis=0)
+        ref[b, :, 0] += np.bincount(cls.ravel(), num.ravel(), nclass)
+        ref[b, :, 1] += np.bincount(cls.ravel(), den.ravel(), nclass)
+        ref[b, :, 2] += np.bincount(cls.ravel(), minlength=nclass)
+        ref[b, :, 3] += np.bincount(cls.ravel(), minlength=nclass) * min(k / 10000.0, 1.0)
+        prev, th = cur, th_new
+    scale = np.max(np.abs(ref[..., 1]))
+    assert np.array_equal(stats[..., 2], ref[..., 2])
+    assert np.max(np.abs(stats[..., 0] - ref[..., 0])) < 1e-10 * scale
+    assert np.max(np.abs(stats[..., 1] - ref[..., 1])) < 1e-10 * scale
+    assert np.max(np.abs(stats[..., 3] - ref[..., 3])) < 1e-6
