@@ -34,9 +34,11 @@ p2 tuple) and theta bucket b, the logged ratio
 estimates the per-step contraction 1 - K0 lambda_eff of that class.  The
 multiplier that would remove it in one step in the linear model is
 m* = 1/(1 - r); it is clamped to [M_LO, M_HI] (M_HI is the largest uniform
-multiplier that kept plain FA-SD stable on the synthetic fields), and the
-loss is the weighted mean square error of log m against log m*, with
-weight |D^_k|^2 normalised per bucket.
+multiplier that kept plain FA-SD stable on the synthetic fields).  The
+linear model holds only once the step is small: in buckets with
+theta >= THETA_LINEAR the target is the plain filter, m* = 1.  The loss is
+the weighted mean square error of log m against log m*, with weight
+|D^_k|^2 normalised per bucket.
 """
 
 from __future__ import annotations
@@ -51,6 +53,7 @@ OFF_W4, OFF_B4 = 8768, 8832
 NPARAM = 8833
 ITER_SCALE = 10000.0
 M_LO, M_HI = 0.25, 1.25
+THETA_LINEAR = 1e-4
 
 
 def unpack(p: np.ndarray):
@@ -153,9 +156,13 @@ def loss_and_grad(p: np.ndarray, X: np.ndarray, Y: np.ndarray, Wt: np.ndarray):
     return loss, pack(gW1, gb1, gW2, gb2, gW3, gb3, gw4, gb4)
 
 
-def targets_from_stats(num: np.ndarray, den: np.ndarray) -> np.ndarray:
-    """log m* = log clamp(1/(1 - r), M_LO, M_HI) with r = num/den (den > 0 entries only)."""
+def targets_from_stats(num: np.ndarray, den: np.ndarray, bucket=None) -> np.ndarray:
+    """log m* = log clamp(1/(1 - r), M_LO, M_HI) with r = num/den (den > 0 entries only);
+    0 (the plain filter) where bucket(theta) >= log10(THETA_LINEAR)."""
     r = num / den
     with np.errstate(divide="ignore"):
         m = np.where(r < 1.0, 1.0 / (1.0 - r), M_HI)
-    return np.log(np.clip(m, M_LO, M_HI))
+    y = np.log(np.clip(m, M_LO, M_HI))
+    if bucket is not None:
+        y = np.where(np.asarray(bucket) < np.log10(THETA_LINEAR), y, 0.0)
+    return y

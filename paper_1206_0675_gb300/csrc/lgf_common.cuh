@@ -112,6 +112,20 @@ template <typename R, int ROWS> struct MatField {
   }
 };
 
+// Division by a run-time constant d >= 1 through a multiply-high and a shift
+// (valid for 0 <= n < 2^31): q = (umulhi(n, m) + n) >> s with s = ceil(log2 d)
+// and m = floor(2^32 (2^s - d) / d) + 1.
+struct FastDiv {
+  uint32_t d, m, s;
+  static FastDiv make(uint32_t d) {
+    uint32_t s = 0;
+    while ((1ull << s) < d) ++s;
+    const uint64_t m = ((1ull << 32) * ((1ull << s) - d)) / d + 1;
+    return FastDiv{d, (uint32_t)m, s};
+  }
+  __device__ __forceinline__ uint32_t div(uint32_t n) const { return (__umulhi(n, m) + n) >> s; }
+};
+
 // Lattice geometry passed by value to every kernel.
 struct Geom {
   int L[4];        // Lx, Ly, Lz, Lt

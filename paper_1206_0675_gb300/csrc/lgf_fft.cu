@@ -108,19 +108,25 @@ template <typename R, int SIGN> struct DFT<R, 8, SIGN> {
 // its elements are es apart.
 struct Lines {
   int nlines, inner, inner_stride, outer_stride, es;
+  FastDiv dn, di;  // divisors by nlines and inner
 };
 
+static Lines make_lines(int nlines, int inner, int inner_stride, int outer_stride, int es) {
+  return Lines{nlines, inner, inner_stride, outer_stride, es, FastDiv::make(nlines), FastDiv::make(inner)};
+}
+
 template <typename R, int RAD, int SIGN, bool DIT>
-__device__ __forceinline__ void ct_stage(C2<R>* __restrict__ tile, const Lines ln, const int N, const int Ns,
+__device__ __forceinline__ void ct_stage(C2<R>* __restrict__ tile, const Lines& ln, const int N, const FastDiv fns,
                                          const C2<R>* __restrict__ tw) {
+  const int Ns = (int)fns.d;
   const int nbl = N / RAD;
   const int NB = ln.nlines * nbl;
-  const int tws = N / (Ns * RAD);
+  const int tws = nbl / Ns;
   for (int b = threadIdx.x; b < NB; b += blockDim.x) {
-    const int l = b % ln.nlines, q = b / ln.nlines;
-    const int j = q % Ns, grp = q / Ns;
-    const int base = (l / ln.inner) * ln.outer_stride + (l % ln.inner) * ln.inner_stride +
-                     (grp * Ns * RAD + j) * ln.es;
+    const int q = (int)ln.dn.div((uint32_t)b), l = b - q * ln.nlines;
+    const int grp = (int)fns.div((uint32_t)q), j = q - grp * Ns;
+    const int lo = (int)ln.di.div((uint32_t)l), li = l - lo * ln.inner;
+    const int base = lo * ln.outer_stride + li * ln.inner_stride + (grp * Ns * RAD + j) * ln.es;
     const int step = Ns * ln.es;
     C2<R> v[RAD];
 #pragma unroll
@@ -147,31 +153,24 @@ __device__ __forceinline__ void ct_stage(C2<R>* __restrict__ tile, const Lines l
 }
 
 template <typename R, int SIGN, bool DIT>
-__device__ __forceinline__ void ct_stage_any(C2<R>* tile, const Lines ln, int N, int Ns, int rad, const C2<R>* tw) {
-  if (rad == 8) ct_stage<R, 8, SIGN, DIT>(tile, ln, N, Ns, tw);
-  else if (rad == 4) ct_stage<R, 4, SIGN, DIT>(tile, ln, N, Ns, tw);
-  else if (rad == 3) ct_stage<R, 3, SIGN, DIT>(tile, ln, N, Ns, tw);
-  else ct_stage<R, 2, SIGN, DIT>(tile, ln, N, Ns, tw);
+__device__ __forceinline__ void ct_stage_any(C2<R>* tile, const Lines& ln, int N, const FastDiv& fns, int rad,
+                                             const C2<R>* tw) {
+  if (rad == 8) ct_stage<R, 8, SIGN, DIT>(tile, ln, N, fns, tw);
+  else if (rad == 4) ct_stage<R, 4, SIGN, DIT>(tile, ln, N, fns, tw);
+  else if (rad == 3) ct_stage<R, 3, SIGN, DIT>(tile, ln, N, fns, tw);
+  else ct_stage<R, 2, SIGN, DIT>(tile, ln, N, fns, tw);
 }
 
 // DFT of every line: input digit-reversed, output natural.
 template <typename R, int SIGN>
-__device__ __forceinline__ void fft_lines_dit(C2<R>* tile, const Lines ln, const FFTDir& d, const C2<R>* tw) {
-  int Ns = 1;
-  for (int st = 0; st < d.nst; ++st) {
-    ct_stage_any<R, SIGN, true>(tile, ln, d.N, Ns, d.radix[st], tw);
-    Ns *= d.radix[st];
-  }
+__device__ __forceinline__ void fft_lines_dit(C2<R>* tile, const Lines& ln, const FFTDir& d, const C2<R>* tw) {
+  for (int st = 0; st < d.nst; ++st) ct_stage_any<R, SIGN, true>(tile, ln, d.N, d.ns[st], d.radix[st], tw);
 }
 
 // DFT of every line: input natural, output digit-reversed.
 template <typename R, int SIGN>
-__device__ __forceinline__ void fft_lines_dif(C2<R>* tile, const Lines ln, const FFTDir& d, const C2<R>* tw) {
-  int Ns = d.N;
-  for (int st = d.nst - 1; st >= 0; --st) {
-    Ns /= d.radix[st];
-    ct_stage_any<R, SIGN, false>(tile, ln, d.N, Ns, d.radix[st], tw);
-  }
+__device__ __forceinline__ void fft_lines_dif(C2<R>* tile, const Lines& ln, const FFTDir& d, const C2<R>* tw) {
+  for (int st = d.nst - 1; st >= 0; --st) ct_stage_any<R, SIGN, false>(tile, ln, d.N, d.ns[st], d.radix[st], tw);
 }
 
 // ---------------------------------------------------------------------------
@@ -205,9 +204,14 @@ template <typename R> __host__ __device__ inline size_t smem_header_bytes(int n0
 // planes, C).
 // ---------------------------------------------------------------------------
 
+// Divisors of the global <-> shared copies of a pass.
+struct CopyDiv {
+  FastDiv a, b;
+};
+
 template <typename R, int SIGN>
 __global__ void __launch_bounds__(512) fft_xy_kernel(Geom g, FFTDir dx, FFTDir dy, C2<R>* __restrict__ data, const C2<R>* __restrict__ twg,
-                              const short* __restrict__ posg, int fpb) {
+                              const short* __restrict__ posg, int fpb, Lines lx, Lines ly, CopyDiv cd) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int Lx = g.L[0], Ly = g.L[1];
   C2<R>* tw;
@@ -219,14 +223,14 @@ __global__ void __launch_bounds__(512) fft_xy_kernel(Geom g, FFTDir dx, FFTDir d
   const int plane = Lx * Ly;
   __syncthreads();
   for (int i = threadIdx.x; i < fpb * plane; i += blockDim.x) {
-    const int f = i / plane, r = i - f * plane, y = r / Lx, x = r - y * Lx;
+    const int f = (int)cd.a.div((uint32_t)i), r = i - f * plane, y = (int)cd.b.div((uint32_t)r), x = r - y * Lx;
     tile[f * PS + pos[Lx + y] * RS + pos[x]] = data[(int64_t)(f0 + f) * g.V + slab * plane + r];
   }
   __syncthreads();
-  fft_lines_dit<R, SIGN>(tile, Lines{fpb * Ly, fpb * Ly, RS, 0, 1}, dx, tw);
-  fft_lines_dit<R, SIGN>(tile, Lines{fpb * Lx, Lx, 1, PS, RS}, dy, tw + Lx);
+  fft_lines_dit<R, SIGN>(tile, lx, dx, tw);
+  fft_lines_dit<R, SIGN>(tile, ly, dy, tw + Lx);
   for (int i = threadIdx.x; i < fpb * plane; i += blockDim.x) {
-    const int f = i / plane, r = i - f * plane, y = r / Lx, x = r - y * Lx;
+    const int f = (int)cd.a.div((uint32_t)i), r = i - f * plane, y = (int)cd.b.div((uint32_t)r), x = r - y * Lx;
     data[(int64_t)(f0 + f) * g.V + slab * plane + r] = tile[f * PS + y * RS + x];
   }
 }
@@ -239,7 +243,7 @@ template <typename R>
 __global__ void __launch_bounds__(512) fft_zt_filter_kernel(Geom g, FFTDir dz, FFTDir dt, C2<R>* __restrict__ data,
                                      const C2<R>* __restrict__ twg, const short* __restrict__ posg,
                                      const R* __restrict__ K, int xc, int mode, const float* __restrict__ mtab,
-                                     int4 H, const int* __restrict__ use_m) {
+                                     int4 H, const int* __restrict__ use_m, Lines lz, Lines lt, CopyDiv cd) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int Lx = g.L[0], Ly = g.L[1], Lz = g.L[2], Lt = g.L[3];
   C2<R>* tw;
@@ -253,13 +257,14 @@ __global__ void __launch_bounds__(512) fft_zt_filter_kernel(Geom g, FFTDir dz, F
   const int64_t sxy = (int64_t)y * Lx + x0;
   const int64_t plane = (int64_t)Lx * Ly;
   __syncthreads();
+#define LGF_ZT_IDX(i)                                                       \
+  const int zt = (int)cd.a.div((uint32_t)(i)), xi = (i) - zt * xc;          \
+  const int t = (int)cd.b.div((uint32_t)zt), z = zt - t * Lz;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const int xi = i % xc, zt = i / xc, z = zt % Lz, t = zt / Lz;
+    LGF_ZT_IDX(i)
     tile[pos[Lz + t] * TS + pos[z] * xc + xi] = fld[(int64_t)zt * plane + sxy + xi];
   }
   __syncthreads();
-  const Lines lz{Lt * xc, xc, 1, TS, xc};
-  const Lines lt{Lz * xc, Lz * xc, 1, 0, TS};
   if (mode == 0) {
     fft_lines_dit<R, -1>(tile, lz, dz, tw);
     fft_lines_dit<R, -1>(tile, lt, dt, tw + Lz);
@@ -267,7 +272,7 @@ __global__ void __launch_bounds__(512) fft_zt_filter_kernel(Geom g, FFTDir dz, F
     const bool learned = mtab != nullptr && *use_m != 0;
     const int fy = min(y, Ly - y);
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const int xi = i % xc, zt = i / xc, z = zt % Lz, t = zt / Lz;
+      LGF_ZT_IDX(i)
       R k = __ldg(&K[(int64_t)zt * plane + sxy + xi]);
       if (learned) {
         const int kx = x0 + xi;
@@ -281,7 +286,7 @@ __global__ void __launch_bounds__(512) fft_zt_filter_kernel(Geom g, FFTDir dz, F
     fft_lines_dif<R, +1>(tile, lt, dt, tw + Lz);
     fft_lines_dif<R, +1>(tile, lz, dz, tw);
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const int xi = i % xc, zt = i / xc, z = zt % Lz, t = zt / Lz;
+      LGF_ZT_IDX(i)
       fld[(int64_t)zt * plane + sxy + xi] = tile[pos[Lz + t] * TS + pos[z] * xc + xi];
     }
   } else {
@@ -293,10 +298,11 @@ __global__ void __launch_bounds__(512) fft_zt_filter_kernel(Geom g, FFTDir dz, F
       fft_lines_dit<R, +1>(tile, lt, dt, tw + Lz);
     }
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const int xi = i % xc, zt = i / xc, z = zt % Lz, t = zt / Lz;
+      LGF_ZT_IDX(i)
       fld[(int64_t)zt * plane + sxy + xi] = tile[t * TS + z * xc + xi];
     }
   }
+#undef LGF_ZT_IDX
 }
 
 // ---------------------------------------------------------------------------
@@ -333,14 +339,31 @@ __device__ __forceinline__ void gauge_from_packed(double2 f0, double2 f1, double
 template <typename RG, int GROWS>
 __device__ __forceinline__ void store_gauge(int64_t V, int64_t s, const double2 u[3], const double2 v[3],
                                             C2<RG>* __restrict__ gf, C2<RG>* __restrict__ Gf) {
-  double2 w[3];
-  const bool need_w = (GROWS == 3) || (Gf != nullptr);
-  if (need_w) su3_third_row<double>(u, v, w);
+  // rows 1-2 in the storage precision; row 3 = (a x b)^* in FP64 when g is
+  // stored in FP64, otherwise from the rounded rows in the storage precision
+  // (a 12-real FP32 update rebuilds it the same way)
+  C2<RG> a[3], b[3], c[3];
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    gf[(0 * 3 + c) * V + s] = ccast<RG, double>(u[c]);
-    gf[(1 * 3 + c) * V + s] = ccast<RG, double>(v[c]);
-    if (GROWS == 3) gf[(2 * 3 + c) * V + s] = ccast<RG, double>(w[c]);
+  for (int j = 0; j < 3; ++j) {
+    a[j] = ccast<RG, double>(u[j]);
+    b[j] = ccast<RG, double>(v[j]);
+  }
+  const bool need_c = (GROWS == 3) || (Gf != nullptr);
+  if (need_c) {
+    if (sizeof(RG) == sizeof(double)) {
+      double2 w[3];
+      su3_third_row<double>(u, v, w);
+#pragma unroll
+      for (int j = 0; j < 3; ++j) c[j] = ccast<RG, double>(w[j]);
+    } else {
+      su3_third_row<RG>(a, b, c);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    gf[(0 * 3 + j) * V + s] = a[j];
+    gf[(1 * 3 + j) * V + s] = b[j];
+    if (GROWS == 3) gf[(2 * 3 + j) * V + s] = c[j];
   }
   if (Gf != nullptr) {
     // G <- g G (full 3x3, precision RG)
@@ -348,28 +371,25 @@ __device__ __forceinline__ void store_gauge(int64_t V, int64_t s, const double2 
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
-      for (int c = 0; c < 3; ++c) Go[r][c] = Gf[(r * 3 + c) * V + s];
-    const double2* rows[3] = {u, v, w};
+      for (int col = 0; col < 3; ++col) Go[r][col] = Gf[(r * 3 + col) * V + s];
+    const C2<RG>* rows[3] = {a, b, c};
 #pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      C2<RG> gr[3];
+    for (int r = 0; r < 3; ++r)
 #pragma unroll
-      for (int k = 0; k < 3; ++k) gr[k] = ccast<RG, double>(rows[r][k]);
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        C2<RG> acc = cmul<RG>(gr[0], Go[0][c]);
-        acc = cfma<RG>(gr[1], Go[1][c], acc);
-        acc = cfma<RG>(gr[2], Go[2][c], acc);
-        Gf[(r * 3 + c) * V + s] = acc;
+      for (int col = 0; col < 3; ++col) {
+        C2<RG> acc = cmul<RG>(rows[r][0], Go[0][col]);
+        acc = cfma<RG>(rows[r][1], Go[1][col], acc);
+        acc = cfma<RG>(rows[r][2], Go[2][col], acc);
+        Gf[(r * 3 + col) * V + s] = acc;
       }
-    }
   }
 }
 
 template <typename R, typename RG, int GROWS>
 __global__ void __launch_bounds__(512) fft_xy_inv_gauge_kernel(Geom g, FFTDir dx, FFTDir dy, const C2<R>* __restrict__ data,
                                         const C2<R>* __restrict__ twg, const short* __restrict__ posg,
-                                        C2<RG>* __restrict__ gf, C2<RG>* __restrict__ Gf) {
+                                        C2<RG>* __restrict__ gf, C2<RG>* __restrict__ Gf, Lines lx, Lines ly,
+                                        CopyDiv cd) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int Lx = g.L[0], Ly = g.L[1];
   C2<R>* tw;
@@ -379,14 +399,14 @@ __global__ void __launch_bounds__(512) fft_xy_inv_gauge_kernel(Geom g, FFTDir dx
   const int64_t slab = blockIdx.x;
   const int plane = Lx * Ly;
   for (int i = threadIdx.x; i < 4 * plane; i += blockDim.x) {
-    const int f = i / plane, r = i - f * plane, y = r / Lx, x = r - y * Lx;
+    const int f = (int)cd.a.div((uint32_t)i), r = i - f * plane, y = (int)cd.b.div((uint32_t)r), x = r - y * Lx;
     tile[f * PS + y * RS + x] = data[(int64_t)f * g.V + slab * plane + r];
   }
   __syncthreads();
-  fft_lines_dif<R, +1>(tile, Lines{4 * Ly, 4 * Ly, RS, 0, 1}, dx, tw);
-  fft_lines_dif<R, +1>(tile, Lines{4 * Lx, Lx, 1, PS, RS}, dy, tw + Lx);
+  fft_lines_dif<R, +1>(tile, lx, dx, tw);
+  fft_lines_dif<R, +1>(tile, ly, dy, tw + Lx);
   for (int i = threadIdx.x; i < plane; i += blockDim.x) {
-    const int y = i / Lx, x = i - y * Lx;
+    const int y = (int)cd.b.div((uint32_t)i), x = i - y * Lx;
     const int o = pos[Lx + y] * RS + pos[x];
     double2 u[3], v[3];
     gauge_from_packed(ccast<double, R>(tile[o]), ccast<double, R>(tile[PS + o]), ccast<double, R>(tile[2 * PS + o]),
@@ -455,6 +475,11 @@ cudaError_t configure_fft_plan(const int L[4], int real_bytes, FFTPlan* p) {
     p->d[mu].N = L[mu];
     p->d[mu].nst = radix_schedule(L[mu], p->d[mu].radix);
     if (p->d[mu].nst < 0) return cudaErrorInvalidValue;
+    int Ns = 1;
+    for (int st = 0; st < p->d[mu].nst; ++st) {
+      p->d[mu].ns[st] = FastDiv::make((uint32_t)Ns);
+      Ns *= p->d[mu].radix[st];
+    }
   }
   const int Lx = L[0], Ly = L[1], Lz = L[2], Lt = L[3];
   const size_t hxy = (size_t)((Lx + Ly + 1) & ~1) * cb + (size_t)((Lx + Ly + 7) & ~7) * 2;
@@ -495,13 +520,16 @@ cudaError_t launch_fft_xy(const Geom& g, const FFTPlan& p, C2<R>* data, const C2
   const int thr = threads_for(fpb * g.L[0] * g.L[1]);
   const size_t smem = smem_header_bytes<R>(g.L[0], g.L[1]) + (size_t)fpb * g.L[1] * (g.L[0] + 1) * sizeof(C2<R>);
   dim3 grid((unsigned)(g.L[2] * g.L[3]), (unsigned)(nfields / fpb));
+  const int Lx = g.L[0], Ly = g.L[1], RS = Lx + 1, PS = Ly * RS;
+  const Lines lx = make_lines(fpb * Ly, fpb * Ly, RS, 0, 1), ly = make_lines(fpb * Lx, Lx, 1, PS, RS);
+  const CopyDiv cd{FastDiv::make((uint32_t)(Lx * Ly)), FastDiv::make((uint32_t)Lx)};
   cudaError_t e;
   if (sign < 0) {
     if ((e = allow_smem(fft_xy_kernel<R, -1>, smem)) != cudaSuccess) return e;
-    fft_xy_kernel<R, -1><<<grid, thr, smem, s>>>(g, p.d[0], p.d[1], data, tw, pos, fpb);
+    fft_xy_kernel<R, -1><<<grid, thr, smem, s>>>(g, p.d[0], p.d[1], data, tw, pos, fpb, lx, ly, cd);
   } else {
     if ((e = allow_smem(fft_xy_kernel<R, +1>, smem)) != cudaSuccess) return e;
-    fft_xy_kernel<R, +1><<<grid, thr, smem, s>>>(g, p.d[0], p.d[1], data, tw, pos, fpb);
+    fft_xy_kernel<R, +1><<<grid, thr, smem, s>>>(g, p.d[0], p.d[1], data, tw, pos, fpb, lx, ly, cd);
   }
   return cudaGetLastError();
 }
@@ -514,8 +542,11 @@ cudaError_t launch_fft_zt(const Geom& g, const FFTPlan& p, C2<R>* data, const C2
   cudaError_t e = allow_smem(fft_zt_filter_kernel<R>, smem);
   if (e != cudaSuccess) return e;
   const int4 H = make_int4(g.L[0] / 2 + 1, g.L[1] / 2 + 1, g.L[2] / 2 + 1, g.L[3] / 2 + 1);
+  const int xc = p.xc, Lz = g.L[2], Lt = g.L[3], TS = Lz * xc + 1;
+  const Lines lz = make_lines(Lt * xc, xc, 1, TS, xc), lt = make_lines(Lz * xc, Lz * xc, 1, 0, TS);
+  const CopyDiv cd{FastDiv::make((uint32_t)xc), FastDiv::make((uint32_t)Lz)};
   fft_zt_filter_kernel<R><<<grid, p.threads_zt, smem, s>>>(g, p.d[2], p.d[3], data, tw, pos, K, p.xc, mode, mtab, H,
-                                                           use_m);
+                                                           use_m, lz, lt, cd);
   return cudaGetLastError();
 }
 
@@ -530,8 +561,11 @@ cudaError_t launch_fft_xy_inv_gauge(const Geom& g, const FFTPlan& p, C2<R>* data
   }
   const size_t smem = p.smem_c;
   if ((e = allow_smem(fft_xy_inv_gauge_kernel<R, RG, GROWS>, smem)) != cudaSuccess) return e;
+  const int Lx = g.L[0], Ly = g.L[1], RS = Lx + 1, PS = Ly * RS;
+  const Lines lx = make_lines(4 * Ly, 4 * Ly, RS, 0, 1), ly = make_lines(4 * Lx, Lx, 1, PS, RS);
+  const CopyDiv cd{FastDiv::make((uint32_t)(Lx * Ly)), FastDiv::make((uint32_t)Lx)};
   fft_xy_inv_gauge_kernel<R, RG, GROWS><<<(unsigned)(g.L[2] * g.L[3]), p.threads_c, smem, s>>>(
-      g, p.d[0], p.d[1], data, tw, pos, gfield, Gfield);
+      g, p.d[0], p.d[1], data, tw, pos, gfield, Gfield, lx, ly, cd);
   return cudaGetLastError();
 }
 

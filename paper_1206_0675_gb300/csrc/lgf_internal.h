@@ -106,6 +106,7 @@ struct FFTDir {
   int N;
   int nst;
   int radix[8];
+  FastDiv ns[8];  // divisors by the span Ns = radix[0] ... radix[st-1] of each stage
 };
 
 struct FFTPlan {

@@ -21,6 +21,29 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+template <typename R> __device__ __forceinline__ R warp_sum_r(R v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block sum of per-thread values given as warp sums already formed in
+// precision R (lane 0 of each warp holds its warp's sum); the sum over warps
+// is in FP64 and fixed order.  Result valid in thread 0.
+template <typename R> __device__ __forceinline__ void block_sum2_warps(R wa, R wb, double& a, double& b) {
+  __shared__ double sa[32], sb[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  if (lane == 0) { sa[warp] = (double)wa; sb[warp] = (double)wb; }
+  __syncthreads();
+  if (warp == 0) {
+    a = lane < nw ? sa[lane] : 0.0;
+    b = lane < nw ? sb[lane] : 0.0;
+    a = warp_sum(a);
+    b = warp_sum(b);
+  }
+  __syncthreads();
+}
+
 // Block sum of two values in a fixed order; result valid in thread 0.
 __device__ __forceinline__ void block_sum2(double& a, double& b) {
   __shared__ double sa[32], sb[32];
@@ -44,7 +67,9 @@ measure_kernel(Geom g, MatField<R, ROWS> U, C2<R>* __restrict__ delta, double* _
                DevState* __restrict__ st, int count_iter, unsigned long long cond, int use_cond, int only_if_revert) {
   if (only_if_revert && !st->revert) return;
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  double fsum = 0.0, tsum = 0.0;
+  // per-site sums in the link precision; warp sums likewise, everything
+  // beyond a warp in FP64
+  R fsum = 0, tsum = 0;
   if (s < g.V) {
     int c[4];
     site_coords(g, s, c);
@@ -56,7 +81,7 @@ measure_kernel(Geom g, MatField<R, ROWS> U, C2<R>* __restrict__ delta, double* _
     for (int mu = 0; mu < 4; ++mu) {
       M3<R> u;
       U.load_ro(mu, s, u);
-      fsum += (double)u.e[0][0].x + (double)u.e[1][1].x + (double)u.e[2][2].x;
+      fsum += u.e[0][0].x + u.e[1][1].x + u.e[2][2].x;
       im0 -= u.e[0][0].y; im1 -= u.e[1][1].y; im2 -= u.e[2][2].y;
       w01 = csub<R>(w01, csub<R>(u.e[0][1], cconj<R>(u.e[1][0])));
       w02 = csub<R>(w02, csub<R>(u.e[0][2], cconj<R>(u.e[2][0])));
@@ -75,17 +100,16 @@ measure_kernel(Geom g, MatField<R, ROWS> U, C2<R>* __restrict__ delta, double* _
     delta[g.V + s] = d01;
     delta[2 * g.V + s] = d02;
     delta[3 * g.V + s] = d12;
-    // ||Delta_A||_F^2 in FP64
-    const double da0 = a0, da1 = a1, da2 = a2;
-    tsum = da0 * da0 + da1 * da1 + da2 * da2 +
-           2.0 * ((double)d01.x * d01.x + (double)d01.y * d01.y + (double)d02.x * d02.x + (double)d02.y * d02.y +
-                  (double)d12.x * d12.x + (double)d12.y * d12.y);
+    // ||Delta_A||_F^2
+    tsum = a0 * a0 + a1 * a1 + a2 * a2 +
+           (R)2 * (d01.x * d01.x + d01.y * d01.y + d02.x * d02.x + d02.y * d02.y + d12.x * d12.x + d12.y * d12.y);
   }
-  block_sum2(fsum, tsum);
+  double fb, tb;
+  block_sum2_warps<R>(warp_sum_r<R>(fsum), warp_sum_r<R>(tsum), fb, tb);
   __shared__ int is_last;
   if (threadIdx.x == 0) {
-    partials[2 * blockIdx.x] = fsum;
-    partials[2 * blockIdx.x + 1] = tsum;
+    partials[2 * blockIdx.x] = fb;
+    partials[2 * blockIdx.x + 1] = tb;
     __threadfence();
     const unsigned int t = atomicAdd(&st->ticket, 1u);
     is_last = (t == gridDim.x - 1);

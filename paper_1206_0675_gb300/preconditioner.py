@@ -11,9 +11,13 @@ and momentum class c the log gives
 contraction of that class under the plain filter.  The training target is
 the multiplier that would remove it in one step in a linear model,
 m* = 1/(1 - r), clamped to [0.25, 1.25] (1.25 is the largest uniform
-multiplier that kept plain FA-SD stable on these fields); the loss is the
-mean square error of log m, weighted by |D^_k|^2 normalised within each
-(configuration, bucket).
+multiplier that kept plain FA-SD stable on these fields).  The linear model
+holds only once the gauge transformations are small: for theta >= 1e-4
+(the first, non-linear part of every trajectory, where a uniformly larger
+step was measured to slow fast-converging fields) the target is the plain
+filter, m* = 1.  Buckets below theta = 1e-15 (rounding noise) are left out.
+The loss is the mean square error of log m, weighted by |D^_k|^2
+normalised within each (configuration, bucket).
 
 Features (identical to the ones the inference kernel builds):
     (p2_x/4, p2_y/4, p2_z/4, p2_t/4, -bucket/16, iter_frac)
@@ -40,6 +44,7 @@ from . import fields, lgf
 HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_WEIGHTS = os.path.join(HERE, "preconditioner_bf16.npy")
 M_LO, M_HI = 0.25, 1.25
+THETA_LINEAR = 1e-4
 NPARAM = lgf.LGF_MLP_NPARAM
 
 
@@ -51,35 +56,41 @@ def class_p2(extents) -> np.ndarray:
     return np.stack([tabs[0][fx], tabs[1][fy], tabs[2][fz], tabs[3][ft]], -1).reshape(-1, 4)
 
 
+def targets(r: np.ndarray, bucket: np.ndarray) -> np.ndarray:
+    """log m*: log clamp(1/(1 - r), M_LO, M_HI) where the linear model holds, else 0."""
+    m = np.where(r < 1.0, 1.0 / np.maximum(1.0 - r, 1e-12), M_HI)
+    y = np.log(np.clip(m, M_LO, M_HI))
+    return np.where(bucket < np.log10(THETA_LINEAR), y, 0.0)
+
+
 def samples_from_log(extents, stats: np.ndarray, rng: np.random.Generator, per_bucket: int = 256):
-    """(X, y, w) training rows from one configuration's mode log [bucket][class][4]."""
+    """(X, r, w) rows from one configuration's mode log [bucket][class][4]: features,
+    logged contraction ratio and weight.  Buckets below theta = 1e-15 are left out."""
     p2 = class_p2(extents)
-    X, Y, W = [], [], []
+    X, Rr, W = [], [], []
     for b in range(stats.shape[0]):
+        if (4 - b) / 2.0 < -15.0:
+            continue
         num, den, cnt, itf = stats[b].T
         ok = np.nonzero((cnt > 0) & (den > 0))[0]
         if ok.size == 0:
             continue
         if ok.size > per_bucket:
             ok = rng.choice(ok, per_bucket, replace=False)
-        r = num[ok] / den[ok]
-        m = np.where(r < 1.0, 1.0 / np.maximum(1.0 - r, 1e-12), M_HI)
-        y = np.log(np.clip(m, M_LO, M_HI))
         bucket = (4 - b) / 2.0
         x = np.empty((ok.size, 6))
         x[:, :4] = p2[ok] / 4.0
         x[:, 4] = -bucket / 16.0
         x[:, 5] = np.minimum(itf[ok] / cnt[ok], 1.0)
-        w = den[ok] / den[ok].sum()
         X.append(x)
-        Y.append(y)
-        W.append(w)
+        Rr.append(num[ok] / den[ok])
+        W.append(den[ok] / den[ok].sum())
     if not X:
         return np.zeros((0, 6)), np.zeros(0), np.zeros(0)
-    return np.concatenate(X), np.concatenate(Y), np.concatenate(W)
+    return np.concatenate(X), np.concatenate(Rr), np.concatenate(W)
 
 
-def collect(extents, eps: float, seed: int, tol: float = 1e-14, max_iter: int = 6000, check_every: int = 25):
+def collect(extents, eps: float, seed: int, tol: float = 1e-15, max_iter: int = 6000):
     """Plain FP64 trajectory with the mode log on; returns (stats, iterations, theta)."""
     U = fields.random_links(extents, eps, seed)
     with lgf.Lattice(extents, "fp64") as lat:
@@ -88,9 +99,10 @@ def collect(extents, eps: float, seed: int, tol: float = 1e-14, max_iter: int = 
         k = 0
         F, th = lat.measure()
         while th >= tol and k < max_iter:
-            for _ in range(check_every):
+            n = 25 if th > 1e-9 else 2
+            for _ in range(n):
                 lat.step(0.08)
-            k += check_every
+            k += n
             F, th = lat.measure()
         return lat.get_mode_log(), k, th
 
@@ -140,6 +152,8 @@ def main():
     ap.add_argument("--out", default=DEFAULT_WEIGHTS)
     ap.add_argument("--seed0", type=int, default=1000)
     ap.add_argument("--per-bucket", type=int, default=256)
+    ap.add_argument("--save-data", default=None, help="also write the training rows to this .npz file")
+    ap.add_argument("--from-data", default=None, help="train on rows saved by --save-data instead of collecting")
     args = ap.parse_args()
     import torch
     assert torch.cuda.is_available()
@@ -147,6 +161,10 @@ def main():
     rng = np.random.Generator(np.random.Philox(key=args.seed0))
     Xs, Ys, Ws, meta = [], [], [], []
     t_start = time.time()
+    if args.from_data:
+        d = np.load(args.from_data)
+        Xs, Ys, Ws = [d["X"].astype(np.float64)], [d["R"].astype(np.float64)], [d["W"].astype(np.float64)]
+        args.configs = 0
     for i in range(args.configs):
         ext = (16,) * 4 if i % 2 == 0 else (24,) * 4
         seed = args.seed0 + i
@@ -160,8 +178,11 @@ def main():
         if i % 20 == 0:
             print(f"config {i}: L={ext[0]} eps={eps:.3f} iters={k} theta={th:.2e} samples={y.size} "
                   f"({time.time() - t_start:.0f} s)", flush=True)
-    X, Y, W = np.concatenate(Xs), np.concatenate(Ys), np.concatenate(Ws)
-    print(f"dataset: {Y.size} samples from {args.configs} configurations ({time.time() - t_start:.0f} s)", flush=True)
+    X, Rr, W = np.concatenate(Xs), np.concatenate(Ys), np.concatenate(Ws)
+    print(f"dataset: {Rr.size} samples from {len(meta)} configurations ({time.time() - t_start:.0f} s)", flush=True)
+    if args.save_data:
+        np.savez_compressed(args.save_data, X=X.astype(np.float32), R=Rr.astype(np.float32), W=W.astype(np.float32))
+    Y = targets(Rr, -16.0 * X[:, 4])
     P32, Pbf, hist, full = train(X, Y, W)
     np.save(args.out, Pbf)
     with open(os.path.splitext(args.out)[0] + ".json", "w") as f:

@@ -214,3 +214,31 @@ def test_mode_log_matches_oracle(torch):
     assert np.max(np.abs(stats[..., 0] - ref[..., 0])) < 1e-10 * scale
     assert np.max(np.abs(stats[..., 1] - ref[..., 1])) < 1e-10 * scale
     assert np.max(np.abs(stats[..., 3] - ref[..., 3])) < 1e-6
+
+
+def test_trained_preconditioner_gains_on_slow_fields(torch):
+    """The committed network (trained on 16^4 and 24^4 trajectories) against plain
+    FA-SD on held-out rough fields: fewer iterations to theta < 1e-12, same
+    gauge orbit (plaquette unchanged), every accepted step raising F."""
+    from paper_1206_0675_gb300.preconditioner import DEFAULT_WEIGHTS
+    weights = np.load(DEFAULT_WEIGHTS)
+    ext = (16, 16, 16, 16)
+    total_plain = total_learned = 0
+    for seed in (104, 105):
+        U = fields.random_links(ext, eps=1.0, seed=seed)
+        with lgf.Lattice(ext, "fp64") as lat:
+            lat.set_links(U)
+            it_p, F_p, th_p, conv_p = lat.fix(1e-12, 20000, 0.08)
+        with lgf.Lattice(ext, "fp64", learned=True) as lat:
+            lat.load_preconditioner(weights)
+            lat.set_links(U)
+            Fh, _ = lat.set_trace(20001)
+            it_l, F_l, th_l, conv_l = lat.fix(1e-12, 20000, 0.08)
+            U_l = lat.get_links()
+        assert conv_p and conv_l
+        assert np.all(np.diff(Fh[: it_l + 1]) >= 0)
+        assert abs(O.plaquette(U_l) - O.plaquette(U)) < 1e-12
+        total_plain += it_p
+        total_learned += it_l
+    print(f"iterations to 1e-12 on two held-out 16^4 eps=1 fields: plain {total_plain}, learned {total_learned}")
+    assert total_learned < 0.95 * total_plain

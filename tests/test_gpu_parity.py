@@ -66,7 +66,9 @@ def test_measure_parity_fp32(ext, store12):
         F, th = lat.measure()
         D = lat.get_divergence()
     Fo, tho, Do = O.measure(U)
-    assert rel(F, Fo) < 1e-6
+    # F is a mean of O(1) traces (here close to 0 for a gauge-rotated field),
+    # so its FP32 error is absolute
+    assert abs(F - Fo) < 1e-6
     assert rel(th, tho) < 1e-5
     assert np.max(np.abs(D - Do)) < 2e-6
 

@@ -63,3 +63,12 @@ def test_targets_and_features():
     x = M.features([[0.0, 4.0, 2.0, 1.0]], 3e-10, 2500)
     assert np.allclose(x, [[0.0, 1.0, 0.5, 0.25, 10.0 / 16.0, 0.25]])
     assert M.theta_bucket(1e-9) == -9.0 and M.theta_bucket(0.0) == -20.0
+
+
+def test_training_targets_match_the_oracle_definition():
+    from paper_1206_0675_gb300 import preconditioner as P
+    rng = np.random.default_rng(5)
+    r = rng.uniform(-3, 1.5, 2000)
+    bucket = rng.integers(-30, 5, 2000) / 2.0
+    assert np.allclose(P.targets(r, bucket), M.targets_from_stats(r, np.ones_like(r), bucket), atol=1e-12)
+    assert np.all(P.targets(r, np.full_like(r, -3.5)) == 0.0)
