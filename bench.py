@@ -304,9 +304,14 @@ def run_lgf(args, rank, world, local_rank):
     # ---- time to theta < 1e-15: plain FP64 vs mixed -------------------------
     ttt = None
     if not args.no_tol:
+        from paper_1206_0675_gb300.preconditioner import DEFAULT_WEIGHTS
+        weights = np.load(DEFAULT_WEIGHTS)
         ttt = {"tol": TOL, "field": f"32^4 eps={EPS} seed={rank}"}
-        for mode, kw in (("fp64_18", dict(precision="fp64")), ("mixed_12", dict(precision="mixed", store12=True))):
+        for mode, kw in (("fp64_18", dict(precision="fp64")), ("mixed_12", dict(precision="mixed", store12=True)),
+                         ("mixed_12_learned", dict(precision="mixed", store12=True, learned=True))):
             L2 = lgf.Lattice(EXT, **kw)
+            if kw.get("learned"):
+                L2.load_preconditioner(weights)
             L2.set_links(U)
             L2.fix(TOL, 1, ALPHA)           # builds the loop graph
             L2.set_links(U)
@@ -315,8 +320,33 @@ def run_lgf(args, rank, world, local_rank):
             it, F, th, conv = L2.fix(TOL, args.max_iter, ALPHA)
             torch.cuda.synchronize()
             ttt[mode] = {"seconds": time.perf_counter() - t0, "iters": it, "F": F, "theta": th, "converged": conv}
+            if kw.get("learned"):
+                ttt[mode]["fallbacks"] = L2.fallbacks()
             L2.close()
         ttt["speedup_mixed"] = ttt["fp64_18"]["seconds"] / ttt["mixed_12"]["seconds"]
+        ttt["speedup_mixed_learned"] = ttt["fp64_18"]["seconds"] / ttt["mixed_12_learned"]["seconds"]
+
+    # ---- 64 configurations of uneven shapes in one graph launch -------------
+    batch = None
+    if not args.no_batch:
+        exts = fields.BATCH64_EXTENTS
+        Ub = [fields.random_links(e, fields.batch_eps(i), 1000 * rank + i) for i, e in enumerate(exts)]
+        with lgf.Batch(exts) as b:
+            for i, u in enumerate(Ub):
+                b.set_links(i, u)
+            b.fix(1e-14, 1)            # builds the loop graph
+            for i, u in enumerate(Ub):
+                b.set_links(i, u)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            it_b, F_b, th_b, conv_b = b.fix(1e-14, 30000)
+            dt_b = time.perf_counter() - t0
+            classes = b.describe()
+        vols = np.array([int(np.prod(e)) for e in exts])
+        batch = {"configs": len(exts), "tol": 1e-14, "seconds": dt_b, "converged": bool(conv_b),
+                 "iters_total": int(it_b.sum()), "iters_max": int(it_b.max()),
+                 "site_updates_per_s": float((vols * it_b).sum() / dt_b), "classes": classes,
+                 "workload": "16x8^4, 16x12^4, 16x16^4, 8x16^3x32, 8x24^4; eps ~ U[0.3,1.0]; one graph launch"}
 
     # ---- CPU oracle on the host cores (rank 0, N = 1 only) ------------------
     cpu = None
@@ -335,7 +365,7 @@ def run_lgf(args, rank, world, local_rank):
                        "l2": "no flush needed: each step streams 604 MB of links (> 129 MB L2)"},
             "site_updates_per_s": value * V,
             "per_kernel": per_kernel, "roofline": roofline, "step_hbm": step_hbm, "fp32_12": fp32,
-            "time_to_tol": ttt, "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
+            "time_to_tol": ttt, "batch64": batch, "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
             "gpu_launches": 5 * args.steps,
             "paper_context": {"c2070_dp_ms_per_iter_12real_tex": 61.16, "c2070_dp_ms_per_iter_18real_tex": 100.65,
                               "note": "derived from the paper's Table 2 (real beta=5.8-6.2 configurations)"},
@@ -353,6 +383,7 @@ def main():
     ap.add_argument("--cpu-iters", type=int, default=3)
     ap.add_argument("--no-tol", action="store_true", help="skip the time-to-threshold runs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-configuration batch")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

@@ -179,18 +179,20 @@ lgf_status lgf_get_timing(lgf_handle h, double* ms, int32_t nkernels, int32_t* n
  *
  * With LGF_LEARNED every step multiplies the filter by m(k) in [0.25, 1.25],
  * predicted for each momentum class (modes with the same per-direction
- * p2_mu = 4 sin^2(pi k_mu / L_mu)) by a network 6 -> 64 -> 64 -> 64 -> 1
+ * p2_mu = 4 sin^2(pi k_mu / L_mu)) by a network 7 -> 64 -> 64 -> 64 -> 1
  * (ReLU hidden layers, m = softplus(z)) with BF16 weights and FP32
  * accumulation on the tensor cores.  Features of a mode:
- *   (p2_x/4, p2_y/4, p2_z/4, p2_t/4, -floor(2 log10 theta)/32, min(iter/10000, 1))
- * where theta and iter are those of the links the step starts from.  A step
- * that lowers F is undone and redone with the plain filter; theta (of the
- * plain definition) decides convergence.
+ *   (p2_x/4, p2_y/4, p2_z/4, p2_t/4, -floor(2 log10 theta)/32, min(iter/10000, 1),
+ *    clamp(log10(theta/theta_prev), -2, 1)/2)
+ * where theta and iter are those of the links the step starts from and
+ * theta_prev that of the links one step earlier (the last feature is 0 on the
+ * first step).  A step that lowers F is undone and redone with the plain
+ * filter; theta (of the plain definition) decides convergence.
  *
- * Parameter layout (8833 numbers, rows [out][in]):
- *   W1[64][6] @0, b1[64] @384, W2[64][64] @448, b2[64] @4544,
- *   W3[64][64] @4608, b3[64] @8704, w4[64] @8768, b4 @8832. */
-#define LGF_MLP_NPARAM 8833
+ * Parameter layout (8897 numbers, rows [out][in]):
+ *   W1[64][7] @0, b1[64] @448, W2[64][64] @512, b2[64] @4608,
+ *   W3[64][64] @4672, b3[64] @8768, w4[64] @8832, b4 @8896. */
+#define LGF_MLP_NPARAM 8897
 
 /* Load BF16 network parameters (n_w must be LGF_MLP_NPARAM) into the
  * handle; where = LGF_HOST or LGF_DEVICE.  Synchronises. */
@@ -202,32 +204,33 @@ lgf_status lgf_get_fallbacks(lgf_handle h, int32_t* n);
 
 /* Mode log (training data).  enable != 0 makes every subsequent lgf_step
  * also accumulate, for each theta bucket b and momentum class c, the sums
- *   Re<D^_{k+1}, D^_k>, |D^_k|^2, count, iteration fraction of step k
+ *   Re<D^_{k+1}, D^_k>, |D^_k|^2, count, iteration fraction of step k,
+ *   last-step contraction feature of step k
  * over the modes of the class, D^ being the 4D Fourier transform of the
  * packed divergence (b = clamp(4 - 2 floor(2 log10 theta_k)/2, 0, 39)).
  * Enabling clears the sums.  Synchronises. */
 lgf_status lgf_set_mode_log(lgf_handle h, int32_t enable);
 
-/* Copy the mode-log sums out: n must be 40 * nclass * 4 doubles, laid out
- * [b][c][4] with nclass = prod_mu (L_mu/2 + 1) and
+/* Copy the mode-log sums out: n must be 40 * nclass * 5 doubles, laid out
+ * [b][c][5] with nclass = prod_mu (L_mu/2 + 1) and
  * c = ((f_t H_z + f_z) H_y + f_y) H_x + f_x, f_mu = min(k_mu, L_mu - k_mu),
  * H_mu = L_mu/2 + 1.  out is a host pointer.  Synchronises. */
 lgf_status lgf_get_mode_log(lgf_handle h, double* out, int64_t n);
 
 /* Network inference on the tensor cores for arbitrary feature rows
- * (device pointers): X[n][6] FP32 features, P[8833] BF16 parameters,
+ * (device pointers): X[n][7] FP32 features, P[8897] BF16 parameters,
  * m[n] = softplus(z) FP32 out (unclamped).  Enqueued on cuda_stream. */
 lgf_status lgf_mlp_eval(const uint16_t* P, const float* X, int64_t n, float* m, void* cuda_stream);
 
 /* Loss L = (1/n) sum_i w_i (log m_i - y_i)^2 over all rows and its gradient
- * with respect to the FP32 parameters (device pointers: P[8833], X[n][6],
- * Y[n], W[n], grad[8833]); *loss on the host.  Synchronises. */
+ * with respect to the FP32 parameters (device pointers: P[8897], X[n][7],
+ * Y[n], W[n], grad[8897]); *loss on the host.  Synchronises. */
 lgf_status lgf_mlp_loss_grad(const float* P, const float* X, const float* Y, const float* W, int64_t n, float* grad,
                              double* loss, void* cuda_stream);
 
 /* Adam training of the FP32 parameters P (device, in place) on minibatches of
  * `batch` rows drawn by a counter-based hash of (seed, step, row): `steps`
- * updates with learning rate lr, moments in adam[2 * 8833] (device, zero for
+ * updates with learning rate lr, moments in adam[2 * 8897] (device, zero for
  * a fresh start), t0 = number of updates done before (bias correction).
  * loss_hist (host, may be NULL) receives the minibatch loss of every
  * update.  Synchronises. */
@@ -235,7 +238,7 @@ lgf_status lgf_mlp_train(float* P, float* adam, const float* X, const float* Y, 
                          int32_t batch, int32_t steps, float lr, uint64_t seed, int32_t t0, double* loss_hist,
                          void* cuda_stream);
 
-/* FP32 -> BF16 (round to nearest even) of the 8833 parameters (device). */
+/* FP32 -> BF16 (round to nearest even) of the 8897 parameters (device). */
 lgf_status lgf_mlp_to_bf16(const float* P, uint16_t* out, void* cuda_stream);
 
 /* Phase of an LGF_MIXED handle: 32 while in the FP32 phase, 64 after the
@@ -271,6 +274,43 @@ lgf_status lgf_get_phase(lgf_handle h, int32_t* bits);
  * Returns LGF_OK, LGF_E_ARG (NULL pointers), LGF_E_UNSUPPORTED or LGF_E_CUDA. */
 lgf_status lgf_measure_static(const int32_t extents[4], const double* U, double* D, double* F_theta,
                               void* cuda_stream);
+
+/* ---- batches of configurations (an addition; the paper fixes one at a time) ----
+ *
+ * Many configurations of possibly different lattice shapes fixed together,
+ * FP64 with 18-real links and the plain filter.  Configurations of the same
+ * shape share their kernel launches (one launch per step kernel per shape);
+ * lgf_batch_fix runs the whole fix as ONE CUDA graph launch whose WHILE loop
+ * continues while any configuration has theta >= tol and fewer than
+ * max_iter updates; a configuration retires (stops being updated) as soon as
+ * its own theta falls below tol.  Every kernel of a retired configuration
+ * returns immediately; no kernel waits on another.  The FFT tile shapes of
+ * each shape are chosen at creation by timing every candidate on the
+ * configurations' buffers (cached per process, and in the file named by the
+ * environment variable LGF_AUTOTUNE_CACHE when it is set). */
+typedef struct lgf_batch_ctx* lgf_batch;
+
+/* n configurations; extents: n*4 int32 ({Lx, Ly, Lz, Lt} of each, rules as
+ * in lgf_create).  prec must be LGF_FP64 and flags 0 (else
+ * LGF_E_UNSUPPORTED).  Allocates and autotunes.  Synchronises. */
+lgf_status lgf_batch_create(int32_t n, const int32_t* extents, lgf_precision prec, uint32_t flags, void* cuda_stream,
+                            lgf_batch* out);
+lgf_status lgf_batch_destroy(lgf_batch b);
+
+/* Links of configuration i (0 <= i < n) in the user layout of its own shape;
+ * validated like lgf_set_links.  Synchronises. */
+lgf_status lgf_batch_set_links(lgf_batch b, int32_t i, const double* U, int where);
+lgf_status lgf_batch_get_links(lgf_batch b, int32_t i, double* U, int where);
+
+/* Fix every configuration: iters, F, theta (each NULL or n entries) receive
+ * the per-configuration update counts and final measurements.
+ * LGF_E_NOTCONV if any configuration reached max_iter.  Synchronises. */
+lgf_status lgf_batch_fix(lgf_batch b, double theta_tol, int32_t max_iter, double alpha, int32_t* iters, double* F,
+                         double* theta);
+
+/* JSON description of the shape classes and their autotuned FFT tiles. */
+lgf_status lgf_batch_describe(lgf_batch b, char* buf, size_t len);
+const char* lgf_batch_last_error(lgf_batch b);
 
 /* Human-readable name of a status code (static string). */
 const char* lgf_status_string(lgf_status s);

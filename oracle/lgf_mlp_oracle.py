@@ -6,20 +6,22 @@ additions -- a per-mode multiplier m(k) applied on top of the
 Fourier-acceleration filter alpha p2max/p2(k) of Eq. (eq:gx), predicted by a
 small MLP and trained on statistics logged from plain FA-SD trajectories.
 
-Network (flat parameter vector, the library's layout, 8833 numbers)
+Network (flat parameter vector, the library's layout, 8897 numbers)
 -------------------------------------------------------------------
-    h1 = relu(W1 x + b1)      W1: [64][6]   offset 0,    b1: [64] offset 384
-    h2 = relu(W2 h1 + b2)     W2: [64][64]  offset 448,  b2: [64] offset 4544
-    h3 = relu(W3 h2 + b3)     W3: [64][64]  offset 4608, b3: [64] offset 8704
-    z  = w4 . h3 + b4         w4: [64]      offset 8768, b4: [1]  offset 8832
+    h1 = relu(W1 x + b1)      W1: [64][7]   offset 0,    b1: [64] offset 448
+    h2 = relu(W2 h1 + b2)     W2: [64][64]  offset 512,  b2: [64] offset 4608
+    h3 = relu(W3 h2 + b3)     W3: [64][64]  offset 4672, b3: [64] offset 8768
+    z  = w4 . h3 + b4         w4: [64]      offset 8832, b4: [1]  offset 8896
     m  = softplus(z) = log(1 + e^z)
 
 Features of a momentum mode k at iteration k_it with stopping quantity theta
 --------------------------------------------------------------------------
-    x = (p2_x/4, p2_y/4, p2_z/4, p2_t/4, -bucket(theta)/16, iter_frac)
+    x = (p2_x/4, p2_y/4, p2_z/4, p2_t/4, -bucket(theta)/16, iter_frac, rate)
     p2_mu = 4 sin^2(pi k_mu / L_mu)        (per direction, as in the filter)
     bucket(theta) = floor(2 log10 theta) / 2   (half decades; theta <= 0 -> -20)
     iter_frac = min(k_it / 10000, 1)
+    rate = clamp(log10(theta / theta_prev), -2, 1) / 2   (0 on the first step),
+           theta_prev being the stopping quantity one step earlier
 
 Inference on the GPU uses BF16 weights with FP32 accumulation: ``forward``
 with ``bf16=True`` emulates it (weights and the inputs of the three mma
@@ -45,12 +47,12 @@ from __future__ import annotations
 
 import numpy as np
 
-NIN, NH = 6, 64
-OFF_W1, OFF_B1 = 0, 384
-OFF_W2, OFF_B2 = 448, 4544
-OFF_W3, OFF_B3 = 4608, 8704
-OFF_W4, OFF_B4 = 8768, 8832
-NPARAM = 8833
+NIN, NH = 7, 64
+OFF_W1, OFF_B1 = 0, 448
+OFF_W2, OFF_B2 = 512, 4608
+OFF_W3, OFF_B3 = 4672, 8768
+OFF_W4, OFF_B4 = 8832, 8896
+NPARAM = 8897
 ITER_SCALE = 10000.0
 M_LO, M_HI = 0.25, 1.25
 THETA_LINEAR = 1e-4
@@ -96,14 +98,21 @@ def theta_bucket(theta: float) -> float:
     return np.floor(2.0 * np.log10(theta)) / 2.0
 
 
-def features(p2_tuple, theta: float, iteration: int) -> np.ndarray:
-    """Feature rows for an array of per-direction p2 tuples, shape (n, 4) -> (n, 6)."""
+def rate_feature(theta: float, theta_prev: float) -> float:
+    if not (theta > 0 and theta_prev > 0):
+        return 0.0
+    return 0.5 * float(np.clip(np.log10(theta / theta_prev), -2.0, 1.0))
+
+
+def features(p2_tuple, theta: float, iteration: int, theta_prev: float = 0.0) -> np.ndarray:
+    """Feature rows for an array of per-direction p2 tuples, shape (n, 4) -> (n, 7)."""
     p2 = np.atleast_2d(np.asarray(p2_tuple, dtype=np.float64))
     n = p2.shape[0]
     x = np.empty((n, NIN))
     x[:, :4] = p2 / 4.0
     x[:, 4] = -theta_bucket(theta) / 16.0
     x[:, 5] = min(iteration / ITER_SCALE, 1.0)
+    x[:, 6] = rate_feature(theta, theta_prev) if iteration > 0 else 0.0
     return x
 
 
@@ -117,7 +126,7 @@ def init_params(seed: int = 0) -> np.ndarray:
 
 
 def forward(p: np.ndarray, X: np.ndarray, bf16: bool = False):
-    """m(x) for feature rows X (n, 6); returns (m, cache)."""
+    """m(x) for feature rows X (n, 7); returns (m, cache)."""
     W1, b1, W2, b2, W3, b3, w4, b4 = unpack(bf16_round(p) if bf16 else p)
     r = bf16_round if bf16 else (lambda a: a)
     X = np.asarray(X, dtype=np.float64)

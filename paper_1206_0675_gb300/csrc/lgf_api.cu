@@ -864,7 +864,7 @@ lgf_status lgf_load_preconditioner(lgf_handle h, const uint16_t* w, size_t n_w, 
   lgf_status s = check_handle(h);
   if (s != LGF_OK) return s;
   if (!w || n_w != (size_t)MLP_NPARAM || (where != LGF_HOST && where != LGF_DEVICE))
-    return fail(h, LGF_E_ARG, "expected 8833 BF16 parameters");
+    return fail(h, LGF_E_ARG, "expected LGF_MLP_NPARAM BF16 parameters");
   if (!h->mlp_w) LGF_CK(h, dalloc(&h->mlp_w, (size_t)MLP_NPARAM));
   LGF_CK(h, cudaMemcpyAsync(h->mlp_w, w, (size_t)MLP_NPARAM * 2,
                             where == LGF_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, h->stream));
@@ -890,7 +890,7 @@ lgf_status lgf_set_mode_log(lgf_handle h, int32_t enable) {
   if (!enable) return LGF_OK;
   const int64_t V = h->geom.V;
   const int64_t nclass = h->phase == 64 ? h->d.mg.nclass : h->f.mg.nclass;
-  if (!h->stats) LGF_CK(h, dalloc(&h->stats, (size_t)MLP_NBUCKET * nclass * 4));
+  if (!h->stats) LGF_CK(h, dalloc(&h->stats, (size_t)MLP_NBUCKET * nclass * MLP_NSTAT));
   if (!h->ls) LGF_CK(h, dalloc(&h->ls, 1));
   if (h->phase == 64 && !h->d.Dlog) {
     LGF_CK(h, dalloc(&h->d.Dlog, (size_t)4 * V));
@@ -900,7 +900,7 @@ lgf_status lgf_set_mode_log(lgf_handle h, int32_t enable) {
     LGF_CK(h, dalloc(&h->f.Dlog, (size_t)4 * V));
     LGF_CK(h, dalloc(&h->f.Dprev, (size_t)4 * V));
   }
-  LGF_CK(h, cudaMemsetAsync(h->stats, 0, sizeof(double) * MLP_NBUCKET * nclass * 4, h->stream));
+  LGF_CK(h, cudaMemsetAsync(h->stats, 0, sizeof(double) * MLP_NBUCKET * nclass * MLP_NSTAT, h->stream));
   LGF_CK(h, cudaMemsetAsync(h->ls, 0, sizeof(LogState), h->stream));
   LGF_CK(h, cudaStreamSynchronize(h->stream));
   h->logging = true;
@@ -911,7 +911,7 @@ lgf_status lgf_get_mode_log(lgf_handle h, double* out, int64_t n) {
   lgf_status s = check_handle(h);
   if (s != LGF_OK) return s;
   const int64_t nclass = h->phase == 64 ? h->d.mg.nclass : h->f.mg.nclass;
-  if (!out || !h->stats || n != (int64_t)MLP_NBUCKET * nclass * 4)
+  if (!out || !h->stats || n != (int64_t)MLP_NBUCKET * nclass * MLP_NSTAT)
     return fail(h, LGF_E_ARG, "mode log not enabled or wrong size");
   LGF_CK(h, cudaMemcpyAsync(out, h->stats, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
   LGF_CK(h, cudaStreamSynchronize(h->stream));

@@ -211,7 +211,9 @@ struct CopyDiv {
 
 template <typename R, int SIGN>
 __global__ void __launch_bounds__(512) fft_xy_kernel(Geom g, FFTDir dx, FFTDir dy, C2<R>* __restrict__ data, const C2<R>* __restrict__ twg,
-                              const short* __restrict__ posg, int fpb, Lines lx, Lines ly, CopyDiv cd) {
+                              const short* __restrict__ posg, int fpb, Lines lx, Lines ly, CopyDiv cd, Batch B) {
+  if (batch_skip(B)) return;
+  data += blockIdx.z * B.s_delta;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int Lx = g.L[0], Ly = g.L[1];
   C2<R>* tw;
@@ -243,7 +245,10 @@ template <typename R>
 __global__ void __launch_bounds__(512) fft_zt_filter_kernel(Geom g, FFTDir dz, FFTDir dt, C2<R>* __restrict__ data,
                                      const C2<R>* __restrict__ twg, const short* __restrict__ posg,
                                      const R* __restrict__ K, int xc, int mode, const float* __restrict__ mtab,
-                                     int4 H, const int* __restrict__ use_m, Lines lz, Lines lt, CopyDiv cd) {
+                                     int4 H, const int* __restrict__ use_m, Lines lz, Lines lt, CopyDiv cd,
+                                     Batch B) {
+  if (batch_skip(B)) return;
+  data += blockIdx.z * B.s_delta;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int Lx = g.L[0], Ly = g.L[1], Lz = g.L[2], Lt = g.L[3];
   C2<R>* tw;
@@ -389,7 +394,11 @@ template <typename R, typename RG, int GROWS>
 __global__ void __launch_bounds__(512) fft_xy_inv_gauge_kernel(Geom g, FFTDir dx, FFTDir dy, const C2<R>* __restrict__ data,
                                         const C2<R>* __restrict__ twg, const short* __restrict__ posg,
                                         C2<RG>* __restrict__ gf, C2<RG>* __restrict__ Gf, Lines lx, Lines ly,
-                                        CopyDiv cd) {
+                                        CopyDiv cd, Batch B) {
+  if (batch_skip(B)) return;
+  data += blockIdx.z * B.s_delta;
+  gf += blockIdx.z * B.s_g;
+  if (Gf != nullptr) Gf += blockIdx.z * B.s_G;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int Lx = g.L[0], Ly = g.L[1];
   C2<R>* tw;
@@ -419,7 +428,11 @@ __global__ void __launch_bounds__(512) fft_xy_inv_gauge_kernel(Geom g, FFTDir dx
 // the inverse (x, y) transform has already been applied to data.
 template <typename R, typename RG, int GROWS>
 __global__ void gauge_from_delta_kernel(Geom g, const C2<R>* __restrict__ data, C2<RG>* __restrict__ gf,
-                                        C2<RG>* __restrict__ Gf) {
+                                        C2<RG>* __restrict__ Gf, Batch B) {
+  if (batch_skip(B)) return;
+  data += blockIdx.z * B.s_delta;
+  gf += blockIdx.z * B.s_g;
+  if (Gf != nullptr) Gf += blockIdx.z * B.s_G;
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= g.V) return;
   double2 u[3], v[3];
@@ -507,6 +520,42 @@ cudaError_t configure_fft_plan(const int L[4], int real_bytes, FFTPlan* p) {
   return cudaSuccess;
 }
 
+// Candidate plans for the autotuner: every fields-per-CTA count of the (x,y)
+// passes, every x-column count of the (z,t) pass that fits shared memory,
+// and two CTA sizes for each.
+void fft_plan_candidates(const int L[4], int real_bytes, std::vector<FFTPlan>& out) {
+  FFTPlan base;
+  out.clear();
+  if (configure_fft_plan(L, real_bytes, &base) != cudaSuccess) return;
+  const size_t cb = 2 * (size_t)real_bytes, maxsm = 220 * 1024;
+  const int Lx = L[0], Ly = L[1], Lz = L[2], Lt = L[3];
+  const size_t hxy = (size_t)((Lx + Ly + 1) & ~1) * cb + (size_t)((Lx + Ly + 7) & ~7) * 2;
+  const size_t hzt = (size_t)((Lz + Lt + 1) & ~1) * cb + (size_t)((Lz + Lt + 7) & ~7) * 2;
+  const size_t plane_xy = (size_t)Ly * (Lx + 1) * cb;
+  for (int fpb = 1; fpb <= 4; fpb *= 2) {
+    if (hxy + fpb * plane_xy > maxsm) continue;
+    for (int xc = 1; xc <= 8; xc *= 2) {
+      if (Lx % xc || hzt + (size_t)Lt * (Lz * xc + 1) * cb > maxsm) continue;
+      for (int tdiv = 8; tdiv <= 16; tdiv *= 2) {
+        FFTPlan p = base;
+        p.fpb_xy = fpb;
+        p.smem_xy = hxy + fpb * plane_xy;
+        p.xc = xc;
+        p.smem_zt = hzt + (size_t)Lt * (Lz * xc + 1) * cb;
+        auto thr = [&](int points) {
+          int t = (points + tdiv - 1) / tdiv;
+          t = ((t + 31) / 32) * 32;
+          return std::max(64, std::min(512, t));
+        };
+        p.threads_xy = thr(fpb * Lx * Ly);
+        p.threads_zt = thr(Lz * Lt * xc);
+        p.threads_c = thr(4 * Lx * Ly);
+        out.push_back(p);
+      }
+    }
+  }
+}
+
 template <typename K> static cudaError_t allow_smem(K kernel, size_t bytes) {
   if (bytes <= 48 * 1024) return cudaSuccess;
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -514,31 +563,32 @@ template <typename K> static cudaError_t allow_smem(K kernel, size_t bytes) {
 
 template <typename R>
 cudaError_t launch_fft_xy(const Geom& g, const FFTPlan& p, C2<R>* data, const C2<R>* tw, const short* pos, int sign,
-                          int nfields, cudaStream_t s) {
+                          int nfields, cudaStream_t s, const Batch& B) {
   int fpb = std::min(p.fpb_xy, nfields);
   while (nfields % fpb) fpb /= 2;
-  const int thr = threads_for(fpb * g.L[0] * g.L[1]);
+  const int thr = fpb == p.fpb_xy ? p.threads_xy : threads_for(fpb * g.L[0] * g.L[1]);
   const size_t smem = smem_header_bytes<R>(g.L[0], g.L[1]) + (size_t)fpb * g.L[1] * (g.L[0] + 1) * sizeof(C2<R>);
-  dim3 grid((unsigned)(g.L[2] * g.L[3]), (unsigned)(nfields / fpb));
+  dim3 grid((unsigned)(g.L[2] * g.L[3]), (unsigned)(nfields / fpb), (unsigned)B.n);
   const int Lx = g.L[0], Ly = g.L[1], RS = Lx + 1, PS = Ly * RS;
   const Lines lx = make_lines(fpb * Ly, fpb * Ly, RS, 0, 1), ly = make_lines(fpb * Lx, Lx, 1, PS, RS);
   const CopyDiv cd{FastDiv::make((uint32_t)(Lx * Ly)), FastDiv::make((uint32_t)Lx)};
   cudaError_t e;
   if (sign < 0) {
     if ((e = allow_smem(fft_xy_kernel<R, -1>, smem)) != cudaSuccess) return e;
-    fft_xy_kernel<R, -1><<<grid, thr, smem, s>>>(g, p.d[0], p.d[1], data, tw, pos, fpb, lx, ly, cd);
+    fft_xy_kernel<R, -1><<<grid, thr, smem, s>>>(g, p.d[0], p.d[1], data, tw, pos, fpb, lx, ly, cd, B);
   } else {
     if ((e = allow_smem(fft_xy_kernel<R, +1>, smem)) != cudaSuccess) return e;
-    fft_xy_kernel<R, +1><<<grid, thr, smem, s>>>(g, p.d[0], p.d[1], data, tw, pos, fpb, lx, ly, cd);
+    fft_xy_kernel<R, +1><<<grid, thr, smem, s>>>(g, p.d[0], p.d[1], data, tw, pos, fpb, lx, ly, cd, B);
   }
   return cudaGetLastError();
 }
 
 template <typename R>
 cudaError_t launch_fft_zt(const Geom& g, const FFTPlan& p, C2<R>* data, const C2<R>* tw, const short* pos,
-                          const R* K, int mode, int nfields, cudaStream_t s, const float* mtab, const int* use_m) {
+                          const R* K, int mode, int nfields, cudaStream_t s, const float* mtab, const int* use_m,
+                          const Batch& B) {
   const size_t smem = p.smem_zt;
-  dim3 grid((unsigned)(g.L[0] / p.xc * g.L[1]), (unsigned)nfields);
+  dim3 grid((unsigned)(g.L[0] / p.xc * g.L[1]), (unsigned)nfields, (unsigned)B.n);
   cudaError_t e = allow_smem(fft_zt_filter_kernel<R>, smem);
   if (e != cudaSuccess) return e;
   const int4 H = make_int4(g.L[0] / 2 + 1, g.L[1] / 2 + 1, g.L[2] / 2 + 1, g.L[3] / 2 + 1);
@@ -546,17 +596,18 @@ cudaError_t launch_fft_zt(const Geom& g, const FFTPlan& p, C2<R>* data, const C2
   const Lines lz = make_lines(Lt * xc, xc, 1, TS, xc), lt = make_lines(Lz * xc, Lz * xc, 1, 0, TS);
   const CopyDiv cd{FastDiv::make((uint32_t)xc), FastDiv::make((uint32_t)Lz)};
   fft_zt_filter_kernel<R><<<grid, p.threads_zt, smem, s>>>(g, p.d[2], p.d[3], data, tw, pos, K, p.xc, mode, mtab, H,
-                                                           use_m, lz, lt, cd);
+                                                           use_m, lz, lt, cd, B);
   return cudaGetLastError();
 }
 
 template <typename R, typename RG, int GROWS>
 cudaError_t launch_fft_xy_inv_gauge(const Geom& g, const FFTPlan& p, C2<R>* data, const C2<R>* tw, const short* pos,
-                                    C2<RG>* gfield, C2<RG>* Gfield, cudaStream_t s) {
+                                    C2<RG>* gfield, C2<RG>* Gfield, cudaStream_t s, const Batch& B) {
   cudaError_t e;
   if (!p.fuse_g) {
-    if ((e = launch_fft_xy<R>(g, p, data, tw, pos, +1, 4, s)) != cudaSuccess) return e;
-    gauge_from_delta_kernel<R, RG, GROWS><<<(unsigned)((g.V + 127) / 128), 128, 0, s>>>(g, data, gfield, Gfield);
+    if ((e = launch_fft_xy<R>(g, p, data, tw, pos, +1, 4, s, B)) != cudaSuccess) return e;
+    gauge_from_delta_kernel<R, RG, GROWS><<<dim3((unsigned)((g.V + 127) / 128), 1, (unsigned)B.n), 128, 0, s>>>(
+        g, data, gfield, Gfield, B);
     return cudaGetLastError();
   }
   const size_t smem = p.smem_c;
@@ -564,22 +615,24 @@ cudaError_t launch_fft_xy_inv_gauge(const Geom& g, const FFTPlan& p, C2<R>* data
   const int Lx = g.L[0], Ly = g.L[1], RS = Lx + 1, PS = Ly * RS;
   const Lines lx = make_lines(4 * Ly, 4 * Ly, RS, 0, 1), ly = make_lines(4 * Lx, Lx, 1, PS, RS);
   const CopyDiv cd{FastDiv::make((uint32_t)(Lx * Ly)), FastDiv::make((uint32_t)Lx)};
-  fft_xy_inv_gauge_kernel<R, RG, GROWS><<<(unsigned)(g.L[2] * g.L[3]), p.threads_c, smem, s>>>(
-      g, p.d[0], p.d[1], data, tw, pos, gfield, Gfield, lx, ly, cd);
+  fft_xy_inv_gauge_kernel<R, RG, GROWS><<<dim3((unsigned)(g.L[2] * g.L[3]), 1, (unsigned)B.n), p.threads_c, smem, s>>>(
+      g, p.d[0], p.d[1], data, tw, pos, gfield, Gfield, lx, ly, cd, B);
   return cudaGetLastError();
 }
 
 template cudaError_t launch_fft_xy<double>(const Geom&, const FFTPlan&, C2<double>*, const C2<double>*, const short*,
-                                           int, int, cudaStream_t);
+                                           int, int, cudaStream_t, const Batch&);
 template cudaError_t launch_fft_xy<float>(const Geom&, const FFTPlan&, C2<float>*, const C2<float>*, const short*,
-                                          int, int, cudaStream_t);
+                                          int, int, cudaStream_t, const Batch&);
 template cudaError_t launch_fft_zt<double>(const Geom&, const FFTPlan&, C2<double>*, const C2<double>*, const short*,
-                                           const double*, int, int, cudaStream_t, const float*, const int*);
+                                           const double*, int, int, cudaStream_t, const float*, const int*,
+                                           const Batch&);
 template cudaError_t launch_fft_zt<float>(const Geom&, const FFTPlan&, C2<float>*, const C2<float>*, const short*,
-                                          const float*, int, int, cudaStream_t, const float*, const int*);
+                                          const float*, int, int, cudaStream_t, const float*, const int*,
+                                          const Batch&);
 #define LGF_INST_C(R, RG, GR)                                                                                    \
   template cudaError_t launch_fft_xy_inv_gauge<R, RG, GR>(const Geom&, const FFTPlan&, C2<R>*, const C2<R>*,      \
-                                                          const short*, C2<RG>*, C2<RG>*, cudaStream_t);
+                                                          const short*, C2<RG>*, C2<RG>*, cudaStream_t, const Batch&);
 LGF_INST_C(double, double, 3)
 LGF_INST_C(double, double, 2)
 LGF_INST_C(float, float, 2)

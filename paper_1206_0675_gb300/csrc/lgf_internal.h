@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "lgf_common.cuh"
 
 namespace lgf {
@@ -16,12 +18,14 @@ struct DevState {
   double F;          // gauge functional of the current links
   double theta;      // stopping quantity of the current links
   double F_prev;     // F before the last step
+  double theta_prev; // theta before the last step (0 before the first)
   double tol;        // loop runs while theta >= tol
   int iter;          // link updates performed since the counter was reset
   int max_iter;      // loop stops when iter reaches it
   int status;        // 0 ok, 1 non-finite F or theta, 2 timeout
   unsigned int ticket;  // CTA completion counter of the measurement reduction
   int hist_cap;      // capacity of the history buffers (0 = none)
+  int done;          // batch mode: this configuration has retired (theta < tol or iter >= max_iter)
   int use_m;         // the running step multiplies the filter by the learned table
   int revert;        // the last learned step lowered F: undo it and redo it with the plain filter
   int n_fallback;    // learned steps rejected since the counter was reset
@@ -30,6 +34,18 @@ struct DevState {
 };
 
 enum { ST_OK = 0, ST_NONFINITE = 1 };
+
+// Batch dimension of a launch: blockIdx.z selects one of n configurations of
+// the same lattice shape, whose buffers are the given strides (in elements)
+// apart.  In batch mode (st != nullptr) st[z] is the configuration's
+// controller state and retired configurations (st[z].done) are skipped.
+struct Batch {
+  int n = 1;
+  int64_t s_links = 0, s_delta = 0, s_g = 0, s_G = 0, s_part = 0;
+  DevState* st = nullptr;
+};
+
+__device__ __forceinline__ bool batch_skip(const Batch& b) { return b.st != nullptr && b.st[blockIdx.z].done; }
 
 constexpr int MEASURE_THREADS = 256;
 
@@ -44,10 +60,12 @@ inline int64_t measure_blocks(int64_t V) { return (V + MEASURE_THREADS - 1) / ME
 // After a counted step that used the learned table (st->use_m) and lowered F,
 // st->revert is set and the WHILE condition stays true so that the next
 // body undoes the step and redoes it with the plain filter.
+// In batch mode (B->st set) each configuration's state is B->st[z] and its
+// last CTA sets that state's `done` instead of a graph condition.
 template <typename R, int ROWS>
 cudaError_t launch_measure(const Geom& g, const C2<R>* links, C2<R>* delta, double* partials, DevState* st,
                            int count_iter, unsigned long long cond_handle, int use_cond, cudaStream_t s,
-                           int only_if_revert = 0);
+                           int only_if_revert = 0, const Batch& B = Batch());
 
 // Undo of the last update when st->revert is set: U_mu(x) <- g^dag(x) U_mu(x)
 // g(x + mu^) and, when G is given (3 rows, precision R), G <- g^dag G.
@@ -58,7 +76,10 @@ cudaError_t launch_revert(const Geom& g, C2<R>* links, const C2<R>* gfield, C2<R
 // U_mu(x) <- g(x) U_mu(x) g^dagger(x + mu^) in place (Sec. 2 eq. 2; kernel k6).
 // Links in precision R with LROWS stored rows; g in precision R with GROWS rows.
 template <typename R, int LROWS, int GROWS>
-cudaError_t launch_update(const Geom& g, C2<R>* links, const C2<R>* gfield, cudaStream_t s);
+cudaError_t launch_update(const Geom& g, C2<R>* links, const C2<R>* gfield, cudaStream_t s, const Batch& B = Batch());
+
+// Graph condition of a batch: true while any of the n configurations is active.
+cudaError_t launch_batch_condition(const DevState* st, int n, unsigned long long cond, cudaStream_t s);
 
 // AoS FP64 user layout [mu][t][z][y][x][3][3][2] -> SoA links of precision R.
 template <typename R, int ROWS>
@@ -127,7 +148,7 @@ struct FFTPlan {
 // pos: digit-reversal position tables of the four directions (fft_positions).
 template <typename R>
 cudaError_t launch_fft_xy(const Geom& g, const FFTPlan& p, C2<R>* data, const C2<R>* tw, const short* pos, int sign,
-                          int nfields, cudaStream_t s);
+                          int nfields, cudaStream_t s, const Batch& B = Batch());
 // mode 0: forward (z,t) DFT, multiply by K, inverse (z,t) DFT (pass B);
 // mode -1 / +1: forward / inverse (z,t) DFT only (K unused).
 // mtab (may be NULL): learned multiplier per momentum class, applied when
@@ -135,14 +156,16 @@ cudaError_t launch_fft_xy(const Geom& g, const FFTPlan& p, C2<R>* data, const C2
 template <typename R>
 cudaError_t launch_fft_zt(const Geom& g, const FFTPlan& p, C2<R>* data, const C2<R>* tw, const short* pos,
                           const R* K, int mode, int nfields, cudaStream_t s, const float* mtab = nullptr,
-                          const int* use_m = nullptr);
+                          const int* use_m = nullptr, const Batch& B = Batch());
 // Inverse (x,y) transform fused with g(x) = reunitarize(1 + Delta'(x)) in FP64;
 // g stored with GROWS rows in precision RG; optional G <- g G (precision RG2 with 3 rows).
 template <typename R, typename RG, int GROWS>
 cudaError_t launch_fft_xy_inv_gauge(const Geom& g, const FFTPlan& p, C2<R>* data, const C2<R>* tw, const short* pos,
-                                    C2<RG>* gfield, C2<RG>* Gfield, cudaStream_t s);
+                                    C2<RG>* gfield, C2<RG>* Gfield, cudaStream_t s, const Batch& B = Batch());
 
 cudaError_t configure_fft_plan(const int L[4], int real_bytes, FFTPlan* p);
+// All plans the autotuner may choose among for a lattice shape.
+void fft_plan_candidates(const int L[4], int real_bytes, std::vector<FFTPlan>& out);
 // Digit-reversal position tables of the four directions, concatenated
 // (Lx + Ly + Lz + Lt entries).
 void fft_positions(const FFTPlan& p, short* out);

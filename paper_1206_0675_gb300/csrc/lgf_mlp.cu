@@ -109,8 +109,8 @@ __device__ __forceinline__ void mlp_tile(const MlpSmem& S, const float xr0[MLP_N
   const int lane = threadIdx.x & 31, g = lane >> 2, tig = lane & 3;
   uint32_t a1[4];
   const int c0 = 2 * tig;
-  a1[0] = c0 + 1 < MLP_NIN ? pack_bf16(xr0[c0], xr0[c0 + 1]) : 0u;
-  a1[1] = c0 + 1 < MLP_NIN ? pack_bf16(xr1[c0], xr1[c0 + 1]) : 0u;
+  a1[0] = pack_bf16(c0 < MLP_NIN ? xr0[c0] : 0.f, c0 + 1 < MLP_NIN ? xr0[c0 + 1] : 0.f);
+  a1[1] = pack_bf16(c0 < MLP_NIN ? xr1[c0] : 0.f, c0 + 1 < MLP_NIN ? xr1[c0 + 1] : 0.f);
   a1[2] = 0u;
   a1[3] = 0u;
   float acc[8][4];
@@ -183,6 +183,7 @@ __global__ void __launch_bounds__(128) mlp_multiplier_kernel(const __nv_bfloat16
   __shared__ MlpSmem S;
   mlp_load_smem(S, P);
   const double theta = st->theta;
+  const double theta_prev = st->theta_prev;
   const int iter = st->iter;
   __syncthreads();
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -192,6 +193,7 @@ __global__ void __launch_bounds__(128) mlp_multiplier_kernel(const __nv_bfloat16
   const float fb = theta > 0.0 ? (float)(floor(2.0 * log10(theta)) * 0.5) : -20.f;
   const float f4 = -fb / 16.f;
   const float f5 = fminf((float)iter / MLP_ITER_SCALE, 1.f);
+  const float f6 = iter > 0 ? mlp_rate_feature(theta, theta_prev) : 0.f;
   const int lane = threadIdx.x & 31, g = lane >> 2;
   const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -212,6 +214,7 @@ __global__ void __launch_bounds__(128) mlp_multiplier_kernel(const __nv_bfloat16
       x[h][3] = 0.25f * p2[mg.off[3] + ft];
       x[h][4] = f4;
       x[h][5] = f5;
+      x[h][6] = f6;
     }
     float z0, z1;
     mlp_tile(S, x[0], x[1], z0, z1);
@@ -481,8 +484,9 @@ cudaError_t launch_f32_to_bf16(const float* in, uint16_t* out, int n, cudaStream
 // logging: per (theta bucket, class) statistics of consecutive D^
 // ---------------------------------------------------------------------------
 
-// stats[(b * nclass + c) * 4 + {0,1,2,3}] += {Re<cur, prev>, |prev|^2, 1, iter_frac}
-// for every mode k of the four packed fields; b and iter_frac belong to prev.
+// stats[(b * nclass + c) * 5 + {0..4}] += {Re<cur, prev>, |prev|^2, 1, iter_frac, rate}
+// for every mode k of the four packed fields; b, iter_frac and the contraction
+// rate feature belong to the links of prev.
 template <typename R>
 __global__ void mode_log_kernel(Geom g, MlpGeom mg, const C2<R>* __restrict__ cur, const C2<R>* __restrict__ prev,
                                 const LogState* __restrict__ ls, double* __restrict__ stats) {
@@ -490,6 +494,7 @@ __global__ void mode_log_kernel(Geom g, MlpGeom mg, const C2<R>* __restrict__ cu
   if (s >= g.V || !ls->have_prev) return;
   const int bucket = mlp_bucket_index(ls->theta_prev);
   const float iter_frac = fminf((float)ls->iter_prev / MLP_ITER_SCALE, 1.f);
+  const float rate = mlp_rate_feature(ls->theta_prev, ls->theta_prev2);
   int c[4];
   site_coords(g, s, c);
   int64_t cls = 0;
@@ -504,11 +509,12 @@ __global__ void mode_log_kernel(Geom g, MlpGeom mg, const C2<R>* __restrict__ cu
     num += (double)a.x * b.x + (double)a.y * b.y;
     den += (double)b.x * b.x + (double)b.y * b.y;
   }
-  double* row = stats + ((int64_t)bucket * mg.nclass + cls) * 4;
+  double* row = stats + ((int64_t)bucket * mg.nclass + cls) * MLP_NSTAT;
   atomicAdd(row, num);
   atomicAdd(row + 1, den);
   atomicAdd(row + 2, 1.0);
   atomicAdd(row + 3, (double)iter_frac);
+  atomicAdd(row + 4, (double)rate);
 }
 
 template <typename R>
@@ -519,6 +525,7 @@ cudaError_t launch_mode_log(const Geom& g, const MlpGeom& mg, const C2<R>* cur, 
 }
 
 __global__ void log_state_update_kernel(LogState* ls, const DevState* st) {
+  ls->theta_prev2 = ls->have_prev ? ls->theta_prev : 0.0;
   ls->theta_prev = st->theta;
   ls->iter_prev = st->iter;
   ls->have_prev = 1;

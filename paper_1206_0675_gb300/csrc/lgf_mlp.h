@@ -8,11 +8,12 @@
 
 namespace lgf {
 
-// 6 -> 64 -> 64 -> 64 -> 1, flat parameter layout (row-major [out][in]):
-constexpr int MLP_NIN = 6, MLP_NH = 64;
-constexpr int MLP_OFF_W1 = 0, MLP_OFF_B1 = 384, MLP_OFF_W2 = 448, MLP_OFF_B2 = 4544;
-constexpr int MLP_OFF_W3 = 4608, MLP_OFF_B3 = 8704, MLP_OFF_W4 = 8768, MLP_OFF_B4 = 8832;
-constexpr int MLP_NPARAM = 8833;
+// 7 -> 64 -> 64 -> 64 -> 1, flat parameter layout (row-major [out][in]):
+constexpr int MLP_NIN = 7, MLP_NH = 64;
+constexpr int MLP_OFF_W1 = 0, MLP_OFF_B1 = 448, MLP_OFF_W2 = 512, MLP_OFF_B2 = 4608;
+constexpr int MLP_OFF_W3 = 4672, MLP_OFF_B3 = 8768, MLP_OFF_W4 = 8832, MLP_OFF_B4 = 8896;
+constexpr int MLP_NPARAM = 8897;
+constexpr int MLP_NSTAT = 5;               // mode-log sums per (bucket, class)
 constexpr float MLP_ITER_SCALE = 10000.f;  // iter_frac = min(iter / 10000, 1)
 constexpr int MLP_NBUCKET = 40;            // theta buckets of the mode log
 
@@ -46,10 +47,20 @@ cudaError_t launch_f32_to_bf16(const float* in, uint16_t* out, int n, cudaStream
 
 // Per-mode statistics of consecutive Fourier-space divergences (see lgf_mlp.cu).
 struct LogState {
-  double theta_prev;
+  double theta_prev;   // theta of the links whose D^ is stored as "previous"
+  double theta_prev2;  // theta one step earlier (0 if none)
   int iter_prev;
   int have_prev;
 };
+
+// Seventh feature: the last step's contraction, clamp(log10(theta/theta_prev), -2, 1)/2
+// (0 when there is no previous step).
+__host__ __device__ inline float mlp_rate_feature(double theta, double theta_prev) {
+  if (!(theta > 0.0) || !(theta_prev > 0.0)) return 0.f;
+  double r = log10(theta / theta_prev);
+  r = r < -2.0 ? -2.0 : (r > 1.0 ? 1.0 : r);
+  return (float)(0.5 * r);
+}
 template <typename R>
 cudaError_t launch_mode_log(const Geom& g, const MlpGeom& mg, const C2<R>* cur, const C2<R>* prev,
                             const LogState* ls, double* stats, cudaStream_t s);

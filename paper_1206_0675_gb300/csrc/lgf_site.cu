@@ -64,7 +64,17 @@ __device__ __forceinline__ void block_sum2(double& a, double& b) {
 template <typename R, int ROWS>
 __global__ void __launch_bounds__(MEASURE_THREADS)
 measure_kernel(Geom g, MatField<R, ROWS> U, C2<R>* __restrict__ delta, double* __restrict__ partials,
-               DevState* __restrict__ st, int count_iter, unsigned long long cond, int use_cond, int only_if_revert) {
+               DevState* __restrict__ st, int count_iter, unsigned long long cond, int use_cond, int only_if_revert,
+               Batch B) {
+  if (batch_skip(B)) return;
+  const bool batch = B.st != nullptr;
+  if (batch) {
+    const int cfg = blockIdx.z;
+    st = B.st + cfg;
+    U.p += cfg * B.s_links;
+    delta += cfg * B.s_delta;
+    partials += cfg * B.s_part;
+  }
   if (only_if_revert && !st->revert) return;
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   // per-site sums in the link precision; warp sums likewise, everything
@@ -135,6 +145,7 @@ measure_kernel(Geom g, MatField<R, ROWS> U, C2<R>* __restrict__ delta, double* _
       it += 1;
       st->iter = it;
       st->F_prev = st->F;
+      st->theta_prev = st->theta;
       // a learned step that lowered F is undone and redone with the plain filter
       if (st->use_m && F < st->F) {
         revert = 1;
@@ -154,6 +165,7 @@ measure_kernel(Geom g, MatField<R, ROWS> U, C2<R>* __restrict__ delta, double* _
     const bool finite = isfinite(F) && isfinite(th);
     if (!finite) st->status = ST_NONFINITE;
     st->ticket = 0u;
+    if (batch) st->done = !(finite && th >= st->tol && it < st->max_iter);
     if (use_cond) {
       cudaGraphConditionalHandle h = (cudaGraphConditionalHandle)cond;
       cudaGraphSetConditional(h, (finite && ((th >= st->tol && it < st->max_iter) || revert)) ? 1u : 0u);
@@ -164,11 +176,26 @@ measure_kernel(Geom g, MatField<R, ROWS> U, C2<R>* __restrict__ delta, double* _
 template <typename R, int ROWS>
 cudaError_t launch_measure(const Geom& g, const C2<R>* links, C2<R>* delta, double* partials, DevState* st,
                            int count_iter, unsigned long long cond_handle, int use_cond, cudaStream_t s,
-                           int only_if_revert) {
+                           int only_if_revert, const Batch& B) {
   MatField<R, ROWS> U{const_cast<C2<R>*>(links), g.V};
   const int64_t nb = measure_blocks(g.V);
-  measure_kernel<R, ROWS><<<(unsigned)nb, MEASURE_THREADS, 0, s>>>(g, U, delta, partials, st, count_iter, cond_handle,
-                                                                   use_cond, only_if_revert);
+  measure_kernel<R, ROWS><<<dim3((unsigned)nb, 1, (unsigned)B.n), MEASURE_THREADS, 0, s>>>(
+      g, U, delta, partials, st, count_iter, cond_handle, use_cond, only_if_revert, B);
+  return cudaGetLastError();
+}
+
+__global__ void batch_condition_kernel(const DevState* __restrict__ st, int n, unsigned long long cond) {
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    if (!st[i].done) any = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, any ? 1u : 0u);
+}
+
+cudaError_t launch_batch_condition(const DevState* st, int n, unsigned long long cond, cudaStream_t s) {
+  batch_condition_kernel<<<1, 256, 0, s>>>(st, n, cond);
   return cudaGetLastError();
 }
 
@@ -180,7 +207,10 @@ constexpr int UPDATE_THREADS = 128;
 
 template <typename R, int LROWS, int GROWS>
 __global__ void __launch_bounds__(UPDATE_THREADS)
-update_kernel(Geom g, MatField<R, LROWS> U, MatField<R, GROWS> Gf) {
+update_kernel(Geom g, MatField<R, LROWS> U, MatField<R, GROWS> Gf, Batch B) {
+  if (batch_skip(B)) return;
+  U.p += blockIdx.z * B.s_links;
+  Gf.p += blockIdx.z * B.s_g;
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= g.V) return;
   int c[4];
@@ -219,11 +249,11 @@ update_kernel(Geom g, MatField<R, LROWS> U, MatField<R, GROWS> Gf) {
 }
 
 template <typename R, int LROWS, int GROWS>
-cudaError_t launch_update(const Geom& g, C2<R>* links, const C2<R>* gfield, cudaStream_t s) {
+cudaError_t launch_update(const Geom& g, C2<R>* links, const C2<R>* gfield, cudaStream_t s, const Batch& B) {
   MatField<R, LROWS> U{links, g.V};
   MatField<R, GROWS> Gf{const_cast<C2<R>*>(gfield), g.V};
   const int64_t nb = (g.V + UPDATE_THREADS - 1) / UPDATE_THREADS;
-  update_kernel<R, LROWS, GROWS><<<(unsigned)nb, UPDATE_THREADS, 0, s>>>(g, U, Gf);
+  update_kernel<R, LROWS, GROWS><<<dim3((unsigned)nb, 1, (unsigned)B.n), UPDATE_THREADS, 0, s>>>(g, U, Gf, B);
   return cudaGetLastError();
 }
 
@@ -493,6 +523,7 @@ __global__ void set_state_kernel(DevState* st, double tol, int max_iter, int res
   st->max_iter = max_iter;
   if (reset_iter) {
     st->iter = 0;
+    st->theta_prev = 0.0;
     st->status = ST_OK;
     st->revert = 0;
     st->use_m = 0;
@@ -576,7 +607,7 @@ cudaError_t launch_project_sites_f32_to_f64(const Geom& g, const float2* G32, do
 
 #define LGF_INST_R_ROWS(R, ROWS)                                                                                     \
   template cudaError_t launch_measure<R, ROWS>(const Geom&, const C2<R>*, C2<R>*, double*, DevState*, int,           \
-                                               unsigned long long, int, cudaStream_t, int);                         \
+                                               unsigned long long, int, cudaStream_t, int, const Batch&);           \
   template cudaError_t launch_links_from_aos<R, ROWS>(const Geom&, const double*, C2<R>*, cudaStream_t);            \
   template cudaError_t launch_links_to_aos<R, ROWS>(const Geom&, const C2<R>*, double*, cudaStream_t);              \
   template cudaError_t launch_sites_to_aos<R, ROWS>(const Geom&, const C2<R>*, double*, cudaStream_t);              \
@@ -596,10 +627,10 @@ template cudaError_t launch_revert<float, 2, 2>(const Geom&, C2<float>*, const C
                                                 const DevState*, cudaStream_t);
 template cudaError_t launch_revert<float, 3, 3>(const Geom&, C2<float>*, const C2<float>*, C2<float>*,
                                                 const DevState*, cudaStream_t);
-template cudaError_t launch_update<double, 3, 3>(const Geom&, C2<double>*, const C2<double>*, cudaStream_t);
-template cudaError_t launch_update<double, 2, 3>(const Geom&, C2<double>*, const C2<double>*, cudaStream_t);
-template cudaError_t launch_update<float, 2, 2>(const Geom&, C2<float>*, const C2<float>*, cudaStream_t);
-template cudaError_t launch_update<float, 3, 3>(const Geom&, C2<float>*, const C2<float>*, cudaStream_t);
+template cudaError_t launch_update<double, 3, 3>(const Geom&, C2<double>*, const C2<double>*, cudaStream_t, const Batch&);
+template cudaError_t launch_update<double, 2, 3>(const Geom&, C2<double>*, const C2<double>*, cudaStream_t, const Batch&);
+template cudaError_t launch_update<float, 2, 2>(const Geom&, C2<float>*, const C2<float>*, cudaStream_t, const Batch&);
+template cudaError_t launch_update<float, 3, 3>(const Geom&, C2<float>*, const C2<float>*, cudaStream_t, const Batch&);
 template cudaError_t launch_delta_to_aos<double>(const Geom&, const C2<double>*, double*, cudaStream_t);
 template cudaError_t launch_delta_to_aos<float>(const Geom&, const C2<float>*, double*, cudaStream_t);
 template cudaError_t launch_filter_table<double>(const Geom&, const double*, int, double, double, int, double*,

@@ -30,8 +30,9 @@ LGF_OK, LGF_E_ARG, LGF_E_NOMEM, LGF_E_CUDA, LGF_E_STATE, LGF_E_NONFINITE, LGF_E_
     LGF_E_UNSUPPORTED = range(9)
 LGF_FP64, LGF_FP32, LGF_MIXED = 0, 1, 2
 LGF_STORE18, LGF_STORE12, LGF_TRACK_G, LGF_LEARNED, LGF_PLAIN_SD = 0, 1, 2, 4, 8
-LGF_MLP_NPARAM = 8833
+LGF_MLP_NPARAM = 8897
 MLP_NBUCKET = 40
+MLP_NSTAT = 5
 LGF_HOST, LGF_DEVICE = 0, 1
 
 _c_int_p = ctypes.POINTER(ctypes.c_int32)
@@ -70,6 +71,15 @@ SIGNATURES = [
                                      ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
                                      ctypes.c_uint64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
     ("lgf_mlp_to_bf16", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("lgf_batch_create", ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.c_int,
+                                        ctypes.c_uint32, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    ("lgf_batch_destroy", ctypes.c_int, [ctypes.c_void_p]),
+    ("lgf_batch_set_links", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int]),
+    ("lgf_batch_get_links", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int]),
+    ("lgf_batch_fix", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int32, ctypes.c_double,
+                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("lgf_batch_describe", ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_size_t]),
+    ("lgf_batch_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("lgf_status_string", ctypes.c_char_p, [ctypes.c_int]),
     ("lgf_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
 ]
@@ -255,6 +265,88 @@ def lgf_measure_static(extents, u_ptr: int, d_ptr: int, f_theta_ptr: int, stream
                                              ctypes.c_void_p(f_theta_ptr or None), ctypes.c_void_p(stream or None))
 
 
+class Batch:
+    """Many configurations fixed together (lgf_batch_*); links as complex128 host arrays."""
+
+    def __init__(self, extents_list, stream: int | None = None):
+        lib = load_library()
+        self.extents = [tuple(int(e) for e in ext) for ext in extents_list]
+        flat = (ctypes.c_int32 * (4 * len(self.extents)))(*[e for ext in self.extents for e in ext])
+        if stream is None:
+            try:
+                import torch
+                stream = torch.cuda.current_stream().cuda_stream
+            except Exception:
+                stream = 0
+        h = ctypes.c_void_p()
+        st = lib.lgf_batch_create(len(self.extents), flat, LGF_FP64, 0, ctypes.c_void_p(stream or None),
+                                  ctypes.byref(h))
+        if st != LGF_OK:
+            raise LgfError(st, "lgf_batch_create")
+        self.handle = h.value
+
+    def _check(self, st, where, allow=()):
+        if st != LGF_OK and st not in allow:
+            raise LgfError(st, where, load_library().lgf_batch_last_error(ctypes.c_void_p(self.handle)).decode())
+        return st
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load_library().lgf_batch_destroy(ctypes.c_void_p(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _shape(self, i):
+        lx, ly, lz, lt = self.extents[i]
+        return (4, lt, lz, ly, lx, 3, 3)
+
+    def set_links(self, i: int, U) -> None:
+        if _is_torch_cuda(U):
+            self._check(load_library().lgf_batch_set_links(ctypes.c_void_p(self.handle), i,
+                                                           ctypes.c_void_p(U.data_ptr()), LGF_DEVICE),
+                        "lgf_batch_set_links")
+            return
+        a = _host_buffer(U, self._shape(i))
+        self._check(load_library().lgf_batch_set_links(ctypes.c_void_p(self.handle), i, ctypes.c_void_p(a.ctypes.data),
+                                                       LGF_HOST), "lgf_batch_set_links")
+
+    def get_links(self, i: int) -> np.ndarray:
+        a = np.empty(self._shape(i), dtype=np.complex128)
+        self._check(load_library().lgf_batch_get_links(ctypes.c_void_p(self.handle), i, ctypes.c_void_p(a.ctypes.data),
+                                                       LGF_HOST), "lgf_batch_get_links")
+        return a
+
+    def fix(self, theta_tol: float = 1e-14, max_iter: int = 20000, alpha: float = 0.08):
+        """Returns (iters, F, theta, all_converged) with per-configuration arrays."""
+        n = len(self.extents)
+        it = np.zeros(n, dtype=np.int32)
+        F = np.zeros(n)
+        th = np.zeros(n)
+        st = load_library().lgf_batch_fix(ctypes.c_void_p(self.handle), float(theta_tol), int(max_iter), float(alpha),
+                                          ctypes.c_void_p(it.ctypes.data), ctypes.c_void_p(F.ctypes.data),
+                                          ctypes.c_void_p(th.ctypes.data))
+        self._check(st, "lgf_batch_fix", allow=(LGF_E_NOTCONV,))
+        return it, F, th, st == LGF_OK
+
+    def describe(self):
+        import json
+        buf = ctypes.create_string_buffer(1 << 16)
+        self._check(load_library().lgf_batch_describe(ctypes.c_void_p(self.handle), buf, len(buf)),
+                    "lgf_batch_describe")
+        return json.loads(buf.value.decode())
+
+
 # --- marshalling helpers ----------------------------------------------------
 
 _PREC = {"fp64": LGF_FP64, "fp32": LGF_FP32, "mixed": LGF_MIXED}
@@ -398,13 +490,13 @@ class Lattice:
         return lgf_get_timing(self.handle)
 
     def load_preconditioner(self, weights_bf16) -> None:
-        """weights_bf16: uint16 numpy array (host) or CUDA tensor (int16/uint16/bfloat16) of 8833 values."""
+        """weights_bf16: uint16 numpy array (host) or CUDA tensor (int16/uint16/bfloat16) of 8897 values."""
         if _is_torch_cuda(weights_bf16):
             lgf_load_preconditioner(self.handle, weights_bf16.data_ptr(), LGF_MLP_NPARAM, LGF_DEVICE)
         else:
             w = np.ascontiguousarray(weights_bf16, dtype=np.uint16)
             if w.size != LGF_MLP_NPARAM:
-                raise ValueError("expected 8833 BF16 parameters")
+                raise ValueError(f"expected {LGF_MLP_NPARAM} BF16 parameters")
             lgf_load_preconditioner(self.handle, w.ctypes.data, LGF_MLP_NPARAM, LGF_HOST)
 
     def fallbacks(self) -> int:
@@ -414,8 +506,8 @@ class Lattice:
         lgf_set_mode_log(self.handle, enable)
 
     def get_mode_log(self) -> np.ndarray:
-        """Sums [bucket][class][4] = (Re<D^_{k+1}, D^_k>, |D^_k|^2, count, iter_frac)."""
-        out = np.zeros((MLP_NBUCKET, self.nclass, 4))
+        """Sums [bucket][class][5] = (Re<D^_{k+1}, D^_k>, |D^_k|^2, count, iter_frac, rate)."""
+        out = np.zeros((MLP_NBUCKET, self.nclass, MLP_NSTAT))
         lgf_get_mode_log(self.handle, out.ctypes.data, out.size)
         return out
 

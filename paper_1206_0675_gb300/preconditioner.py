@@ -20,9 +20,11 @@ The loss is the mean square error of log m, weighted by |D^_k|^2
 normalised within each (configuration, bucket).
 
 Features (identical to the ones the inference kernel builds):
-    (p2_x/4, p2_y/4, p2_z/4, p2_t/4, -bucket/16, iter_frac)
+    (p2_x/4, p2_y/4, p2_z/4, p2_t/4, -bucket/16, iter_frac, rate)
 with p2_mu = 4 sin^2(pi f_mu / L_mu), bucket = floor(2 log10 theta)/2 of the
-step's starting links and iter_frac = min(iteration / 10000, 1).
+step's starting links, iter_frac = min(iteration / 10000, 1) and
+rate = clamp(log10(theta/theta_prev), -2, 1)/2 the contraction of theta over
+the previous step (0 on the first step), averaged over the steps of a bucket.
 
 The network is trained with Adam by ``lgf_mlp_train`` (FP32 forward and
 backward kernels of liblgf) and stored as BF16 (``lgf_mlp_to_bf16``).
@@ -71,22 +73,23 @@ def samples_from_log(extents, stats: np.ndarray, rng: np.random.Generator, per_b
     for b in range(stats.shape[0]):
         if (4 - b) / 2.0 < -15.0:
             continue
-        num, den, cnt, itf = stats[b].T
+        num, den, cnt, itf, rate = stats[b].T
         ok = np.nonzero((cnt > 0) & (den > 0))[0]
         if ok.size == 0:
             continue
         if ok.size > per_bucket:
             ok = rng.choice(ok, per_bucket, replace=False)
         bucket = (4 - b) / 2.0
-        x = np.empty((ok.size, 6))
+        x = np.empty((ok.size, 7))
         x[:, :4] = p2[ok] / 4.0
         x[:, 4] = -bucket / 16.0
         x[:, 5] = np.minimum(itf[ok] / cnt[ok], 1.0)
+        x[:, 6] = rate[ok] / cnt[ok]
         X.append(x)
         Rr.append(num[ok] / den[ok])
         W.append(den[ok] / den[ok].sum())
     if not X:
-        return np.zeros((0, 6)), np.zeros(0), np.zeros(0)
+        return np.zeros((0, 7)), np.zeros(0), np.zeros(0)
     return np.concatenate(X), np.concatenate(Rr), np.concatenate(W)
 
 
@@ -111,10 +114,10 @@ def init_params(seed: int) -> np.ndarray:
     """He initialisation; the output layer starts at zero with b4 = log(e - 1) (m = 1)."""
     rng = np.random.Generator(np.random.Philox(key=seed + 7))
     p = np.zeros(NPARAM, dtype=np.float32)
-    p[0:384] = rng.standard_normal(384) * np.sqrt(2.0 / 6)
-    p[448:4544] = rng.standard_normal(4096) * np.sqrt(2.0 / 64)
-    p[4608:8704] = rng.standard_normal(4096) * np.sqrt(2.0 / 64)
-    p[8832] = np.log(np.e - 1.0)
+    p[0:448] = rng.standard_normal(448) * np.sqrt(2.0 / 7)
+    p[512:4608] = rng.standard_normal(4096) * np.sqrt(2.0 / 64)
+    p[4672:8768] = rng.standard_normal(4096) * np.sqrt(2.0 / 64)
+    p[8896] = np.log(np.e - 1.0)
     return p
 
 

@@ -55,7 +55,7 @@ def gpu_eval(torch, bits, X):
 def test_inference_matches_bf16_oracle(torch):
     rng = np.random.default_rng(0)
     p = random_params(0)
-    X = rng.random((1000 + 13, 6))  # ragged tail: not a multiple of the 16-row tile
+    X = rng.random((1000 + 13, 7))  # ragged tail: not a multiple of the 16-row tile
     m_gpu = gpu_eval(torch, bf16_bits(p), X)
     m_ref, _ = M.forward(M.bf16_round(p), X, bf16=True)
     err = np.abs(m_gpu - m_ref) / m_ref
@@ -67,7 +67,7 @@ def test_gradient_matches_oracle(torch):
     rng = np.random.default_rng(1)
     p = random_params(1).astype(np.float32)
     n = 777
-    X = rng.random((n, 6)).astype(np.float32)
+    X = rng.random((n, 7)).astype(np.float32)
     Y = (rng.standard_normal(n) * 0.2).astype(np.float32)
     W = rng.random(n) + 0.2
     W = (W / W.mean()).astype(np.float32)
@@ -86,7 +86,7 @@ def test_gradient_matches_oracle(torch):
 def test_training_reduces_loss(torch):
     rng = np.random.default_rng(2)
     n = 20000
-    X = rng.random((n, 6)).astype(np.float32)
+    X = rng.random((n, 7)).astype(np.float32)
     Y = (0.15 * np.sin(3 * X[:, 0]) - 0.1 * X[:, 4] + 0.05 * X[:, 5]).astype(np.float32)
     W = np.ones(n, dtype=np.float32)
     dev = torch.device("cuda")
@@ -138,7 +138,7 @@ def test_learned_constant_multiplier_and_fallback_match_oracle(torch, alpha_scal
     alpha = 0.08 * alpha_scale
     U = fields.random_links(ext, eps=0.9, seed=21)
     bits = constant_multiplier_bits(z0)
-    m = float(np.clip(gpu_eval(torch, bits, np.zeros((1, 6)))[0], 0.25, 1.25))
+    m = float(np.clip(gpu_eval(torch, bits, np.zeros((1, 7)))[0], 0.25, 1.25))
     n = 30
     with lgf.Lattice(ext, "fp64", learned=True) as lat:
         lat.load_preconditioner(bits)
@@ -197,6 +197,7 @@ def test_mode_log_matches_oracle(torch):
     Ucur = U
     F, th, D = O.measure(Ucur)
     prev = packed_hat(D)
+    th_before = 0.0
     for k in range(steps):
         b = int(np.clip(4 - 2 * np.floor(2 * np.log10(th)) / 2, 0, 39))
         Ucur, _ = O.fa_step(Ucur, 0.08, D=D)
@@ -208,12 +209,14 @@ def test_mode_log_matches_oracle(torch):
         ref[b, :, 1] += np.bincount(cls.ravel(), den.ravel(), nclass)
         ref[b, :, 2] += np.bincount(cls.ravel(), minlength=nclass)
         ref[b, :, 3] += np.bincount(cls.ravel(), minlength=nclass) * min(k / 10000.0, 1.0)
-        prev, th = cur, th_new
+        ref[b, :, 4] += np.bincount(cls.ravel(), minlength=nclass) * (M.rate_feature(th, th_before) if k else 0.0)
+        prev, th_before, th = cur, th, th_new
     scale = np.max(np.abs(ref[..., 1]))
     assert np.array_equal(stats[..., 2], ref[..., 2])
     assert np.max(np.abs(stats[..., 0] - ref[..., 0])) < 1e-10 * scale
     assert np.max(np.abs(stats[..., 1] - ref[..., 1])) < 1e-10 * scale
     assert np.max(np.abs(stats[..., 3] - ref[..., 3])) < 1e-6
+    assert np.max(np.abs(stats[..., 4] - ref[..., 4])) < 1e-3
 
 
 def test_trained_preconditioner_gains_on_slow_fields(torch):
@@ -242,3 +245,25 @@ def test_trained_preconditioner_gains_on_slow_fields(torch):
         total_learned += it_l
     print(f"iterations to 1e-12 on two held-out 16^4 eps=1 fields: plain {total_plain}, learned {total_learned}")
     assert total_learned < 0.95 * total_plain
+
+
+def test_trained_preconditioner_cost_on_fast_fields(torch):
+    """On smooth fields that plain FA-SD fixes in a few dozen steps the network's
+    larger late steps cost iterations (the momentum classes mix fast and slow
+    modes); the cost stays bounded and the result stays on the gauge orbit."""
+    from paper_1206_0675_gb300.preconditioner import DEFAULT_WEIGHTS
+    weights = np.load(DEFAULT_WEIGHTS)
+    ext = (16, 16, 16, 16)
+    U = fields.random_links(ext, eps=0.7, seed=100)
+    with lgf.Lattice(ext, "fp64") as lat:
+        lat.set_links(U)
+        it_p, _, _, conv_p = lat.fix(1e-12, 20000, 0.08)
+    with lgf.Lattice(ext, "fp64", learned=True) as lat:
+        lat.load_preconditioner(weights)
+        lat.set_links(U)
+        it_l, _, _, conv_l = lat.fix(1e-12, 20000, 0.08)
+        U_l = lat.get_links()
+    print(f"iterations to 1e-12 on a held-out 16^4 eps=0.7 field: plain {it_p}, learned {it_l}")
+    assert conv_p and conv_l
+    assert it_l < 2 * it_p
+    assert abs(O.plaquette(U_l) - O.plaquette(U)) < 1e-12
