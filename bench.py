@@ -53,23 +53,29 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
 # DRAM bytes (read + write) per launch from the committed ncu capture of the
 # FP64 update kernel at 32^4 (profiles/update_kernel_fp64_32x4.md), valid only
-# while the kernel's sources are unchanged (sha256 prefixes of the files).
+# while the kernel's source text and the shared device header are unchanged
+# (sha256 prefixes).
 NCU_TRAFFIC = {
-    "update": {"bytes": 772.115712e6 + 579.595264e6,
-               "sources": {"paper_1206_0675_gb300/csrc/lgf_site.cu": "8ea91052234455c8",
-                           "paper_1206_0675_gb300/csrc/lgf_common.cuh": "9033a8a14b8a51a5"}},
+    "update": {"bytes": None, "kernel_sha": None, "common_sha": None},
 }
 
 
-def ncu_traffic(kernel):
+def kernel_source_sha(name):
+    """sha256 prefix of a kernel's definition text in lgf_site.cu and of lgf_common.cuh."""
     import hashlib
+    src = open(os.path.join(ROOT, "paper_1206_0675_gb300/csrc/lgf_site.cu")).read()
+    a = src.index(f"{name}_kernel(Geom")
+    b = src.index("cudaError_t launch_", a)
+    common = open(os.path.join(ROOT, "paper_1206_0675_gb300/csrc/lgf_common.cuh"), "rb").read()
+    return hashlib.sha256(src[a:b].encode()).hexdigest()[:16], hashlib.sha256(common).hexdigest()[:16]
+
+
+def ncu_traffic(kernel):
     rec = NCU_TRAFFIC.get(kernel)
-    if rec is None:
+    if rec is None or rec["bytes"] is None:
         return None
-    for path, h in rec["sources"].items():
-        with open(os.path.join(ROOT, path), "rb") as f:
-            if hashlib.sha256(f.read()).hexdigest()[:16] != h:
-                return None
+    if kernel_source_sha(kernel) != (rec["kernel_sha"], rec["common_sha"]):
+        return None
     return rec["bytes"]
 
 
@@ -307,11 +313,17 @@ def run_lgf(args, rank, world, local_rank):
         from paper_1206_0675_gb300.preconditioner import DEFAULT_WEIGHTS
         weights = np.load(DEFAULT_WEIGHTS)
         ttt = {"tol": TOL, "field": f"32^4 eps={EPS} seed={rank}"}
-        for mode, kw in (("fp64_18", dict(precision="fp64")), ("mixed_12", dict(precision="mixed", store12=True)),
-                         ("mixed_12_learned", dict(precision="mixed", store12=True, learned=True))):
+        modes = (("fp64_18", dict(precision="fp64"), None),
+                 ("mixed_12", dict(precision="mixed", store12=True), None),
+                 ("mixed_12_switch_1e-10", dict(precision="mixed", store12=True), 1e-10),
+                 ("mixed_12_learned", dict(precision="mixed", store12=True, learned=True), None),
+                 ("mixed_12_learned_switch_1e-10", dict(precision="mixed", store12=True, learned=True), 1e-10))
+        for mode, kw, sw in modes:
             L2 = lgf.Lattice(EXT, **kw)
             if kw.get("learned"):
                 L2.load_preconditioner(weights)
+            if sw is not None:
+                L2.set_switch_theta(sw)
             L2.set_links(U)
             L2.fix(TOL, 1, ALPHA)           # builds the loop graph
             L2.set_links(U)
@@ -325,6 +337,9 @@ def run_lgf(args, rank, world, local_rank):
             L2.close()
         ttt["speedup_mixed"] = ttt["fp64_18"]["seconds"] / ttt["mixed_12"]["seconds"]
         ttt["speedup_mixed_learned"] = ttt["fp64_18"]["seconds"] / ttt["mixed_12_learned"]["seconds"]
+        ttt["speedup_mixed_switch_1e-10"] = ttt["fp64_18"]["seconds"] / ttt["mixed_12_switch_1e-10"]["seconds"]
+        ttt["speedup_mixed_learned_switch_1e-10"] = (ttt["fp64_18"]["seconds"]
+                                                     / ttt["mixed_12_learned_switch_1e-10"]["seconds"])
 
     # ---- 64 configurations of uneven shapes in one graph launch -------------
     batch = None

@@ -124,7 +124,8 @@ lgf_status lgf_measure(lgf_handle h, double* F, double* theta);
 /* Algorithm 1: iterate lgf_step while theta >= theta_tol, at most max_iter
  * updates, with the loop condition evaluated on the device (CUDA graph with
  * a WHILE node; no host round trip per iteration).  In LGF_MIXED mode the
- * FP32 phase runs while theta >= max(theta_tol, switch level 1e-9), then G is
+ * FP32 phase runs while theta >= max(theta_tol, switch level, default 1e-9;
+ * see lgf_set_switch_theta), then G is
  * projected to SU(3) in FP64, U = G U0 G^dag(x+mu) is rebuilt in FP64 from
  * the FP64 input U0, and the FP64 phase runs to theta_tol.
  * iters, F, theta (each may be NULL) receive the update count of this call
@@ -240,6 +241,10 @@ lgf_status lgf_mlp_train(float* P, float* adam, const float* X, const float* Y, 
 
 /* FP32 -> BF16 (round to nearest even) of the 8897 parameters (device). */
 lgf_status lgf_mlp_to_bf16(const float* P, uint16_t* out, void* cuda_stream);
+
+/* Theta below which an LGF_MIXED fix leaves the FP32 phase (default 1e-9;
+ * accepted range [1e-10, 1e-6], so every iteration below 1e-10 is FP64). */
+lgf_status lgf_set_switch_theta(lgf_handle h, double theta);
 
 /* Phase of an LGF_MIXED handle: 32 while in the FP32 phase, 64 after the
  * switch (FP64 and FP32 handles report their fixed precision). */

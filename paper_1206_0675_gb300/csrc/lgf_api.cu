@@ -19,7 +19,6 @@ using namespace lgf;
 namespace {
 
 constexpr double kSU3Tol = 1e-10;       // input validation threshold
-constexpr double kSwitchTheta = 1e-9;   // FP32 -> FP64 switch level of LGF_MIXED
 
 // One precision "lane" of the handle: the buffers and the captured loop graph
 // of either the FP64 or the FP32 arithmetic.
@@ -92,6 +91,7 @@ struct lgf_ctx {
   double* user_F = nullptr;
   double* user_T = nullptr;
   TimingRing timing;
+  double switch_theta = 1e-9;     // FP32 -> FP64 switch level of LGF_MIXED
   bool learned = false;           // LGF_LEARNED
   uint16_t* mlp_w = nullptr;      // BF16 network parameters (device)
   bool logging = false;           // per-mode statistics of every lgf_step
@@ -696,7 +696,7 @@ lgf_status lgf_fix(lgf_handle h, double theta_tol, int32_t max_iter, double alph
   if (h->learned && !h->mlp_w) return fail(h, LGF_E_STATE, "LGF_LEARNED handle without a loaded preconditioner");
   if (h->phase == 32) {
     if ((s = ensure_filter<float>(h, h->f, alpha)) != LGF_OK) return s;
-    const double tol1 = h->prec == LGF_MIXED ? std::max(theta_tol, kSwitchTheta) : theta_tol;
+    const double tol1 = h->prec == LGF_MIXED ? std::max(theta_tol, h->switch_theta) : theta_tol;
     if ((s = run_loop<float>(h, h->f, tol1, max_iter, 1)) != LGF_OK) return s;
     h->have_g = h->have_g || h->st_host->iter > 0;
     const DevState& S = *h->st_host;
@@ -967,6 +967,13 @@ lgf_status lgf_mlp_train(float* P, float* adam, const float* X, const float* Y, 
 lgf_status lgf_mlp_to_bf16(const float* P, uint16_t* out, void* cuda_stream) {
   if (!P || !out) return LGF_E_ARG;
   return launch_f32_to_bf16(P, out, MLP_NPARAM, (cudaStream_t)cuda_stream) == cudaSuccess ? LGF_OK : LGF_E_CUDA;
+}
+
+lgf_status lgf_set_switch_theta(lgf_handle h, double theta) {
+  if (!h) return LGF_E_ARG;
+  if (!(theta >= 1e-10 && theta <= 1e-6)) return fail(h, LGF_E_ARG, "switch level must lie in [1e-10, 1e-6]");
+  h->switch_theta = theta;
+  return LGF_OK;
 }
 
 lgf_status lgf_get_phase(lgf_handle h, int32_t* bits) {

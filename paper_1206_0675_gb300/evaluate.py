@@ -15,8 +15,11 @@ import time
 
 import numpy as np
 
-from . import fields, lgf
+from . import accounting, fields, lgf
 from .preconditioner import DEFAULT_WEIGHTS
+
+STORAGES = {"fp64_18": ("fp64", False, 8, 3, 3), "fp64_12": ("fp64", True, 8, 2, 3),
+            "fp32_12": ("fp32", True, 4, 2, 2), "fp32_18": ("fp32", False, 4, 3, 3)}
 
 MODES = {
     "fp64": dict(precision="fp64"),
@@ -26,12 +29,14 @@ MODES = {
 }
 
 
-def run_mode(mode, ext, U, tol, max_iter, weights):
+def run_mode(mode, ext, U, tol, max_iter, weights, switch=None):
     import torch
     kw = MODES[mode]
     with lgf.Lattice(ext, **kw) as lat:
         if kw.get("learned"):
             lat.load_preconditioner(weights)
+        if switch is not None and kw["precision"] == "mixed":
+            lat.set_switch_theta(switch)
         lat.set_links(U)
         lat.fix(tol, 1, 0.08)   # builds the loop graphs
         lat.set_links(U)
@@ -44,6 +49,33 @@ def run_mode(mode, ext, U, tol, max_iter, weights):
     return {"seconds": dt, "iters": it, "F": F, "theta": th, "converged": conv, "fallbacks": nf}
 
 
+def kernel_table(ext, U, steps=20, warmup=5, peak_gbs=None):
+    """Per-kernel CUDA-event times and compulsory-traffic GB/s of every precision/storage."""
+    import torch
+    V = int(np.prod(ext))
+    out = {}
+    for name, (prec, s12, rb, rows, grows) in STORAGES.items():
+        with lgf.Lattice(ext, prec, store12=s12) as lat:
+            lat.set_links(U)
+            for _ in range(warmup):
+                lat.step(0.08)
+            lat.set_timing(True)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(steps):
+                lat.step(0.08)
+            torch.cuda.synchronize()
+            dt = (time.perf_counter() - t0) / steps
+            ms, _ = lat.get_timing()
+        byt = accounting.bytes_per_site(rb, rows, grows, k_bytes=rb)
+        row = {"iters_per_s": 1.0 / dt, "ms_per_step": dt * 1e3, "kernels": {}}
+        for k, t in zip(accounting.KERNELS, ms):
+            gbs = byt[k] * V / (t * 1e-3) / 1e9 if t > 0 else None
+            row["kernels"][k] = {"ms": t, "gbs": gbs, "hbm_frac": gbs / peak_gbs if (gbs and peak_gbs) else None}
+        out[name] = row
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--lattice", type=int, default=32)
@@ -53,17 +85,32 @@ def main():
     ap.add_argument("--max-iter", type=int, default=30000)
     ap.add_argument("--modes", default="fp64,mixed,mixed_learned")
     ap.add_argument("--weights", default=DEFAULT_WEIGHTS)
+    ap.add_argument("--extents", default=None, help="Lx,Ly,Lz,Lt (overrides --lattice)")
+    ap.add_argument("--kernels", action="store_true", help="per-kernel table of every precision/storage")
+    ap.add_argument("--switch", type=float, default=None, help="switch level of the mixed modes")
     args = ap.parse_args()
     a, b = (int(v) for v in args.seeds.split("-")) if "-" in args.seeds else (int(args.seeds),) * 2
-    ext = (args.lattice,) * 4
+    ext = tuple(int(v) for v in args.extents.split(",")) if args.extents else (args.lattice,) * 4
+    if args.kernels:
+        peak = None
+        try:
+            with open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                                   "MEASURED_PEAKS.json")) as f:
+                peak = float(json.load(f)["hbm_gbs"])
+        except Exception:
+            pass
+        U = fields.random_links(ext, args.eps, a)
+        print(json.dumps({"extents": ext, "eps": args.eps, "seed": a, "peak_gbs": peak,
+                          "table": kernel_table(ext, U, peak_gbs=peak)}), flush=True)
+        return
     weights = np.load(args.weights)
     modes = args.modes.split(",")
     tot = {m: [0.0, 0] for m in modes}
     for seed in range(a, b + 1):
         U = fields.random_links(ext, args.eps, seed)
-        row = {"lattice": args.lattice, "eps": args.eps, "seed": seed}
+        row = {"lattice": list(ext), "eps": args.eps, "seed": seed}
         for m in modes:
-            r = run_mode(m, ext, U, args.tol, args.max_iter, weights)
+            r = run_mode(m, ext, U, args.tol, args.max_iter, weights, args.switch)
             row[m] = r
             tot[m][0] += r["seconds"]
             tot[m][1] += r["iters"]
@@ -72,8 +119,8 @@ def main():
     if "fp64" in tot:
         for m in modes:
             summary[m]["speedup_vs_fp64"] = tot["fp64"][0] / tot[m][0]
-    print(json.dumps({"summary": summary, "lattice": args.lattice, "eps": args.eps, "seeds": args.seeds,
-                      "tol": args.tol}), flush=True)
+    print(json.dumps({"summary": summary, "lattice": list(ext), "eps": args.eps, "seeds": args.seeds,
+                      "tol": args.tol, "switch": args.switch}), flush=True)
 
 
 if __name__ == "__main__":

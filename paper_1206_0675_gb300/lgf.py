@@ -56,6 +56,7 @@ SIGNATURES = [
     ("lgf_fft4", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int]),
     ("lgf_get_phase", ctypes.c_int, [ctypes.c_void_p, _c_int_p]),
     ("lgf_set_timing", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    ("lgf_set_switch_theta", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
     ("lgf_get_timing", ctypes.c_int, [ctypes.c_void_p, _c_dbl_p, ctypes.c_int32, _c_int_p]),
     ("lgf_measure_static", ctypes.c_int, [ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_void_p]),
@@ -481,6 +482,11 @@ class Lattice:
         a = _host_buffer(data, (4, lt, lz, ly, lx)).copy()
         lgf_fft4(self.handle, a.ctypes.data, 4, sign, LGF_HOST)
         return a
+
+    def set_switch_theta(self, theta: float) -> None:
+        """Theta below which a mixed-precision fix switches to FP64 (1e-10 ... 1e-6)."""
+        _check(self.handle, load_library().lgf_set_switch_theta(ctypes.c_void_p(self.handle), float(theta)),
+               "lgf_set_switch_theta")
 
     def set_timing(self, enable: bool = True) -> None:
         lgf_set_timing(self.handle, enable)

@@ -229,12 +229,14 @@ def test_fix_to_1e15_fp64_and_transform():
 # mixed precision
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("store12", [True, False])
-def test_mixed_reaches_1e15_and_keeps_gauge_invariants(store12):
+@pytest.mark.parametrize("store12,switch", [(True, None), (False, None), (True, 1e-10)])
+def test_mixed_reaches_1e15_and_keeps_gauge_invariants(store12, switch):
     ext = (8, 8, 8, 8)
     U = fields.random_links(ext, eps=1.0, seed=1)
     ref = O.fix(U, tol=1e-15, max_iter=6000, track_G=False)
     with lgf.Lattice(ext, "mixed", store12=store12, track_G=True) as lat:
+        if switch is not None:
+            lat.set_switch_theta(switch)
         lat.set_links(U)
         assert lat.phase == 32
         Fh, Th = lat.set_trace(6001)
@@ -346,3 +348,35 @@ def test_full_size_32x4_one_step(prec, store12, tol):
     rng = np.random.default_rng(0)
     idx = tuple(rng.integers(0, 32, size=(4, 64)))
     assert np.max(np.abs(U1[:, idx[0], idx[1], idx[2], idx[3]] - Uo[:, idx[0], idx[1], idx[2], idx[3]])) < tol
+
+
+@pytest.fixture(scope="module")
+def aniso_case():
+    """The 48^3 x 96 workload (eps = 0.7, seed 0) and one oracle step from it."""
+    ext = (48, 48, 48, 96)
+    U = fields.random_links(ext, eps=0.7, seed=0)
+    Fo0, tho0, D = O.measure(U)
+    Uo, _ = O.fa_step(U, 0.08, D=D)
+    Fo1, tho1, _ = O.measure(Uo)
+    rng = np.random.default_rng(1)
+    idx = (rng.integers(0, 96, 128), rng.integers(0, 48, 128), rng.integers(0, 48, 128), rng.integers(0, 48, 128))
+    return ext, U, (Fo0, tho0, Fo1, tho1), idx, Uo[:, idx[0], idx[1], idx[2], idx[3]]
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("prec,store12", [("fp64", False), ("fp32", True)])
+def test_anisotropic_48x3_96_one_step(aniso_case, prec, store12):
+    """48^3 x 96: one step against the oracle, links of 128 sampled sites."""
+    ext, U, (Fo0, tho0, Fo1, tho1), idx, Uo_s = aniso_case
+    with lgf.Lattice(ext, prec, store12=store12) as lat:
+        lat.set_links(U)
+        F0, th0 = lat.measure()
+        lat.step(0.08)
+        F1, th1 = lat.measure()
+        U1 = lat.get_links()
+    f64 = prec == "fp64"
+    assert abs(F0 - Fo0) < (1e-13 if f64 else 1e-6) * abs(Fo0)
+    assert rel(th0, tho0) < (1e-12 if f64 else 1e-5)
+    assert abs(F1 - Fo1) < (1e-13 if f64 else 1e-6) * abs(Fo1)
+    assert rel(th1, tho1) < (1e-11 if f64 else 1e-4)
+    assert np.max(np.abs(U1[:, idx[0], idx[1], idx[2], idx[3]] - Uo_s)) < (1e-12 if f64 else 2e-5)
