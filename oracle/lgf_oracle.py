@@ -39,6 +39,12 @@ Readings of the paper (where it is silent or ambiguous)
    reunitarised (Sec. 2, the sentence after Eq. (eq:gx)).  Reunitarisation is
    Gram-Schmidt on rows 1 and 2 with row 3 = (a x b)^* (Sec. 3.2, the
    12-real reconstruction formula), so that det g = 1.
+   The exact-exponential variant (``exact_exp=True``) evaluates the
+   exponential of Eq. (eq:gx) itself, ``g = exp(Delta')`` with Delta'
+   traceless anti-Hermitian, and then applies the same Gram-Schmidt
+   projection (a change at rounding level only for a matrix that is
+   already in SU(3)), so that both variants hand the update a g built
+   the same way.
 6. The stop test is strict: iterate while theta >= tol (Algorithm 1); the
    iteration count is the number of link updates performed.
 7. The FFT is applied to all 9 complex entries of the 3x3 matrix Delta_A
@@ -225,15 +231,32 @@ def reunitarize(M: np.ndarray) -> np.ndarray:
     return np.stack([a, b, c], axis=-2)
 
 
-def gauge_transform_from_divergence(D: np.ndarray, K: np.ndarray) -> np.ndarray:
+def expm_antihermitian(X: np.ndarray) -> np.ndarray:
+    """exp(X) for traceless anti-Hermitian 3x3 matrices X (reading 5, exact variant).
+
+    X = i Q with Q Hermitian; Q = W diag(lambda) W^dagger (eigendecomposition),
+    so exp(X) = W diag(exp(i lambda)) W^dagger.
+    """
+    Q = -1j * X
+    Q = 0.5 * (Q + dagger(Q))  # Hermitian part: removes rounding asymmetry only
+    lam, W = np.linalg.eigh(Q)
+    return (W * np.exp(1j * lam)[..., None, :]) @ dagger(W)
+
+
+def gauge_transform_from_divergence(D: np.ndarray, K: np.ndarray, exact_exp: bool = False) -> np.ndarray:
     """Eq. (eq:gx) to first order, then reunitarised.
 
     Algorithm 1: for every element of the Delta matrix, FFT forward, apply
     the momentum filter, FFT backward, normalise; then for all x obtain
-    g(x) = reunitarize(1 + Delta'(x)).
+    g(x) = reunitarize(1 + Delta'(x)).  With ``exact_exp`` the exponential is
+    evaluated instead: g(x) = reunitarize(exp(Delta'(x))), Delta' taken as
+    its traceless anti-Hermitian part (it is one up to rounding, because the
+    filter is real and even in k).
     """
     Dhat = fft4(D)
     Dp = ifft4(Dhat * K[..., None, None])
+    if exact_exp:
+        return reunitarize(expm_antihermitian(traceless_antihermitian(Dp)))
     gt = Dp.copy()
     for i in range(NC):
         gt[..., i, i] += 1.0
@@ -253,23 +276,24 @@ def apply_gauge(U: np.ndarray, g: np.ndarray) -> np.ndarray:
 # ---------------------------------------------------------------------------
 
 def fa_step(U: np.ndarray, alpha: float = ALPHA_DEFAULT, K: np.ndarray | None = None,
-            D: np.ndarray | None = None) -> tuple[np.ndarray, np.ndarray]:
+            D: np.ndarray | None = None, exact_exp: bool = False) -> tuple[np.ndarray, np.ndarray]:
     """One body of the Algorithm 1 loop: FFT, filter, IFFT, g, link update.
 
     Returns (new links, g).  ``D`` may be passed when the divergence of ``U``
     is already known (it is the measurement that ends the previous body).
+    ``exact_exp`` selects g = exp(Delta') over the first-order form.
     """
     if K is None:
         K = fa_filter(extents_of(U), alpha)
     if D is None:
         D = divergence(U)
-    g = gauge_transform_from_divergence(D, K)
+    g = gauge_transform_from_divergence(D, K, exact_exp)
     return apply_gauge(U, g), g
 
 
 def fix(U: np.ndarray, alpha: float = ALPHA_DEFAULT, tol: float = 1e-15,
         max_iter: int = 1000, K: np.ndarray | None = None, track_G: bool = True,
-        callback=None):
+        callback=None, exact_exp: bool = False):
     """Algorithm 1: measure; while theta >= tol: step and measure again.
 
     Returns a dict with the final links, the accumulated transform
@@ -284,7 +308,7 @@ def fix(U: np.ndarray, alpha: float = ALPHA_DEFAULT, tol: float = 1e-15,
     F_hist, th_hist = [F], [th]
     k = 0
     while th >= tol and k < max_iter:
-        U, g = fa_step(U, alpha, K, D)
+        U, g = fa_step(U, alpha, K, D, exact_exp)
         if track_G:
             G = g @ G
         F, th, D = measure(U)
