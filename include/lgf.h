@@ -78,7 +78,9 @@ enum {
   LGF_STORE12 = 1 << 0,   /* keep rows 1-2 (12 reals), rebuild row 3 = (a x b)^* (Sec. 3.2) */
   LGF_TRACK_G = 1 << 1,   /* accumulate G(x) = g_k(x)...g_1(x) for lgf_get_transform */
   LGF_LEARNED = 1 << 2,   /* multiply the filter by the learned per-mode multiplier (lgf_load_preconditioner) */
-  LGF_PLAIN_SD = 1 << 3   /* plain steepest descent: filter K(k) = alpha (no Fourier acceleration) */
+  LGF_PLAIN_SD = 1 << 3,  /* plain steepest descent: filter K(k) = alpha (no Fourier acceleration) */
+  LGF_EXACT_EXP = 1 << 4  /* g = reunitarize(exp(Delta')) instead of the first-order reunitarize(1 + Delta')
+                             of Sec. 2 (the exponential of Eq. (eq:gx) evaluated exactly, in FP64) */
 };
 
 enum { LGF_HOST = 0, LGF_DEVICE = 1 };
@@ -89,7 +91,8 @@ enum { LGF_HOST = 0, LGF_DEVICE = 1 };
  *   (all extents up to 96, and 128 in z and t, are accepted); otherwise
  *   LGF_E_UNSUPPORTED.
  * prec: LGF_FP64, LGF_FP32 or LGF_MIXED.  flags: LGF_STORE12, LGF_TRACK_G,
- *   LGF_PLAIN_SD (LGF_MIXED always tracks G).
+ *   LGF_PLAIN_SD, LGF_LEARNED, LGF_EXACT_EXP (LGF_MIXED always tracks G);
+ *   any other bit gives LGF_E_ARG.
  * cuda_stream: a cudaStream_t or NULL.  out: receives the handle.
  * Allocates all device workspace up front (LGF_E_NOMEM if it does not fit). */
 lgf_status lgf_create(const int32_t extents[4], lgf_precision prec, uint32_t flags, void* cuda_stream,

@@ -234,6 +234,8 @@ template <typename R> int body_kernels(const lgf_ctx* h, int* ks) {
 
 inline int kernel_category(int k) { return k <= K_MEAS ? k : 5; }
 
+inline int exact_exp(const lgf_ctx* h) { return (h->flags & LGF_EXACT_EXP) ? 1 : 0; }
+
 template <typename R> cudaError_t enqueue_kernel(lgf_ctx* h, Lane<R>& L, int k, unsigned long long cond,
                                                   int use_cond, cudaStream_t s);
 
@@ -243,7 +245,9 @@ template <> cudaError_t enqueue_kernel<double>(lgf_ctx* h, Lane<double>& L, int 
   switch (k) {
     case K_A: return launch_fft_xy<double>(g, L.plan, L.D, L.tw, L.pos, -1, 4, s);
     case K_B: return launch_fft_zt<double>(g, L.plan, L.D, L.tw, L.pos, L.K, 0, 4, s, L.mtab, &h->st->use_m);
-    case K_C: return launch_fft_xy_inv_gauge<double, double, 3>(g, L.plan, L.D, L.tw, L.pos, L.g, L.G, s);
+    case K_C:
+      return launch_fft_xy_inv_gauge<double, double, 3>(g, L.plan, L.D, L.tw, L.pos, L.g, L.G, s, Batch(),
+                                                        exact_exp(h));
     case K_UPD:
       return L.rows == 3 ? launch_update<double, 3, 3>(g, L.U, L.g, s) : launch_update<double, 2, 3>(g, L.U, L.g, s);
     case K_MEAS: return enqueue_measure<double>(h, L, 1, cond, use_cond, s);
@@ -262,8 +266,10 @@ template <> cudaError_t enqueue_kernel<float>(lgf_ctx* h, Lane<float>& L, int k,
     case K_A: return launch_fft_xy<float>(g, L.plan, L.D, L.tw, L.pos, -1, 4, s);
     case K_B: return launch_fft_zt<float>(g, L.plan, L.D, L.tw, L.pos, L.K, 0, 4, s, L.mtab, &h->st->use_m);
     case K_C:
-      return L.grows == 2 ? launch_fft_xy_inv_gauge<float, float, 2>(g, L.plan, L.D, L.tw, L.pos, L.g, L.G, s)
-                          : launch_fft_xy_inv_gauge<float, float, 3>(g, L.plan, L.D, L.tw, L.pos, L.g, L.G, s);
+      return L.grows == 2 ? launch_fft_xy_inv_gauge<float, float, 2>(g, L.plan, L.D, L.tw, L.pos, L.g, L.G, s,
+                                                                     Batch(), exact_exp(h))
+                          : launch_fft_xy_inv_gauge<float, float, 3>(g, L.plan, L.D, L.tw, L.pos, L.g, L.G, s,
+                                                                     Batch(), exact_exp(h));
     case K_UPD: return L.grows == 2 ? launch_update<float, 2, 2>(g, L.U, L.g, s) : launch_update<float, 3, 3>(g, L.U, L.g, s);
     case K_MEAS: return enqueue_measure<float>(h, L, 1, cond, use_cond, s);
     case K_REVERT:
@@ -517,7 +523,7 @@ lgf_status lgf_create(const int32_t extents[4], lgf_precision prec, uint32_t fla
   if (!extents || !out) return LGF_E_ARG;
   *out = nullptr;
   if (prec != LGF_FP64 && prec != LGF_FP32 && prec != LGF_MIXED) return LGF_E_ARG;
-  if (flags & ~(uint32_t)(LGF_STORE12 | LGF_TRACK_G | LGF_PLAIN_SD | LGF_LEARNED)) return LGF_E_ARG;
+  if (flags & ~(uint32_t)(LGF_STORE12 | LGF_TRACK_G | LGF_PLAIN_SD | LGF_LEARNED | LGF_EXACT_EXP)) return LGF_E_ARG;
   for (int mu = 0; mu < 4; ++mu)
     if (!extent_ok(extents[mu])) return LGF_E_UNSUPPORTED;
   lgf_ctx* h = new (std::nothrow) lgf_ctx();

@@ -341,6 +341,96 @@ __device__ __forceinline__ void gauge_from_packed(double2 f0, double2 f1, double
   v[2] = cscale<double>(v[2], i2);
 }
 
+// Rows 1 and 2 of g = exp(X) (the exponential of Eq. (eq:gx) evaluated
+// exactly instead of to first order), for X traceless anti-Hermitian packed
+// as above, followed by the same Gram-Schmidt projection.
+//
+// With X = iQ (Q Hermitian, traceless) the Cayley-Hamilton theorem gives
+// Q^3 = u Q + w 1, u = tr(Q^2)/2, w = det Q, so exp(iQ) = c0 1 + c1 Q + c2 Q^2.
+// Scaling and squaring (Moler and Van Loan, "Nineteen dubious ways to compute
+// the exponential of a matrix", 1978): Z = Q / 2^s with |Z|_F <= 1/4, the
+// Taylor series of exp(iZ) to order 12 (remainder below 3e-18) reduced to
+// c0 + c1 Z + c2 Z^2 through Z^3 = uz Z + wz 1, then s squarings carried out on
+// the three coefficients with the same reduction.
+__device__ __forceinline__ void gauge_exp_from_packed(double2 f0, double2 f1, double2 f2, double2 f3, double2 u[3],
+                                                      double2 v[3]) {
+  const double a = f0.x, d = f0.y, q33 = -(a + d);
+  // Q = -iX: off-diagonal entries q12, q13, q23; Q_ji = conj(Q_ij)
+  const double2 q12 = make_double2(f1.y, -f1.x), q13 = make_double2(f2.y, -f2.x), q23 = make_double2(f3.y, -f3.x);
+  const double n12 = cnorm2<double>(q12), n13 = cnorm2<double>(q13), n23 = cnorm2<double>(q23);
+  const double uq = 0.5 * (a * a + d * d + q33 * q33) + n12 + n13 + n23;
+  const double2 t = cconjmul<double>(q13, cmul<double>(q12, q23));  // q12 q23 conj(q13)
+  const double wq = a * d * q33 + 2.0 * t.x - a * n23 - d * n13 - q33 * n12;
+  int s = 0;
+  double n2 = 2.0 * uq, uz = uq, wz = wq;
+  while (n2 > 0.0625 && s < 64) {
+    n2 *= 0.25;
+    uz *= 0.25;
+    wz *= 0.125;
+    ++s;
+  }
+  // Z^n / n! = al 1 + be Z + ga Z^2 (real); exp(iZ) = sum_n i^n Z^n / n!
+  double al = 1.0, be = 0.0, ga = 0.0;
+  double2 c0 = make_double2(1.0, 0.0), c1 = make_double2(0.0, 0.0), c2 = make_double2(0.0, 0.0);
+#pragma unroll
+  for (int n = 1; n <= 12; ++n) {
+    const double inv = 1.0 / (double)n;
+    const double al2 = ga * wz * inv, be2 = fma(ga, uz, al) * inv, ga2 = be * inv;
+    al = al2;
+    be = be2;
+    ga = ga2;
+    const double sg = ((n & 3) < 2) ? 1.0 : -1.0;
+    if (n & 1) {
+      c0.y = fma(sg, al, c0.y);
+      c1.y = fma(sg, be, c1.y);
+      c2.y = fma(sg, ga, c2.y);
+    } else {
+      c0.x = fma(sg, al, c0.x);
+      c1.x = fma(sg, be, c1.x);
+      c2.x = fma(sg, ga, c2.x);
+    }
+  }
+  double h1 = 1.0;
+  for (int k = 0; k < s; ++k) {
+    const double2 p00 = cmul<double>(c0, c0), p12 = cmul<double>(c1, c2), p01 = cmul<double>(c0, c1);
+    const double2 p22 = cmul<double>(c2, c2), p02 = cmul<double>(c0, c2), p11 = cmul<double>(c1, c1);
+    c0 = make_double2(fma(2.0 * wz, p12.x, p00.x), fma(2.0 * wz, p12.y, p00.y));
+    c1 = make_double2(fma(wz, p22.x, fma(2.0 * uz, p12.x, 2.0 * p01.x)),
+                      fma(wz, p22.y, fma(2.0 * uz, p12.y, 2.0 * p01.y)));
+    c2 = make_double2(fma(uz, p22.x, fma(2.0, p02.x, p11.x)), fma(uz, p22.y, fma(2.0, p02.y, p11.y)));
+    h1 *= 0.5;
+  }
+  c1 = cscale<double>(c1, h1);       // coefficient of Q
+  c2 = cscale<double>(c2, h1 * h1);  // coefficient of Q^2
+  // rows 1 and 2 of Q^2
+  const double s11 = a * a + n12 + n13, s22 = n12 + d * d + n23;
+  const double2 s12 = cadd<double>(cscale<double>(q12, a + d), cmulc<double>(q13, q23));  // + q13 conj(q23)
+  const double2 s13 = cadd<double>(cscale<double>(q13, -d), cmul<double>(q12, q23));
+  const double2 s23 = cadd<double>(cconjmul<double>(q12, q13), cscale<double>(q23, -a));  // conj(q12) q13 - a q23
+  const double2 s21 = make_double2(s12.x, -s12.y);
+  const double2 q21 = make_double2(q12.x, -q12.y);
+  double2 r1[3], r2[3];
+  r1[0] = cadd<double>(cadd<double>(c0, cscale<double>(c1, a)), cscale<double>(c2, s11));
+  r1[1] = cadd<double>(cmul<double>(c1, q12), cmul<double>(c2, s12));
+  r1[2] = cadd<double>(cmul<double>(c1, q13), cmul<double>(c2, s13));
+  r2[0] = cadd<double>(cmul<double>(c1, q21), cmul<double>(c2, s21));
+  r2[1] = cadd<double>(cadd<double>(c0, cscale<double>(c1, d)), cscale<double>(c2, s22));
+  r2[2] = cadd<double>(cmul<double>(c1, q23), cmul<double>(c2, s23));
+  // Gram-Schmidt: u = r1/|r1|, v = (r2 - <u,r2> u)/|.|
+  const double i1 = rsqrt(cnorm2<double>(r1[0]) + cnorm2<double>(r1[1]) + cnorm2<double>(r1[2]));
+#pragma unroll
+  for (int j = 0; j < 3; ++j) u[j] = cscale<double>(r1[j], i1);
+  double2 ip = cconjmul<double>(u[0], r2[0]);
+  ip = cadd<double>(ip, cconjmul<double>(u[1], r2[1]));
+  ip = cadd<double>(ip, cconjmul<double>(u[2], r2[2]));
+  const double2 nip = make_double2(-ip.x, -ip.y);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) v[j] = cfma<double>(nip, u[j], r2[j]);
+  const double i2 = rsqrt(cnorm2<double>(v[0]) + cnorm2<double>(v[1]) + cnorm2<double>(v[2]));
+#pragma unroll
+  for (int j = 0; j < 3; ++j) v[j] = cscale<double>(v[j], i2);
+}
+
 template <typename RG, int GROWS>
 __device__ __forceinline__ void store_gauge(int64_t V, int64_t s, const double2 u[3], const double2 v[3],
                                             C2<RG>* __restrict__ gf, C2<RG>* __restrict__ Gf) {
@@ -390,7 +480,7 @@ __device__ __forceinline__ void store_gauge(int64_t V, int64_t s, const double2 
   }
 }
 
-template <typename R, typename RG, int GROWS>
+template <typename R, typename RG, int GROWS, bool EXPG>
 __global__ void __launch_bounds__(512) fft_xy_inv_gauge_kernel(Geom g, FFTDir dx, FFTDir dy, const C2<R>* __restrict__ data,
                                         const C2<R>* __restrict__ twg, const short* __restrict__ posg,
                                         C2<RG>* __restrict__ gf, C2<RG>* __restrict__ Gf, Lines lx, Lines ly,
@@ -418,15 +508,19 @@ __global__ void __launch_bounds__(512) fft_xy_inv_gauge_kernel(Geom g, FFTDir dx
     const int y = (int)cd.b.div((uint32_t)i), x = i - y * Lx;
     const int o = pos[Lx + y] * RS + pos[x];
     double2 u[3], v[3];
-    gauge_from_packed(ccast<double, R>(tile[o]), ccast<double, R>(tile[PS + o]), ccast<double, R>(tile[2 * PS + o]),
-                      ccast<double, R>(tile[3 * PS + o]), u, v);
+    if constexpr (EXPG)
+      gauge_exp_from_packed(ccast<double, R>(tile[o]), ccast<double, R>(tile[PS + o]),
+                            ccast<double, R>(tile[2 * PS + o]), ccast<double, R>(tile[3 * PS + o]), u, v);
+    else
+      gauge_from_packed(ccast<double, R>(tile[o]), ccast<double, R>(tile[PS + o]), ccast<double, R>(tile[2 * PS + o]),
+                        ccast<double, R>(tile[3 * PS + o]), u, v);
     store_gauge<RG, GROWS>(g.V, slab * plane + i, u, v, gf, Gf);
   }
 }
 
 // Unfused variant for planes whose four fields do not fit in shared memory:
 // the inverse (x, y) transform has already been applied to data.
-template <typename R, typename RG, int GROWS>
+template <typename R, typename RG, int GROWS, bool EXPG>
 __global__ void gauge_from_delta_kernel(Geom g, const C2<R>* __restrict__ data, C2<RG>* __restrict__ gf,
                                         C2<RG>* __restrict__ Gf, Batch B) {
   if (batch_skip(B)) return;
@@ -436,8 +530,12 @@ __global__ void gauge_from_delta_kernel(Geom g, const C2<R>* __restrict__ data, 
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= g.V) return;
   double2 u[3], v[3];
-  gauge_from_packed(ccast<double, R>(data[s]), ccast<double, R>(data[g.V + s]), ccast<double, R>(data[2 * g.V + s]),
-                    ccast<double, R>(data[3 * g.V + s]), u, v);
+  if constexpr (EXPG)
+    gauge_exp_from_packed(ccast<double, R>(data[s]), ccast<double, R>(data[g.V + s]),
+                          ccast<double, R>(data[2 * g.V + s]), ccast<double, R>(data[3 * g.V + s]), u, v);
+  else
+    gauge_from_packed(ccast<double, R>(data[s]), ccast<double, R>(data[g.V + s]), ccast<double, R>(data[2 * g.V + s]),
+                      ccast<double, R>(data[3 * g.V + s]), u, v);
   store_gauge<RG, GROWS>(g.V, s, u, v, gf, Gf);
 }
 
@@ -600,24 +698,32 @@ cudaError_t launch_fft_zt(const Geom& g, const FFTPlan& p, C2<R>* data, const C2
   return cudaGetLastError();
 }
 
-template <typename R, typename RG, int GROWS>
-cudaError_t launch_fft_xy_inv_gauge(const Geom& g, const FFTPlan& p, C2<R>* data, const C2<R>* tw, const short* pos,
-                                    C2<RG>* gfield, C2<RG>* Gfield, cudaStream_t s, const Batch& B) {
+template <typename R, typename RG, int GROWS, bool EXPG>
+static cudaError_t launch_pass_c(const Geom& g, const FFTPlan& p, C2<R>* data, const C2<R>* tw, const short* pos,
+                                 C2<RG>* gfield, C2<RG>* Gfield, cudaStream_t s, const Batch& B) {
   cudaError_t e;
   if (!p.fuse_g) {
     if ((e = launch_fft_xy<R>(g, p, data, tw, pos, +1, 4, s, B)) != cudaSuccess) return e;
-    gauge_from_delta_kernel<R, RG, GROWS><<<dim3((unsigned)((g.V + 127) / 128), 1, (unsigned)B.n), 128, 0, s>>>(
+    gauge_from_delta_kernel<R, RG, GROWS, EXPG><<<dim3((unsigned)((g.V + 127) / 128), 1, (unsigned)B.n), 128, 0, s>>>(
         g, data, gfield, Gfield, B);
     return cudaGetLastError();
   }
   const size_t smem = p.smem_c;
-  if ((e = allow_smem(fft_xy_inv_gauge_kernel<R, RG, GROWS>, smem)) != cudaSuccess) return e;
+  if ((e = allow_smem(fft_xy_inv_gauge_kernel<R, RG, GROWS, EXPG>, smem)) != cudaSuccess) return e;
   const int Lx = g.L[0], Ly = g.L[1], RS = Lx + 1, PS = Ly * RS;
   const Lines lx = make_lines(4 * Ly, 4 * Ly, RS, 0, 1), ly = make_lines(4 * Lx, Lx, 1, PS, RS);
   const CopyDiv cd{FastDiv::make((uint32_t)(Lx * Ly)), FastDiv::make((uint32_t)Lx)};
-  fft_xy_inv_gauge_kernel<R, RG, GROWS><<<dim3((unsigned)(g.L[2] * g.L[3]), 1, (unsigned)B.n), p.threads_c, smem, s>>>(
-      g, p.d[0], p.d[1], data, tw, pos, gfield, Gfield, lx, ly, cd, B);
+  fft_xy_inv_gauge_kernel<R, RG, GROWS, EXPG>
+      <<<dim3((unsigned)(g.L[2] * g.L[3]), 1, (unsigned)B.n), p.threads_c, smem, s>>>(g, p.d[0], p.d[1], data, tw, pos,
+                                                                                    gfield, Gfield, lx, ly, cd, B);
   return cudaGetLastError();
+}
+
+template <typename R, typename RG, int GROWS>
+cudaError_t launch_fft_xy_inv_gauge(const Geom& g, const FFTPlan& p, C2<R>* data, const C2<R>* tw, const short* pos,
+                                    C2<RG>* gfield, C2<RG>* Gfield, cudaStream_t s, const Batch& B, int exact_exp) {
+  return exact_exp ? launch_pass_c<R, RG, GROWS, true>(g, p, data, tw, pos, gfield, Gfield, s, B)
+                   : launch_pass_c<R, RG, GROWS, false>(g, p, data, tw, pos, gfield, Gfield, s, B);
 }
 
 template cudaError_t launch_fft_xy<double>(const Geom&, const FFTPlan&, C2<double>*, const C2<double>*, const short*,
@@ -632,7 +738,8 @@ template cudaError_t launch_fft_zt<float>(const Geom&, const FFTPlan&, C2<float>
                                           const Batch&);
 #define LGF_INST_C(R, RG, GR)                                                                                    \
   template cudaError_t launch_fft_xy_inv_gauge<R, RG, GR>(const Geom&, const FFTPlan&, C2<R>*, const C2<R>*,      \
-                                                          const short*, C2<RG>*, C2<RG>*, cudaStream_t, const Batch&);
+                                                          const short*, C2<RG>*, C2<RG>*, cudaStream_t, const Batch&, \
+                                                          int);
 LGF_INST_C(double, double, 3)
 LGF_INST_C(double, double, 2)
 LGF_INST_C(float, float, 2)

@@ -157,11 +157,13 @@ template <typename R>
 cudaError_t launch_fft_zt(const Geom& g, const FFTPlan& p, C2<R>* data, const C2<R>* tw, const short* pos,
                           const R* K, int mode, int nfields, cudaStream_t s, const float* mtab = nullptr,
                           const int* use_m = nullptr, const Batch& B = Batch());
-// Inverse (x,y) transform fused with g(x) = reunitarize(1 + Delta'(x)) in FP64;
-// g stored with GROWS rows in precision RG; optional G <- g G (precision RG2 with 3 rows).
+// Inverse (x,y) transform fused with g(x) = reunitarize(1 + Delta'(x)) in FP64
+// (exact_exp != 0: g(x) = reunitarize(exp(Delta'(x)))); g stored with GROWS
+// rows in precision RG; optional G <- g G (precision RG with 3 rows).
 template <typename R, typename RG, int GROWS>
 cudaError_t launch_fft_xy_inv_gauge(const Geom& g, const FFTPlan& p, C2<R>* data, const C2<R>* tw, const short* pos,
-                                    C2<RG>* gfield, C2<RG>* Gfield, cudaStream_t s, const Batch& B = Batch());
+                                    C2<RG>* gfield, C2<RG>* Gfield, cudaStream_t s, const Batch& B = Batch(),
+                                    int exact_exp = 0);
 
 cudaError_t configure_fft_plan(const int L[4], int real_bytes, FFTPlan* p);
 // All plans the autotuner may choose among for a lattice shape.

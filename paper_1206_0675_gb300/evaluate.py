@@ -1,7 +1,10 @@
 """Wall time and iterations to a threshold: plain FP64 FA-SD against the
-mixed FP32 -> FP64 mode with and without the learned multiplier.
+mixed FP32 -> FP64 mode with and without the learned multiplier, the
+exact-exponential and plain-SD variants, and scans over alpha.
 
     python -m paper_1206_0675_gb300.evaluate --lattice 32 --eps 0.7 --seeds 100-107 [--tol 1e-15]
+    python -m paper_1206_0675_gb300.evaluate --lattice 16 --eps 1.0 --seeds 100-101 \
+        --modes fp64,fp64_exp,fp64_sd --alphas 0.04,0.06,0.08,0.1,0.12 --tol 1e-12
 
 Prints one JSON line per configuration and a summary line.
 """
@@ -26,10 +29,13 @@ MODES = {
     "fp64_learned": dict(precision="fp64", learned=True),
     "mixed": dict(precision="mixed", store12=True),
     "mixed_learned": dict(precision="mixed", store12=True, learned=True),
+    "fp64_exp": dict(precision="fp64", exact_exp=True),
+    "mixed_exp": dict(precision="mixed", store12=True, exact_exp=True),
+    "fp64_sd": dict(precision="fp64", plain_sd=True),
 }
 
 
-def run_mode(mode, ext, U, tol, max_iter, weights, switch=None):
+def run_mode(mode, ext, U, tol, max_iter, weights, switch=None, alpha=0.08):
     import torch
     kw = MODES[mode]
     with lgf.Lattice(ext, **kw) as lat:
@@ -38,11 +44,16 @@ def run_mode(mode, ext, U, tol, max_iter, weights, switch=None):
         if switch is not None and kw["precision"] == "mixed":
             lat.set_switch_theta(switch)
         lat.set_links(U)
-        lat.fix(tol, 1, 0.08)   # builds the loop graphs
+        lat.fix(tol, 1, alpha)   # builds the loop graphs
         lat.set_links(U)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        it, F, th, conv = lat.fix(tol, max_iter, 0.08)
+        try:
+            it, F, th, conv = lat.fix(tol, max_iter, alpha)
+        except lgf.LgfError as e:  # a diverging step size: reported, not fatal to a scan
+            torch.cuda.synchronize()
+            return {"seconds": time.perf_counter() - t0, "iters": max_iter, "F": None, "theta": None,
+                    "converged": False, "fallbacks": 0, "error": str(e)}
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         nf = lat.fallbacks() if kw.get("learned") else 0
@@ -88,6 +99,7 @@ def main():
     ap.add_argument("--extents", default=None, help="Lx,Ly,Lz,Lt (overrides --lattice)")
     ap.add_argument("--kernels", action="store_true", help="per-kernel table of every precision/storage")
     ap.add_argument("--switch", type=float, default=None, help="switch level of the mixed modes")
+    ap.add_argument("--alphas", default="0.08", help="comma-separated step sizes alpha (a scan if several)")
     args = ap.parse_args()
     a, b = (int(v) for v in args.seeds.split("-")) if "-" in args.seeds else (int(args.seeds),) * 2
     ext = tuple(int(v) for v in args.extents.split(",")) if args.extents else (args.lattice,) * 4
@@ -104,23 +116,27 @@ def main():
                           "table": kernel_table(ext, U, peak_gbs=peak)}), flush=True)
         return
     weights = np.load(args.weights)
-    modes = args.modes.split(",")
-    tot = {m: [0.0, 0] for m in modes}
+    alphas = [float(v) for v in args.alphas.split(",")]
+    scan = len(alphas) > 1
+    runs = [(m, al, f"{m}@{al:g}" if scan else m) for al in alphas for m in args.modes.split(",")]
+    tot = {key: [0.0, 0, 0] for _, _, key in runs}
     for seed in range(a, b + 1):
         U = fields.random_links(ext, args.eps, seed)
         row = {"lattice": list(ext), "eps": args.eps, "seed": seed}
-        for m in modes:
-            r = run_mode(m, ext, U, args.tol, args.max_iter, weights, args.switch)
-            row[m] = r
-            tot[m][0] += r["seconds"]
-            tot[m][1] += r["iters"]
+        for m, al, key in runs:
+            r = run_mode(m, ext, U, args.tol, args.max_iter, weights, args.switch, al)
+            row[key] = r
+            tot[key][0] += r["seconds"]
+            tot[key][1] += r["iters"]
+            tot[key][2] += int(not r["converged"])
         print(json.dumps(row), flush=True)
-    summary = {m: {"seconds": v[0], "iters": v[1]} for m, v in tot.items()}
-    if "fp64" in tot:
-        for m in modes:
-            summary[m]["speedup_vs_fp64"] = tot["fp64"][0] / tot[m][0]
+    summary = {k: {"seconds": v[0], "iters": v[1], "not_converged": v[2]} for k, v in tot.items()}
+    for m, al, key in runs:
+        base = f"fp64@{al:g}" if scan else "fp64"
+        if base in tot:
+            summary[key]["speedup_vs_fp64"] = tot[base][0] / tot[key][0]
     print(json.dumps({"summary": summary, "lattice": list(ext), "eps": args.eps, "seeds": args.seeds,
-                      "tol": args.tol, "switch": args.switch}), flush=True)
+                      "tol": args.tol, "switch": args.switch, "alphas": alphas}), flush=True)
 
 
 if __name__ == "__main__":

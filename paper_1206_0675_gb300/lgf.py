@@ -29,7 +29,7 @@ LIB_PATH = os.path.join(_HERE, "liblgf.so")
 LGF_OK, LGF_E_ARG, LGF_E_NOMEM, LGF_E_CUDA, LGF_E_STATE, LGF_E_NONFINITE, LGF_E_NOTCONV, LGF_E_TIMEOUT, \
     LGF_E_UNSUPPORTED = range(9)
 LGF_FP64, LGF_FP32, LGF_MIXED = 0, 1, 2
-LGF_STORE18, LGF_STORE12, LGF_TRACK_G, LGF_LEARNED, LGF_PLAIN_SD = 0, 1, 2, 4, 8
+LGF_STORE18, LGF_STORE12, LGF_TRACK_G, LGF_LEARNED, LGF_PLAIN_SD, LGF_EXACT_EXP = 0, 1, 2, 4, 8, 16
 LGF_MLP_NPARAM = 8897
 MLP_NBUCKET = 40
 MLP_NSTAT = 5
@@ -379,14 +379,15 @@ class Lattice:
     """One lattice configuration on the GPU (owns an lgf handle)."""
 
     def __init__(self, extents, precision: str = "fp64", store12: bool = False, track_G: bool = False,
-                 plain_sd: bool = False, learned: bool = False, stream: int | None = None):
+                 plain_sd: bool = False, learned: bool = False, exact_exp: bool = False,
+                 stream: int | None = None):
         self.extents = tuple(int(e) for e in extents)
         lx, ly, lz, lt = self.extents
         self.link_shape = (4, lt, lz, ly, lx, 3, 3)
         self.site_shape = (lt, lz, ly, lx, 3, 3)
         self.nclass = int(np.prod([e // 2 + 1 for e in self.extents]))
         flags = ((LGF_STORE12 if store12 else 0) | (LGF_TRACK_G if track_G else 0) | (LGF_PLAIN_SD if plain_sd else 0)
-                 | (LGF_LEARNED if learned else 0))
+                 | (LGF_LEARNED if learned else 0) | (LGF_EXACT_EXP if exact_exp else 0))
         if stream is None:
             try:
                 import torch
