@@ -249,6 +249,21 @@ lgf_status lgf_mlp_to_bf16(const float* P, uint16_t* out, void* cuda_stream);
  * accepted range [1e-10, 1e-6], so every iteration below 1e-10 is FP64). */
 lgf_status lgf_set_switch_theta(lgf_handle h, double theta);
 
+/* Decomposition of the 4D transform of every following step (Sec. 3.2
+ * compares the three on cuFFT; here each is a set of shared-memory passes):
+ *   LGF_FFT_2D2D (default): (x,y) pass; (z,t) pass with the filter; inverse
+ *     (x,y) pass fused with g -- three passes over the divergence.
+ *   LGF_FFT_1D4: one pass per direction and sign, the t pass carrying the
+ *     filter, then a separate g kernel -- seven passes plus g.
+ *   LGF_FFT_3D1D: an (x,y,z) pass per t plane, a t pass with the filter, the
+ *     inverse (x,y,z) pass, then g -- three passes plus g; only where one
+ *     field's (x,y,z) slab fits in shared memory (up to 16^3 in FP64, 24^3
+ *     in FP32), else LGF_E_UNSUPPORTED.
+ * All three give the same result up to rounding.  With LGF_LEARNED only
+ * LGF_FFT_2D2D is accepted (LGF_E_UNSUPPORTED).  Synchronises. */
+enum { LGF_FFT_2D2D = 0, LGF_FFT_1D4 = 1, LGF_FFT_3D1D = 2 };
+lgf_status lgf_set_fft_decomposition(lgf_handle h, int32_t decomposition);
+
 /* Phase of an LGF_MIXED handle: 32 while in the FP32 phase, 64 after the
  * switch (FP64 and FP32 handles report their fixed precision). */
 lgf_status lgf_get_phase(lgf_handle h, int32_t* bits);

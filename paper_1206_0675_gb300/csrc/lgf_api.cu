@@ -47,8 +47,10 @@ template <typename R> struct Lane {
 // Per-kernel CUDA-event timing of lgf_step (ring of in-flight steps).
 // Categories: 0 pass A, 1 pass B, 2 pass C, 3 update, 4 measure, 5 learned
 // extras (undo of a rejected step, its re-measurement, network inference).
+// With the 1D x 4 or 3D + 1D decompositions, category 0 holds the forward
+// passes, 1 the pass with the filter and 2 the inverse passes and g.
 struct TimingRing {
-  static constexpr int kSlots = 64, kMaxK = 8, kCat = 6;
+  static constexpr int kSlots = 64, kMaxK = 12, kCat = 6;
   cudaEvent_t ev[kSlots][kMaxK + 1] = {};
   int cat[kSlots][kMaxK] = {};
   int nk[kSlots] = {};
@@ -98,6 +100,7 @@ struct lgf_ctx {
   bool log_primed = false;
   LogState* ls = nullptr;
   double* stats = nullptr;        // [MLP_NBUCKET][nclass][4]
+  int fft_decomp = FFT_2D2D;      // decomposition of the 4D transform (lgf_set_fft_decomposition)
 };
 
 namespace {
@@ -130,9 +133,15 @@ bool extent_ok(int L) {
 
 template <typename T> cudaError_t dalloc(T** p, size_t n) { return cudaMalloc((void**)p, n * sizeof(T)); }
 
-template <typename R> void free_lane(Lane<R>& L) {
+template <typename R> void drop_graph(Lane<R>& L) {
   if (L.exec) cudaGraphExecDestroy(L.exec);
   if (L.graph) cudaGraphDestroy(L.graph);
+  L.exec = nullptr;
+  L.graph = nullptr;
+}
+
+template <typename R> void free_lane(Lane<R>& L) {
+  drop_graph(L);
   cudaFree(L.U); cudaFree(L.g); cudaFree(L.D); cudaFree(L.K); cudaFree(L.tw); cudaFree(L.pos); cudaFree(L.G);
   cudaFree(L.mtab); cudaFree(L.p2f); cudaFree(L.Dlog); cudaFree(L.Dprev);
   L = Lane<R>();
@@ -215,7 +224,10 @@ template <typename R> cudaError_t enqueue_measure(lgf_ctx* h, Lane<R>& L, int co
 // pass A, pass B, pass C (+g), update, measure.  Learned: undo of a rejected
 // step, its re-measurement and the network inference come first (each does
 // nothing unless it has work), then the plain sequence with the multiplier.
-enum { K_A = 0, K_B, K_C, K_UPD, K_MEAS, K_REVERT, K_RESTORE, K_MLP };
+// 1D x 4: forward x, y, z; forward t, filter, inverse t; inverse z, y, x; g.
+// 3D + 1D: forward (x,y,z); t with the filter; inverse (x,y,z); g.
+enum { K_A = 0, K_B, K_C, K_UPD, K_MEAS, K_REVERT, K_RESTORE, K_MLP,
+       K_F1X, K_F1Y, K_F1Z, K_T1, K_I1Z, K_I1Y, K_I1X, K_F3, K_I3, K_GD };
 
 template <typename R> int body_kernels(const lgf_ctx* h, int* ks) {
   int n = 0;
@@ -224,17 +236,48 @@ template <typename R> int body_kernels(const lgf_ctx* h, int* ks) {
     ks[n++] = K_RESTORE;
     ks[n++] = K_MLP;
   }
-  ks[n++] = K_A;
-  ks[n++] = K_B;
-  ks[n++] = K_C;
+  if (h->fft_decomp == FFT_1D4) {
+    for (int k : {K_F1X, K_F1Y, K_F1Z, K_T1, K_I1Z, K_I1Y, K_I1X, K_GD}) ks[n++] = k;
+  } else if (h->fft_decomp == FFT_3D1D) {
+    for (int k : {K_F3, K_T1, K_I3, K_GD}) ks[n++] = k;
+  } else {
+    ks[n++] = K_A;
+    ks[n++] = K_B;
+    ks[n++] = K_C;
+  }
   ks[n++] = K_UPD;
   ks[n++] = K_MEAS;
   return n;
 }
 
-inline int kernel_category(int k) { return k <= K_MEAS ? k : 5; }
+inline int kernel_category(int k) {
+  if (k <= K_MEAS) return k;
+  if (k == K_F1X || k == K_F1Y || k == K_F1Z || k == K_F3) return 0;
+  if (k == K_T1) return 1;
+  if (k >= K_I1Z) return 2;
+  return 5;
+}
 
 inline int exact_exp(const lgf_ctx* h) { return (h->flags & LGF_EXACT_EXP) ? 1 : 0; }
+
+// Passes of the 1D x 4 and 3D + 1D decompositions, and g from their output.
+template <typename R> cudaError_t enqueue_alt_fft(lgf_ctx* h, Lane<R>& L, int k, cudaStream_t s) {
+  const Geom& g = h->geom;
+  switch (k) {
+    case K_F1X: return launch_fft_line<R>(g, L.plan, 0, L.D, L.tw, L.pos, L.K, -1, 4, s);
+    case K_F1Y: return launch_fft_line<R>(g, L.plan, 1, L.D, L.tw, L.pos, L.K, -1, 4, s);
+    case K_F1Z: return launch_fft_line<R>(g, L.plan, 2, L.D, L.tw, L.pos, L.K, -1, 4, s);
+    case K_T1: return launch_fft_line<R>(g, L.plan, 3, L.D, L.tw, L.pos, L.K, 0, 4, s);
+    case K_I1Z: return launch_fft_line<R>(g, L.plan, 2, L.D, L.tw, L.pos, L.K, +1, 4, s);
+    case K_I1Y: return launch_fft_line<R>(g, L.plan, 1, L.D, L.tw, L.pos, L.K, +1, 4, s);
+    case K_I1X: return launch_fft_line<R>(g, L.plan, 0, L.D, L.tw, L.pos, L.K, +1, 4, s);
+    case K_F3: return launch_fft_xyz<R>(g, L.plan, L.D, L.tw, L.pos, -1, 4, s);
+    case K_I3: return launch_fft_xyz<R>(g, L.plan, L.D, L.tw, L.pos, +1, 4, s);
+    default:
+      if (L.grows == 3) return launch_gauge_from_delta<R, R, 3>(g, L.D, L.g, L.G, s, Batch(), exact_exp(h));
+      return launch_gauge_from_delta<R, R, 2>(g, L.D, L.g, L.G, s, Batch(), exact_exp(h));
+  }
+}
 
 template <typename R> cudaError_t enqueue_kernel(lgf_ctx* h, Lane<R>& L, int k, unsigned long long cond,
                                                   int use_cond, cudaStream_t s);
@@ -255,7 +298,8 @@ template <> cudaError_t enqueue_kernel<double>(lgf_ctx* h, Lane<double>& L, int 
       return L.rows == 3 ? launch_revert<double, 3, 3>(g, L.U, L.g, L.G, h->st, s)
                          : launch_revert<double, 2, 3>(g, L.U, L.g, L.G, h->st, s);
     case K_RESTORE: return enqueue_measure<double>(h, L, -1, 0, 0, s, 1);
-    default: return launch_mlp_multiplier(h->mlp_w, L.mg, L.p2f, h->st, L.mtab, s);
+    case K_MLP: return launch_mlp_multiplier(h->mlp_w, L.mg, L.p2f, h->st, L.mtab, s);
+    default: return enqueue_alt_fft<double>(h, L, k, s);
   }
 }
 
@@ -276,7 +320,8 @@ template <> cudaError_t enqueue_kernel<float>(lgf_ctx* h, Lane<float>& L, int k,
       return L.grows == 2 ? launch_revert<float, 2, 2>(g, L.U, L.g, L.G, h->st, s)
                           : launch_revert<float, 3, 3>(g, L.U, L.g, L.G, h->st, s);
     case K_RESTORE: return enqueue_measure<float>(h, L, -1, 0, 0, s, 1);
-    default: return launch_mlp_multiplier(h->mlp_w, L.mg, L.p2f, h->st, L.mtab, s);
+    case K_MLP: return launch_mlp_multiplier(h->mlp_w, L.mg, L.p2f, h->st, L.mtab, s);
+    default: return enqueue_alt_fft<float>(h, L, k, s);
   }
 }
 
@@ -979,6 +1024,24 @@ lgf_status lgf_set_switch_theta(lgf_handle h, double theta) {
   if (!h) return LGF_E_ARG;
   if (!(theta >= 1e-10 && theta <= 1e-6)) return fail(h, LGF_E_ARG, "switch level must lie in [1e-10, 1e-6]");
   h->switch_theta = theta;
+  return LGF_OK;
+}
+
+lgf_status lgf_set_fft_decomposition(lgf_handle h, int32_t decomposition) {
+  lgf_status s = check_handle(h);
+  if (s != LGF_OK) return s;
+  if (decomposition != LGF_FFT_2D2D && decomposition != LGF_FFT_1D4 && decomposition != LGF_FFT_3D1D)
+    return fail(h, LGF_E_ARG, "unknown decomposition");
+  if (decomposition != LGF_FFT_2D2D && h->learned)
+    return fail(h, LGF_E_UNSUPPORTED, "the learned multiplier runs with the 2D + 2D decomposition only");
+  if (decomposition == LGF_FFT_3D1D && ((h->d.active && !h->d.plan.fit_xyz) || (h->f.active && !h->f.plan.fit_xyz)))
+    return fail(h, LGF_E_UNSUPPORTED, "the (x, y, z) slab does not fit in shared memory");
+  if (decomposition == h->fft_decomp) return LGF_OK;
+  LGF_CK(h, cudaStreamSynchronize(h->stream));
+  // the loop graphs hold the old body: rebuild them on the next fix
+  drop_graph(h->d);
+  drop_graph(h->f);
+  h->fft_decomp = decomposition;
   return LGF_OK;
 }
 

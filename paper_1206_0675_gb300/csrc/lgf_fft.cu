@@ -311,6 +311,129 @@ __global__ void __launch_bounds__(512) fft_zt_filter_kernel(Geom g, FFTDir dz, F
 }
 
 // ---------------------------------------------------------------------------
+// Alternative decompositions of the 4D transform (Sec. 3.2 compares 1D x 4,
+// 3D + 1D and 2D + 2D on cuFFT): one pass per direction, or one pass over
+// the (x, y, z) slab of each t plus a pass over t.  Both keep every line of a
+// pass in shared memory with the same Cooley-Tukey stages as the plane passes.
+// ---------------------------------------------------------------------------
+
+// One 1D pass along direction mu.  Contiguous form (mu = x): each CTA takes nl
+// consecutive x-lines.  Strided form (mu = y, z, t): each CTA takes xc
+// consecutive x columns at fixed other coordinates, so that the global
+// accesses are runs of xc elements.  Tile: line l at l * (N + 1).
+struct LinePass {
+  int N;            // line length L_mu
+  int nl;           // lines per CTA
+  int contiguous;   // 1 for mu = x
+  int64_t S;        // element stride of mu in a field
+  int64_t SN;       // S * N
+  FastDiv dload;    // by N (contiguous) or by nl (strided)
+  FastDiv dlob;     // by S / nl (strided): column blocks per (coordinate above mu)
+};
+
+// mode -1: forward DFT; +1: inverse DFT (unnormalised); 0: forward DFT,
+// multiplication by K (same layout as the field), inverse DFT.
+template <typename R>
+__global__ void __launch_bounds__(512) fft_line_kernel(LinePass lp, FFTDir d, int64_t V, C2<R>* __restrict__ data,
+                                                       const C2<R>* __restrict__ twg, const short* __restrict__ posg,
+                                                       const R* __restrict__ K, int mode, Lines ln, Batch B) {
+  if (batch_skip(B)) return;
+  data += blockIdx.z * B.s_delta;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2<R>* tw;
+  short* pos;
+  C2<R>* tile = setup_smem<R>(smem_raw, twg, posg, lp.N, 0, &tw, &pos);
+  C2<R>* fld = data + (int64_t)blockIdx.y * V;
+  const int N = lp.N, RS = N + 1, n_el = lp.nl * N;
+  int64_t s0;
+  if (lp.contiguous) {
+    s0 = (int64_t)blockIdx.x * n_el;
+  } else {
+    const uint32_t b = blockIdx.x;
+    const uint32_t hi = lp.dlob.div(b), lob = b - hi * lp.dlob.d;
+    s0 = (int64_t)lob * lp.nl + (int64_t)hi * lp.SN;
+  }
+  // element i of the CTA -> (line l, position n) and its site
+#define LGF_LINE_IDX(i)                                                          \
+  int l, n;                                                                      \
+  if (lp.contiguous) { l = (int)lp.dload.div((uint32_t)(i)); n = (i) - l * N; }  \
+  else { n = (int)lp.dload.div((uint32_t)(i)); l = (i) - n * lp.nl; }            \
+  const int64_t site = lp.contiguous ? s0 + (i) : s0 + l + (int64_t)n * lp.S;
+  __syncthreads();
+  const bool natural_in = mode > 0;
+  for (int i = threadIdx.x; i < n_el; i += blockDim.x) {
+    LGF_LINE_IDX(i)
+    tile[l * RS + (natural_in ? n : pos[n])] = fld[site];
+  }
+  __syncthreads();
+  if (mode < 0) {
+    fft_lines_dit<R, -1>(tile, ln, d, tw);
+  } else if (mode > 0) {
+    fft_lines_dif<R, +1>(tile, ln, d, tw);
+  } else {
+    fft_lines_dit<R, -1>(tile, ln, d, tw);
+    for (int i = threadIdx.x; i < n_el; i += blockDim.x) {
+      LGF_LINE_IDX(i)
+      const R k = __ldg(&K[site]);
+      C2<R>& e = tile[l * RS + n];
+      e = mkc<R>(e.x * k, e.y * k);
+    }
+    __syncthreads();
+    fft_lines_dif<R, +1>(tile, ln, d, tw);
+  }
+  const bool natural_out = mode < 0;
+  for (int i = threadIdx.x; i < n_el; i += blockDim.x) {
+    LGF_LINE_IDX(i)
+    fld[site] = tile[l * RS + (natural_out ? n : pos[n])];
+  }
+#undef LGF_LINE_IDX
+}
+
+// 3D DFT over the (x, y, z) slab of one t and one field (SIGN -1 forward:
+// digit-reversed load, DIT, natural store; +1 inverse: natural load, DIF,
+// digit-reversed read-out).  The slab must fit in shared memory.
+template <typename R, int SIGN>
+__global__ void __launch_bounds__(512) fft_xyz_kernel(Geom g, FFTDir dx, FFTDir dy, FFTDir dz, C2<R>* __restrict__ data,
+                                                      const C2<R>* __restrict__ twg, const short* __restrict__ posg,
+                                                      Lines lx, Lines ly, Lines lz, CopyDiv cd, Batch B) {
+  if (batch_skip(B)) return;
+  data += blockIdx.z * B.s_delta;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int Lx = g.L[0], Ly = g.L[1], Lz = g.L[2];
+  C2<R>* tw;
+  short* pos;
+  C2<R>* tile = setup_smem<R>(smem_raw, twg, posg, Lx, Ly + Lz, &tw, &pos);
+  const int RS = Lx + 1, PS = Ly * RS;
+  const int n_el = Lx * Ly * Lz;
+  C2<R>* fld = data + (int64_t)blockIdx.y * g.V + (int64_t)blockIdx.x * n_el;
+  __syncthreads();
+#define LGF_XYZ_IDX(i)                                                     \
+  const int z = (int)cd.a.div((uint32_t)(i)), r = (i) - z * Lx * Ly;       \
+  const int y = (int)cd.b.div((uint32_t)r), x = r - y * Lx;
+  for (int i = threadIdx.x; i < n_el; i += blockDim.x) {
+    LGF_XYZ_IDX(i)
+    const int o = SIGN < 0 ? pos[Lx + Ly + z] * PS + pos[Lx + y] * RS + pos[x] : z * PS + y * RS + x;
+    tile[o] = fld[i];
+  }
+  __syncthreads();
+  if (SIGN < 0) {
+    fft_lines_dit<R, -1>(tile, lx, dx, tw);
+    fft_lines_dit<R, -1>(tile, ly, dy, tw + Lx);
+    fft_lines_dit<R, -1>(tile, lz, dz, tw + Lx + Ly);
+  } else {
+    fft_lines_dif<R, +1>(tile, lz, dz, tw + Lx + Ly);
+    fft_lines_dif<R, +1>(tile, ly, dy, tw + Lx);
+    fft_lines_dif<R, +1>(tile, lx, dx, tw);
+  }
+  for (int i = threadIdx.x; i < n_el; i += blockDim.x) {
+    LGF_XYZ_IDX(i)
+    const int o = SIGN < 0 ? z * PS + y * RS + x : pos[Lx + Ly + z] * PS + pos[Lx + y] * RS + pos[x];
+    fld[i] = tile[o];
+  }
+#undef LGF_XYZ_IDX
+}
+
+// ---------------------------------------------------------------------------
 // g(x) = reunitarize(1 + Delta'(x)) in FP64 (Sec. 2 first-order expansion,
 // Gram-Schmidt on rows 1-2, row 3 = (a x b)^* as in Sec. 3.2)
 // ---------------------------------------------------------------------------
@@ -580,6 +703,33 @@ static int threads_for(int points) {
   return std::max(64, std::min(512, t));
 }
 
+// Tiles of the 1D x 4 and 3D + 1D decompositions: up to 32 x-lines per CTA
+// in the x pass, up to 16 x columns in the y, z, t passes (runs of 16
+// elements), and the whole (x, y, z) slab of one field in the 3D pass when
+// it fits.
+static void configure_alt_passes(const int L[4], int real_bytes, FFTPlan* p) {
+  const size_t cb = 2 * (size_t)real_bytes, maxsm = 220 * 1024;
+  const int64_t V = (int64_t)L[0] * L[1] * L[2] * L[3];
+  const int64_t xlines = V / L[0];
+  int nl = 32;
+  while (nl > 1 && (xlines % nl || smem_header_bytes<double>(L[0], 0) + (size_t)nl * (L[0] + 1) * cb > 64 * 1024))
+    --nl;
+  p->nl_x = nl;
+  int xc = 16;
+  while (xc > 1 && L[0] % xc) --xc;
+  p->xc_line = xc;
+  for (int mu = 0; mu < 4; ++mu) {
+    const int lines = mu == 0 ? p->nl_x : p->xc_line;
+    const size_t hdr = (size_t)((L[mu] + 1) & ~1) * cb + (size_t)((L[mu] + 7) & ~7) * 2;
+    p->smem_line[mu] = hdr + (size_t)lines * (L[mu] + 1) * cb;
+    p->threads_line[mu] = threads_for(lines * L[mu]);
+  }
+  const size_t hxyz = (size_t)((L[0] + L[1] + L[2] + 1) & ~1) * cb + (size_t)((L[0] + L[1] + L[2] + 7) & ~7) * 2;
+  p->smem_xyz = hxyz + (size_t)L[2] * L[1] * (L[0] + 1) * cb;
+  p->fit_xyz = p->smem_xyz <= maxsm ? 1 : 0;
+  p->threads_xyz = threads_for(L[0] * L[1] * L[2]);
+}
+
 cudaError_t configure_fft_plan(const int L[4], int real_bytes, FFTPlan* p) {
   const size_t cb = 2 * (size_t)real_bytes;  // bytes per complex element
   for (int mu = 0; mu < 4; ++mu) {
@@ -615,6 +765,7 @@ cudaError_t configure_fft_plan(const int L[4], int real_bytes, FFTPlan* p) {
   p->threads_xy = threads_for(p->fpb_xy * Lx * Ly);
   p->threads_zt = threads_for(Lz * Lt * xc);
   p->threads_c = threads_for(4 * Lx * Ly);
+  configure_alt_passes(L, real_bytes, p);
   return cudaSuccess;
 }
 
@@ -698,6 +849,63 @@ cudaError_t launch_fft_zt(const Geom& g, const FFTPlan& p, C2<R>* data, const C2
   return cudaGetLastError();
 }
 
+template <typename R>
+cudaError_t launch_fft_line(const Geom& g, const FFTPlan& p, int mu, C2<R>* data, const C2<R>* tw, const short* pos,
+                            const R* K, int mode, int nfields, cudaStream_t s, const Batch& B) {
+  const int N = g.L[mu];
+  LinePass lp;
+  lp.N = N;
+  lp.contiguous = mu == 0;
+  lp.nl = mu == 0 ? p.nl_x : p.xc_line;
+  lp.S = g.stride[mu];
+  lp.SN = lp.S * N;
+  lp.dload = FastDiv::make((uint32_t)(lp.contiguous ? N : lp.nl));
+  lp.dlob = FastDiv::make((uint32_t)(lp.contiguous ? 1 : lp.S / lp.nl));
+  const int64_t blocks = g.V / ((int64_t)N * lp.nl);
+  const size_t smem = p.smem_line[mu];
+  cudaError_t e = allow_smem(fft_line_kernel<R>, smem);
+  if (e != cudaSuccess) return e;
+  const int off = mu == 0 ? 0 : mu == 1 ? g.L[0] : mu == 2 ? g.L[0] + g.L[1] : g.L[0] + g.L[1] + g.L[2];
+  const Lines ln = make_lines(lp.nl, lp.nl, N + 1, 0, 1);
+  fft_line_kernel<R><<<dim3((unsigned)blocks, (unsigned)nfields, (unsigned)B.n), p.threads_line[mu], smem, s>>>(
+      lp, p.d[mu], g.V, data, tw + off, pos + off, K, mode, ln, B);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_fft_xyz(const Geom& g, const FFTPlan& p, C2<R>* data, const C2<R>* tw, const short* pos, int sign,
+                           int nfields, cudaStream_t s, const Batch& B) {
+  if (!p.fit_xyz) return cudaErrorInvalidConfiguration;
+  const int Lx = g.L[0], Ly = g.L[1], Lz = g.L[2], RS = Lx + 1, PS = Ly * RS;
+  const Lines lx = make_lines(Ly * Lz, Ly * Lz, RS, 0, 1);
+  const Lines ly = make_lines(Lx * Lz, Lx, 1, PS, RS);
+  const Lines lz = make_lines(Lx * Ly, Lx, 1, RS, PS);
+  const CopyDiv cd{FastDiv::make((uint32_t)(Lx * Ly)), FastDiv::make((uint32_t)Lx)};
+  const dim3 grid((unsigned)g.L[3], (unsigned)nfields, (unsigned)B.n);
+  cudaError_t e;
+  if (sign < 0) {
+    if ((e = allow_smem(fft_xyz_kernel<R, -1>, p.smem_xyz)) != cudaSuccess) return e;
+    fft_xyz_kernel<R, -1><<<grid, p.threads_xyz, p.smem_xyz, s>>>(g, p.d[0], p.d[1], p.d[2], data, tw, pos, lx, ly, lz,
+                                                                  cd, B);
+  } else {
+    if ((e = allow_smem(fft_xyz_kernel<R, +1>, p.smem_xyz)) != cudaSuccess) return e;
+    fft_xyz_kernel<R, +1><<<grid, p.threads_xyz, p.smem_xyz, s>>>(g, p.d[0], p.d[1], p.d[2], data, tw, pos, lx, ly, lz,
+                                                                  cd, B);
+  }
+  return cudaGetLastError();
+}
+
+template <typename R, typename RG, int GROWS>
+cudaError_t launch_gauge_from_delta(const Geom& g, const C2<R>* data, C2<RG>* gfield, C2<RG>* Gfield, cudaStream_t s,
+                                    const Batch& B, int exact_exp) {
+  const dim3 grid((unsigned)((g.V + 127) / 128), 1, (unsigned)B.n);
+  if (exact_exp)
+    gauge_from_delta_kernel<R, RG, GROWS, true><<<grid, 128, 0, s>>>(g, data, gfield, Gfield, B);
+  else
+    gauge_from_delta_kernel<R, RG, GROWS, false><<<grid, 128, 0, s>>>(g, data, gfield, Gfield, B);
+  return cudaGetLastError();
+}
+
 template <typename R, typename RG, int GROWS, bool EXPG>
 static cudaError_t launch_pass_c(const Geom& g, const FFTPlan& p, C2<R>* data, const C2<R>* tw, const short* pos,
                                  C2<RG>* gfield, C2<RG>* Gfield, cudaStream_t s, const Batch& B) {
@@ -744,5 +952,19 @@ LGF_INST_C(double, double, 3)
 LGF_INST_C(double, double, 2)
 LGF_INST_C(float, float, 2)
 LGF_INST_C(float, float, 3)
+#define LGF_INST_G(R, RG, GR)                                                                                   \
+  template cudaError_t launch_gauge_from_delta<R, RG, GR>(const Geom&, const C2<R>*, C2<RG>*, C2<RG>*,         \
+                                                          cudaStream_t, const Batch&, int);
+LGF_INST_G(double, double, 3)
+LGF_INST_G(double, double, 2)
+LGF_INST_G(float, float, 2)
+LGF_INST_G(float, float, 3)
+#define LGF_INST_ALT(R)                                                                                         \
+  template cudaError_t launch_fft_line<R>(const Geom&, const FFTPlan&, int, C2<R>*, const C2<R>*, const short*, \
+                                          const R*, int, int, cudaStream_t, const Batch&);                      \
+  template cudaError_t launch_fft_xyz<R>(const Geom&, const FFTPlan&, C2<R>*, const C2<R>*, const short*, int,  \
+                                         int, cudaStream_t, const Batch&);
+LGF_INST_ALT(double)
+LGF_INST_ALT(float)
 
 }  // namespace lgf

@@ -141,7 +141,18 @@ struct FFTPlan {
   size_t smem_zt;
   size_t smem_c;   // pass C (needs all 4 fields when fused with g)
   int fuse_g;      // pass C computes g directly (4 fields fit in shared memory)
+  // alternative decompositions (1D x 4 and 3D + 1D)
+  int nl_x;        // x-lines per CTA of the 1D x pass
+  int xc_line;     // x columns per CTA of the 1D y, z, t passes
+  int threads_line[4];
+  size_t smem_line[4];
+  int fit_xyz;     // the (x, y, z) slab of one field fits in shared memory
+  int threads_xyz;
+  size_t smem_xyz;
 };
+
+// Decomposition of the 4D transform of one step.
+enum FFTDecomp { FFT_2D2D = 0, FFT_1D4 = 1, FFT_3D1D = 2 };
 
 // Twiddle tables W_N^m = exp(-2 pi i m / N), m < N, for the four directions,
 // concatenated at offsets 0, Lx, Lx+Ly, Lx+Ly+Lz (FP64 and FP32 copies).
@@ -164,6 +175,21 @@ template <typename R, typename RG, int GROWS>
 cudaError_t launch_fft_xy_inv_gauge(const Geom& g, const FFTPlan& p, C2<R>* data, const C2<R>* tw, const short* pos,
                                     C2<RG>* gfield, C2<RG>* Gfield, cudaStream_t s, const Batch& B = Batch(),
                                     int exact_exp = 0);
+
+// 1D pass along mu (0..3) over nfields fields: mode -1 forward, +1 inverse,
+// 0 forward, multiply by K, inverse.
+template <typename R>
+cudaError_t launch_fft_line(const Geom& g, const FFTPlan& p, int mu, C2<R>* data, const C2<R>* tw, const short* pos,
+                            const R* K, int mode, int nfields, cudaStream_t s, const Batch& B = Batch());
+// 3D DFT over every (x, y, z) slab (requires p.fit_xyz); sign -1 / +1.
+template <typename R>
+cudaError_t launch_fft_xyz(const Geom& g, const FFTPlan& p, C2<R>* data, const C2<R>* tw, const short* pos, int sign,
+                           int nfields, cudaStream_t s, const Batch& B = Batch());
+// g(x) from the filtered field in natural order (after an inverse transform
+// that is not fused with g); same storage conventions as launch_fft_xy_inv_gauge.
+template <typename R, typename RG, int GROWS>
+cudaError_t launch_gauge_from_delta(const Geom& g, const C2<R>* data, C2<RG>* gfield, C2<RG>* Gfield, cudaStream_t s,
+                                    const Batch& B = Batch(), int exact_exp = 0);
 
 cudaError_t configure_fft_plan(const int L[4], int real_bytes, FFTPlan* p);
 // All plans the autotuner may choose among for a lattice shape.

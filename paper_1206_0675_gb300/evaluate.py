@@ -60,30 +60,49 @@ def run_mode(mode, ext, U, tol, max_iter, weights, switch=None, alpha=0.08):
     return {"seconds": dt, "iters": it, "F": F, "theta": th, "converged": conv, "fallbacks": nf}
 
 
-def kernel_table(ext, U, steps=20, warmup=5, peak_gbs=None):
-    """Per-kernel CUDA-event times and compulsory-traffic GB/s of every precision/storage."""
+def time_steps(lat, steps, warmup):
+    """Wall seconds per lgf_step and the mean per-kernel CUDA-event times."""
     import torch
+    for _ in range(warmup):
+        lat.step(0.08)
+    lat.set_timing(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        lat.step(0.08)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / steps
+    ms, _ = lat.get_timing()
+    return dt, ms
+
+
+def kernel_table(ext, U, steps=20, warmup=5, peak_gbs=None, decomps=("2d2d",)):
+    """Per-kernel CUDA-event times and compulsory-traffic GB/s of every precision/storage.
+
+    With several decompositions of the 4D transform, every storage is timed
+    with each of them; pass A / B / C then read "forward passes", "the pass
+    with the filter" and "inverse passes + g" (the GB/s of the 2D + 2D passes
+    are left out for the others, whose traffic differs)."""
     V = int(np.prod(ext))
     out = {}
     for name, (prec, s12, rb, rows, grows) in STORAGES.items():
-        with lgf.Lattice(ext, prec, store12=s12) as lat:
-            lat.set_links(U)
-            for _ in range(warmup):
-                lat.step(0.08)
-            lat.set_timing(True)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            for _ in range(steps):
-                lat.step(0.08)
-            torch.cuda.synchronize()
-            dt = (time.perf_counter() - t0) / steps
-            ms, _ = lat.get_timing()
         byt = accounting.bytes_per_site(rb, rows, grows, k_bytes=rb)
-        row = {"iters_per_s": 1.0 / dt, "ms_per_step": dt * 1e3, "kernels": {}}
-        for k, t in zip(accounting.KERNELS, ms):
-            gbs = byt[k] * V / (t * 1e-3) / 1e9 if t > 0 else None
-            row["kernels"][k] = {"ms": t, "gbs": gbs, "hbm_frac": gbs / peak_gbs if (gbs and peak_gbs) else None}
-        out[name] = row
+        for dec in decomps:
+            key = name if dec == "2d2d" else f"{name}/{dec}"
+            with lgf.Lattice(ext, prec, store12=s12) as lat:
+                try:
+                    lat.set_fft_decomposition(dec)
+                except lgf.LgfError as e:
+                    out[key] = {"unsupported": str(e)}
+                    continue
+                lat.set_links(U)
+                dt, ms = time_steps(lat, steps, warmup)
+            row = {"iters_per_s": 1.0 / dt, "ms_per_step": dt * 1e3, "kernels": {}}
+            for k, t in zip(accounting.KERNELS, ms):
+                own = dec == "2d2d" or k in ("update", "measure")
+                gbs = byt[k] * V / (t * 1e-3) / 1e9 if (t > 0 and own) else None
+                row["kernels"][k] = {"ms": t, "gbs": gbs, "hbm_frac": gbs / peak_gbs if (gbs and peak_gbs) else None}
+            out[key] = row
     return out
 
 
@@ -98,6 +117,8 @@ def main():
     ap.add_argument("--weights", default=DEFAULT_WEIGHTS)
     ap.add_argument("--extents", default=None, help="Lx,Ly,Lz,Lt (overrides --lattice)")
     ap.add_argument("--kernels", action="store_true", help="per-kernel table of every precision/storage")
+    ap.add_argument("--decomps", default="2d2d",
+                    help="decompositions of the 4D transform for --kernels (2d2d,1d4,3d1d)")
     ap.add_argument("--switch", type=float, default=None, help="switch level of the mixed modes")
     ap.add_argument("--alphas", default="0.08", help="comma-separated step sizes alpha (a scan if several)")
     args = ap.parse_args()
@@ -113,7 +134,8 @@ def main():
             pass
         U = fields.random_links(ext, args.eps, a)
         print(json.dumps({"extents": ext, "eps": args.eps, "seed": a, "peak_gbs": peak,
-                          "table": kernel_table(ext, U, peak_gbs=peak)}), flush=True)
+                          "table": kernel_table(ext, U, peak_gbs=peak, decomps=args.decomps.split(","))}),
+              flush=True)
         return
     weights = np.load(args.weights)
     alphas = [float(v) for v in args.alphas.split(",")]

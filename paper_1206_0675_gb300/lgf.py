@@ -30,6 +30,7 @@ LGF_OK, LGF_E_ARG, LGF_E_NOMEM, LGF_E_CUDA, LGF_E_STATE, LGF_E_NONFINITE, LGF_E_
     LGF_E_UNSUPPORTED = range(9)
 LGF_FP64, LGF_FP32, LGF_MIXED = 0, 1, 2
 LGF_STORE18, LGF_STORE12, LGF_TRACK_G, LGF_LEARNED, LGF_PLAIN_SD, LGF_EXACT_EXP = 0, 1, 2, 4, 8, 16
+LGF_FFT_2D2D, LGF_FFT_1D4, LGF_FFT_3D1D = 0, 1, 2
 LGF_MLP_NPARAM = 8897
 MLP_NBUCKET = 40
 MLP_NSTAT = 5
@@ -57,6 +58,7 @@ SIGNATURES = [
     ("lgf_get_phase", ctypes.c_int, [ctypes.c_void_p, _c_int_p]),
     ("lgf_set_timing", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     ("lgf_set_switch_theta", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
+    ("lgf_set_fft_decomposition", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     ("lgf_get_timing", ctypes.c_int, [ctypes.c_void_p, _c_dbl_p, ctypes.c_int32, _c_int_p]),
     ("lgf_measure_static", ctypes.c_int, [ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_void_p]),
@@ -488,6 +490,12 @@ class Lattice:
         """Theta below which a mixed-precision fix switches to FP64 (1e-10 ... 1e-6)."""
         _check(self.handle, load_library().lgf_set_switch_theta(ctypes.c_void_p(self.handle), float(theta)),
                "lgf_set_switch_theta")
+
+    def set_fft_decomposition(self, decomposition: str) -> None:
+        """Decomposition of the 4D transform of every following step: "2d2d" (default), "1d4" or "3d1d"."""
+        code = {"2d2d": LGF_FFT_2D2D, "1d4": LGF_FFT_1D4, "3d1d": LGF_FFT_3D1D}[decomposition]
+        _check(self.handle, load_library().lgf_set_fft_decomposition(ctypes.c_void_p(self.handle), code),
+               "lgf_set_fft_decomposition")
 
     def set_timing(self, enable: bool = True) -> None:
         lgf_set_timing(self.handle, enable)
