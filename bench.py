@@ -49,6 +49,8 @@ FALLBACK_HBM_GBS = 6800.0
 # FP64 pipe of a GB300: 152 SMs x 2 FP64 instructions per clock x 2070 MHz;
 # counted as FMA-equivalents (2 flops per FP64 instruction).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+# kernels of one step: the transform passes, g where it is not fused, update, measure
+KERNELS_PER_STEP = {"2d2d": 5, "1d4": 10, "3d1d": 6}
 
 
 # DRAM bytes (read + write) per launch from the committed ncu capture of the
@@ -232,6 +234,10 @@ def run_lgf(args, rank, world, local_rank):
     # ---- plain FP64, 18-real: the headline --------------------------------
     lat = lgf.Lattice(EXT, "fp64")
     lat.set_links(U)
+    tune = lat.autotune()["fp64"]
+    chosen = tune["candidates"][tune["chosen"]]
+    decomp = chosen["decomposition"]
+    default_ms = tune["candidates"][0]["ms"]   # the built-in 2D + 2D plan is the first candidate
     for _ in range(args.warmup):
         lat.step(ALPHA)
     torch.cuda.synchronize()
@@ -252,8 +258,8 @@ def run_lgf(args, rank, world, local_rank):
     ms_step = ms / args.steps
     value = world * args.steps / (ms / 1e3)
 
-    ops = accounting.fp64_ops_per_site(EXT, rows=3)
-    byt = accounting.bytes_per_site(8, 3, 3, k_bytes=8)
+    ops = accounting.fp64_ops_per_site(EXT, rows=3, decomposition=decomp)
+    byt = accounting.bytes_per_site(8, 3, 3, k_bytes=8, decomposition=decomp)
     per_kernel = {}
     for name, t_ms in zip(accounting.KERNELS, kms):
         per_kernel[name] = {
@@ -294,15 +300,18 @@ def run_lgf(args, rank, world, local_rank):
     # ---- FP32 12-real rate --------------------------------------------------
     lat32 = lgf.Lattice(EXT, "fp32", store12=True)
     lat32.set_links(U)
+    tune32 = lat32.autotune()["fp32"]
+    decomp32 = tune32["candidates"][tune32["chosen"]]["decomposition"]
     for _ in range(args.warmup):
         lat32.step(ALPHA)
     lat32.set_timing(True)
     ms32 = time_steps(torch, lat32, args.steps)
     kms32, _ = lat32.get_timing()
     lat32.close()
-    b32 = accounting.bytes_per_site(4, 2, 2, k_bytes=4)
+    b32 = accounting.bytes_per_site(4, 2, 2, k_bytes=4, decomposition=decomp32)
     ops32 = accounting.fp32_path_fp64_ops_per_site()
     fp32 = {"iters_per_s": args.steps / (ms32 / 1e3), "ms_per_step": ms32 / args.steps,
+            "fft_decomposition": decomp32,
             "per_kernel": {k: {"ms": t, "gbs": b32[k] * V / (t * 1e-3) / 1e9 if t > 0 else None,
                                "fp64_tflops": 2 * ops32[k] * V / (t * 1e-3) / 1e12 if t > 0 else None}
                            for k, t in zip(accounting.KERNELS, kms32)},
@@ -326,6 +335,7 @@ def run_lgf(args, rank, world, local_rank):
             if sw is not None:
                 L2.set_switch_theta(sw)
             L2.set_links(U)
+            L2.autotune()
             L2.fix(TOL, 1, ALPHA)           # builds the loop graph
             L2.set_links(U)
             torch.cuda.synchronize()
@@ -382,7 +392,13 @@ def run_lgf(args, rank, world, local_rank):
             "site_updates_per_s": value * V,
             "per_kernel": per_kernel, "roofline": roofline, "step_hbm": step_hbm, "fp32_12": fp32,
             "time_to_tol": ttt, "batch64": batch, "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
-            "gpu_launches": 5 * args.steps,
+            "gpu_launches": KERNELS_PER_STEP[decomp] * args.steps,
+            "autotune": {"fft_decomposition": decomp, "fields_per_cta_xy": chosen["fields_per_cta_xy"],
+                         "x_columns_zt": chosen["x_columns_zt"], "threads": chosen["threads"],
+                         "transform_ms": chosen["ms"], "default_plan_transform_ms": default_ms,
+                         "candidates": len(tune["candidates"]),
+                         "note": "lgf_autotune before the warm-up: every tile plan of the 2D+2D passes and the "
+                                 "1D x 4 / 3D + 1D decompositions timed on the device, fastest kept"},
             "paper_context": {"c2070_dp_ms_per_iter_12real_tex": 61.16, "c2070_dp_ms_per_iter_18real_tex": 100.65,
                               "note": "derived from the paper's Table 2 (real beta=5.8-6.2 configurations)"},
         }

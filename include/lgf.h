@@ -264,6 +264,19 @@ lgf_status lgf_set_switch_theta(lgf_handle h, double theta);
 enum { LGF_FFT_2D2D = 0, LGF_FFT_1D4 = 1, LGF_FFT_3D1D = 2 };
 lgf_status lgf_set_fft_decomposition(lgf_handle h, int32_t decomposition);
 
+/* Autotuner of a handle: times the transform and g of one step (CUDA events,
+ * best of 3 after a warm-up) under every tile plan of the 2D + 2D passes
+ * (fields per CTA of the (x,y) passes, x columns of the (z,t) pass, CTA
+ * sizes) and under LGF_FFT_1D4 and LGF_FFT_3D1D where they apply (not with
+ * LGF_LEARNED), for each precision the handle runs in, and keeps the fastest
+ * for the following steps.  report (may be NULL): receives a JSON object
+ * {"fp64": {"chosen": i, "candidates": [{"decomposition", "fields_per_cta_xy",
+ * "x_columns_zt", "threads", "ms"}, ...]}, "fp32": ...}; LGF_E_ARG if len is
+ * too small (the choice is kept).  Overwrites the divergence workspace and
+ * g (lgf_get_gauge then fails until the next step) and re-measures the
+ * current links.  Synchronises. */
+lgf_status lgf_autotune(lgf_handle h, char* report, size_t len);
+
 /* Phase of an LGF_MIXED handle: 32 while in the FP32 phase, 64 after the
  * switch (FP64 and FP32 handles report their fixed precision). */
 lgf_status lgf_get_phase(lgf_handle h, int32_t* bits);

@@ -57,11 +57,19 @@ def fft1d_ops_per_point(N: int) -> float:
     return ops / N
 
 
-def fp64_ops_per_site(extents, rows: int = 3, track_G: bool = False) -> dict[str, float]:
-    """FP64-pipe operations per site of every kernel of the FP64 body."""
+def fp64_ops_per_site(extents, rows: int = 3, track_G: bool = False,
+                      decomposition: str = "2d2d") -> dict[str, float]:
+    """FP64-pipe operations per site of every kernel of the FP64 body.
+
+    With the 1D x 4 or 3D + 1D decompositions "pass_A" is the forward x, y, z
+    transforms, "pass_B" the t pass with the filter and "pass_C" the inverse
+    x, y, z transforms and g."""
     lx, ly, lz, lt = extents
     fxy = fft1d_ops_per_point(lx) + fft1d_ops_per_point(ly)
     fzt = fft1d_ops_per_point(lz) + fft1d_ops_per_point(lt)
+    if decomposition != "2d2d":
+        fxy = fxy + fft1d_ops_per_point(lz)
+        fzt = fft1d_ops_per_point(lt)
     recon = 24 if rows == 2 else 0          # third row of a 12-real matrix
     link_update = 72 + 72 + 24              # rows 1-2 of g U, rows 1-2 of (g U) h^dag, row 3
     update = 4 * (link_update + 2 * recon)  # U and g(x+mu) rebuilt when stored as 12 reals
@@ -83,17 +91,22 @@ def fp32_path_fp64_ops_per_site() -> dict[str, float]:
 
 
 def bytes_per_site(real_bytes: int, rows: int, g_rows: int, track_G: bool = False,
-                   k_bytes: int | None = None) -> dict[str, float]:
-    """Compulsory DRAM bytes per site of every kernel (links and fields read/written once)."""
+                   k_bytes: int | None = None, decomposition: str = "2d2d") -> dict[str, float]:
+    """Compulsory DRAM bytes per site of every kernel (links and fields read/written once).
+
+    1D x 4 moves the divergence 3 times in each of the forward and inverse
+    groups; 3D + 1D once (the categories are those of ``fp64_ops_per_site``)."""
     link = 4 * rows * 3 * 2 * real_bytes      # four links
     gsz = g_rows * 3 * 2 * real_bytes
     delta = 4 * 2 * real_bytes                # four complex fields
     kb = real_bytes if k_bytes is None else k_bytes
     G = 2 * 9 * 2 * real_bytes if track_G else 0
+    sweeps = 3 if decomposition == "1d4" else 1
+    g_read = delta if decomposition != "2d2d" else 0   # the separate g kernel reads the field again
     return {
-        "pass_A": 2 * delta,
+        "pass_A": sweeps * 2 * delta,
         "pass_B": 2 * delta + kb,
-        "pass_C": delta + gsz + G,
+        "pass_C": (sweeps * 2 * delta + g_read if decomposition != "2d2d" else delta) + gsz + G,
         "update": 2 * link + gsz,
         "measure": link + delta,
     }

@@ -33,6 +33,7 @@ template <typename R> struct Lane {
   int rows = 3, grows = 3;
   FFTPlan plan{};
   double alpha = NAN;      // alpha the filter table holds
+  int decomp = FFT_2D2D;   // decomposition of the 4D transform (lgf_set_fft_decomposition, lgf_autotune)
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
   bool active = false;
@@ -100,7 +101,6 @@ struct lgf_ctx {
   bool log_primed = false;
   LogState* ls = nullptr;
   double* stats = nullptr;        // [MLP_NBUCKET][nclass][4]
-  int fft_decomp = FFT_2D2D;      // decomposition of the 4D transform (lgf_set_fft_decomposition)
 };
 
 namespace {
@@ -138,6 +138,13 @@ template <typename R> void drop_graph(Lane<R>& L) {
   if (L.graph) cudaGraphDestroy(L.graph);
   L.exec = nullptr;
   L.graph = nullptr;
+}
+
+// A new decomposition or plan invalidates the captured loop body.
+template <typename R> void set_decomp(Lane<R>& L, int decomposition) {
+  if (L.decomp == decomposition) return;
+  drop_graph(L);
+  L.decomp = decomposition;
 }
 
 template <typename R> void free_lane(Lane<R>& L) {
@@ -229,16 +236,16 @@ template <typename R> cudaError_t enqueue_measure(lgf_ctx* h, Lane<R>& L, int co
 enum { K_A = 0, K_B, K_C, K_UPD, K_MEAS, K_REVERT, K_RESTORE, K_MLP,
        K_F1X, K_F1Y, K_F1Z, K_T1, K_I1Z, K_I1Y, K_I1X, K_F3, K_I3, K_GD };
 
-template <typename R> int body_kernels(const lgf_ctx* h, int* ks) {
+template <typename R> int body_kernels(const lgf_ctx* h, const Lane<R>& L, int* ks) {
   int n = 0;
   if (h->learned) {
     ks[n++] = K_REVERT;
     ks[n++] = K_RESTORE;
     ks[n++] = K_MLP;
   }
-  if (h->fft_decomp == FFT_1D4) {
+  if (L.decomp == FFT_1D4) {
     for (int k : {K_F1X, K_F1Y, K_F1Z, K_T1, K_I1Z, K_I1Y, K_I1X, K_GD}) ks[n++] = k;
-  } else if (h->fft_decomp == FFT_3D1D) {
+  } else if (L.decomp == FFT_3D1D) {
     for (int k : {K_F3, K_T1, K_I3, K_GD}) ks[n++] = k;
   } else {
     ks[n++] = K_A;
@@ -357,7 +364,7 @@ template <typename R> cudaError_t enqueue_body(lgf_ctx* h, Lane<R>& L, unsigned 
     if ((e = cudaEventRecord(T.ev[slot][0], s)) != cudaSuccess) return e;
   }
   int ks[TimingRing::kMaxK];
-  const int nk = body_kernels<R>(h, ks);
+  const int nk = body_kernels<R>(h, L, ks);
   for (int i = 0; i < nk; ++i) {
     if ((e = enqueue_kernel<R>(h, L, ks[i], cond, use_cond, s)) != cudaSuccess) return e;
     if (timed) {
@@ -1027,6 +1034,114 @@ lgf_status lgf_set_switch_theta(lgf_handle h, double theta) {
   return LGF_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+const char* decomp_name(int d) { return d == FFT_1D4 ? "1d4" : d == FFT_3D1D ? "3d1d" : "2d2d"; }
+
+// Device time (ms, best of 3 after a warm-up) of the transform and g of one
+// step under the lane's current plan and decomposition.
+template <typename R> cudaError_t time_transform(lgf_ctx* h, Lane<R>& L, float* ms_out) {
+  int ks[TimingRing::kMaxK];
+  int nk = 0;
+  if (L.decomp == FFT_1D4) {
+    for (int k : {K_F1X, K_F1Y, K_F1Z, K_T1, K_I1Z, K_I1Y, K_I1X, K_GD}) ks[nk++] = k;
+  } else if (L.decomp == FFT_3D1D) {
+    for (int k : {K_F3, K_T1, K_I3, K_GD}) ks[nk++] = k;
+  } else {
+    for (int k : {K_A, K_B, K_C}) ks[nk++] = k;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  float best = 1e30f;
+  for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+    e = cudaEventRecord(e0, h->stream);
+    for (int i = 0; i < nk && e == cudaSuccess; ++i) e = enqueue_kernel<R>(h, L, ks[i], 0, 0, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0) best = std::min(best, ms);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  *ms_out = best;
+  return e;
+}
+
+// Times every tile plan of the 2D + 2D passes and the other decompositions
+// (not with LGF_LEARNED), keeps the fastest and appends a JSON report.
+template <typename R> lgf_status tune_lane(lgf_ctx* h, Lane<R>& L, std::string& rep) {
+  lgf_status s = ensure_filter<R>(h, L, std::isnan(L.alpha) ? 0.08 : L.alpha);
+  if (s != LGF_OK) return s;
+  std::vector<FFTPlan> cand;
+  fft_plan_candidates(h->geom.L, (int)sizeof(R), cand);
+  struct Trial { int decomp; FFTPlan plan; float ms; };
+  std::vector<Trial> trials;
+  for (const FFTPlan& p : cand) trials.push_back({FFT_2D2D, p, 0.f});
+  if (!h->learned) {
+    trials.push_back({FFT_1D4, L.plan, 0.f});
+    if (L.plan.fit_xyz) trials.push_back({FFT_3D1D, L.plan, 0.f});
+  }
+  int best = -1;
+  for (size_t i = 0; i < trials.size(); ++i) {
+    L.plan = trials[i].plan;
+    L.decomp = trials[i].decomp;
+    LGF_CK(h, time_transform<R>(h, L, &trials[i].ms));
+    if (best < 0 || trials[i].ms < trials[best].ms) best = (int)i;
+  }
+  drop_graph(L);
+  L.plan = trials[best].plan;
+  L.decomp = trials[best].decomp;
+  char item[256];
+  rep += "{\"chosen\":" + std::to_string(best) + ",\"candidates\":[";
+  for (size_t i = 0; i < trials.size(); ++i) {
+    const Trial& t = trials[i];
+    std::snprintf(item, sizeof(item),
+                  "%s{\"decomposition\":\"%s\",\"fields_per_cta_xy\":%d,\"x_columns_zt\":%d,"
+                  "\"threads\":[%d,%d,%d],\"ms\":%.5f}",
+                  i ? "," : "", decomp_name(t.decomp), t.plan.fpb_xy, t.plan.xc, t.plan.threads_xy,
+                  t.plan.threads_zt, t.plan.threads_c, t.ms);
+    rep += item;
+  }
+  rep += "]}";
+  return LGF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lgf_status lgf_autotune(lgf_handle h, char* report, size_t len) {
+  lgf_status s = check_handle(h);
+  if (s != LGF_OK) return s;
+  std::string rep = "{";
+  if (h->d.active) {
+    rep += "\"fp64\":";
+    if ((s = tune_lane<double>(h, h->d, rep)) != LGF_OK) return s;
+  }
+  if (h->f.active) {
+    rep += h->d.active ? ",\"fp32\":" : "\"fp32\":";
+    if ((s = tune_lane<float>(h, h->f, rep)) != LGF_OK) return s;
+  }
+  rep += "}";
+  // the trials overwrote the divergence and g: restore the measurement
+  h->have_g = false;
+  if (h->have_links) {
+    if ((s = measure_current(h)) != LGF_OK) return s;
+    if ((s = sync_state(h)) != LGF_OK) return s;
+  } else {
+    LGF_CK(h, cudaStreamSynchronize(h->stream));
+  }
+  if (report && len) {
+    std::snprintf(report, len, "%s", rep.c_str());
+    if (rep.size() >= len) return fail(h, LGF_E_ARG, "report buffer too small");
+  }
+  return LGF_OK;
+}
+
 lgf_status lgf_set_fft_decomposition(lgf_handle h, int32_t decomposition) {
   lgf_status s = check_handle(h);
   if (s != LGF_OK) return s;
@@ -1036,12 +1151,10 @@ lgf_status lgf_set_fft_decomposition(lgf_handle h, int32_t decomposition) {
     return fail(h, LGF_E_UNSUPPORTED, "the learned multiplier runs with the 2D + 2D decomposition only");
   if (decomposition == LGF_FFT_3D1D && ((h->d.active && !h->d.plan.fit_xyz) || (h->f.active && !h->f.plan.fit_xyz)))
     return fail(h, LGF_E_UNSUPPORTED, "the (x, y, z) slab does not fit in shared memory");
-  if (decomposition == h->fft_decomp) return LGF_OK;
   LGF_CK(h, cudaStreamSynchronize(h->stream));
   // the loop graphs hold the old body: rebuild them on the next fix
-  drop_graph(h->d);
-  drop_graph(h->f);
-  h->fft_decomp = decomposition;
+  set_decomp(h->d, decomposition);
+  set_decomp(h->f, decomposition);
   return LGF_OK;
 }
 

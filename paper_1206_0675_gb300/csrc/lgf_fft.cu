@@ -771,7 +771,7 @@ cudaError_t configure_fft_plan(const int L[4], int real_bytes, FFTPlan* p) {
 
 // Candidate plans for the autotuner: every fields-per-CTA count of the (x,y)
 // passes, every x-column count of the (z,t) pass that fits shared memory,
-// and two CTA sizes for each.
+// and three CTA sizes (8, 16 or 32 elements per thread) for each.
 void fft_plan_candidates(const int L[4], int real_bytes, std::vector<FFTPlan>& out) {
   FFTPlan base;
   out.clear();
@@ -785,7 +785,7 @@ void fft_plan_candidates(const int L[4], int real_bytes, std::vector<FFTPlan>& o
     if (hxy + fpb * plane_xy > maxsm) continue;
     for (int xc = 1; xc <= 8; xc *= 2) {
       if (Lx % xc || hzt + (size_t)Lt * (Lz * xc + 1) * cb > maxsm) continue;
-      for (int tdiv = 8; tdiv <= 16; tdiv *= 2) {
+      for (int tdiv = 8; tdiv <= 32; tdiv *= 2) {
         FFTPlan p = base;
         p.fpb_xy = fpb;
         p.smem_xy = hxy + fpb * plane_xy;

@@ -130,3 +130,33 @@ def test_unsupported_combinations():
         with pytest.raises(lgf.LgfError) as e:
             lat.set_fft_decomposition("1d4")
         assert e.value.status == lgf.LGF_E_UNSUPPORTED
+
+
+@pytest.mark.parametrize("prec,store12", [("fp64", False), ("mixed", True)])
+def test_autotune_keeps_results_and_reports(prec, store12):
+    """The autotuner picks the fastest plan or decomposition; the step is
+    the same transform whichever it picks."""
+    ext = (8, 12, 8, 6)
+    U = fields.random_links(ext, eps=0.8, seed=2)
+    with lgf.Lattice(ext, prec, store12=store12, track_G=True) as lat:
+        lat.set_links(U)
+        F0, th0 = lat.measure()
+        rep = lat.autotune()
+        assert lat.measure() == (F0, th0)   # the current links were re-measured
+        lanes = ["fp64"] + (["fp32"] if prec == "mixed" else [])
+        for lane in lanes:
+            c = rep[lane]["candidates"]
+            assert {x["decomposition"] for x in c} == {"2d2d", "1d4", "3d1d"}
+            assert all(x["ms"] > 0 for x in c)
+            assert c[rep[lane]["chosen"]]["ms"] == min(x["ms"] for x in c)
+        with pytest.raises(lgf.LgfError):
+            lat.get_gauge()                 # g was overwritten by the trials
+        if prec == "fp64":
+            lat.step(0.08)
+            Uo, go = O.fa_step(U, 0.08)
+            assert np.max(np.abs(lat.get_gauge() - go)) < 1e-12
+            assert np.max(np.abs(lat.get_links() - Uo)) < 1e-12
+        else:
+            ref = O.fix(U, tol=1e-15, max_iter=6000, track_G=False)
+            it, F, th, conv = lat.fix(1e-15, 6000, 0.08)
+            assert conv and abs(F - ref["F"][-1]) < 1e-10
