@@ -264,6 +264,16 @@ lgf_status lgf_set_switch_theta(lgf_handle h, double theta);
 enum { LGF_FFT_2D2D = 0, LGF_FFT_1D4 = 1, LGF_FFT_3D1D = 2 };
 lgf_status lgf_set_fft_decomposition(lgf_handle h, int32_t decomposition);
 
+/* FP32 phase only: run the link update and the following measurement as one
+ * kernel (enable != 0, the default for LGF_FP32 and LGF_MIXED handles
+ * without LGF_LEARNED) or as two (enable = 0).  The fused kernel reads the
+ * links from one of two buffers and writes the updated links to the other;
+ * it recomputes the updated backward links U'_mu(x - mu^) in registers
+ * instead of reading them back, so the links cross HBM once less per step.
+ * Results are bit-identical either way.  No effect on FP64 phases.
+ * LGF_E_UNSUPPORTED for enable != 0 with LGF_LEARNED.  Synchronises. */
+lgf_status lgf_set_fused_update(lgf_handle h, int32_t enable);
+
 /* Autotuner of a handle: times the transform and g of one step (CUDA events,
  * best of 3 after a warm-up) under every tile plan of the 2D + 2D passes
  * (fields per CTA of the (x,y) passes, x columns of the (z,t) pass, CTA
@@ -272,9 +282,13 @@ lgf_status lgf_set_fft_decomposition(lgf_handle h, int32_t decomposition);
  * for the following steps.  report (may be NULL): receives a JSON object
  * {"fp64": {"chosen": i, "candidates": [{"decomposition", "fields_per_cta_xy",
  * "x_columns_zt", "threads", "ms"}, ...]}, "fp32": ...}; LGF_E_ARG if len is
- * too small (the choice is kept).  Overwrites the divergence workspace and
- * g (lgf_get_gauge then fails until the next step) and re-measures the
- * current links.  Synchronises. */
+ * too small (the choice is kept).  When the environment variable
+ * LGF_AUTOTUNE_CACHE names a file, a choice recorded there for the same
+ * lattice, precision, storage and device is applied without timing (report:
+ * "cached": true, one candidate with "ms": null) and new choices are
+ * appended to it, so that separate runs use the same plan.  Overwrites the
+ * divergence workspace and g (lgf_get_gauge then fails until the next step)
+ * and re-measures the current links.  Synchronises. */
 lgf_status lgf_autotune(lgf_handle h, char* report, size_t len);
 
 /* Phase of an LGF_MIXED handle: 32 while in the FP32 phase, 64 after the

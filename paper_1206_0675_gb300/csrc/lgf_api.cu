@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -24,6 +25,8 @@ constexpr double kSU3Tol = 1e-10;       // input validation threshold
 // of either the FP64 or the FP32 arithmetic.
 template <typename R> struct Lane {
   C2<R>* U = nullptr;      // links [4][rows][3][V]
+  C2<R>* U2 = nullptr;     // second link buffer (FP32 lanes without the learned multiplier)
+  bool fused = false;      // update and measurement run as one kernel, links ping-pong between U and U2
   C2<R>* g = nullptr;      // gauge transform of the last step [grows][3][V]
   C2<R>* D = nullptr;      // packed divergence / FFT workspace [4][V]
   R* K = nullptr;          // filter table [V]
@@ -149,7 +152,7 @@ template <typename R> void set_decomp(Lane<R>& L, int decomposition) {
 
 template <typename R> void free_lane(Lane<R>& L) {
   drop_graph(L);
-  cudaFree(L.U); cudaFree(L.g); cudaFree(L.D); cudaFree(L.K); cudaFree(L.tw); cudaFree(L.pos); cudaFree(L.G);
+  cudaFree(L.U); cudaFree(L.U2); cudaFree(L.g); cudaFree(L.D); cudaFree(L.K); cudaFree(L.tw); cudaFree(L.pos); cudaFree(L.G);
   cudaFree(L.mtab); cudaFree(L.p2f); cudaFree(L.Dlog); cudaFree(L.Dprev);
   L = Lane<R>();
 }
@@ -159,6 +162,13 @@ template <typename R> lgf_status alloc_lane(lgf_ctx* h, Lane<R>& L, int rows, in
   L.rows = rows;
   L.grows = grows;
   LGF_CK(h, dalloc(&L.U, (size_t)4 * rows * 3 * V));
+  // FP32 lanes stream HBM in the update and the measurement: fuse them
+  // (not with the learned multiplier, whose undo of a rejected step
+  // transforms the links in place)
+  if (sizeof(R) == sizeof(float) && !h->learned) {
+    LGF_CK(h, dalloc(&L.U2, (size_t)4 * rows * 3 * V));
+    L.fused = true;
+  }
   LGF_CK(h, dalloc(&L.g, (size_t)grows * 3 * V));
   LGF_CK(h, dalloc(&L.D, (size_t)4 * V));
   LGF_CK(h, dalloc(&L.K, (size_t)V));
@@ -220,8 +230,9 @@ template <typename R> cudaError_t enqueue_measure(lgf_ctx* h, Lane<R>& L, int co
                                                    int only_if_revert = 0) {
   if (L.rows == 3)
     return launch_measure<R, 3>(h->geom, L.U, L.D, h->partials, h->st, count_iter, cond, use_cond, s,
-                                only_if_revert);
-  return launch_measure<R, 2>(h->geom, L.U, L.D, h->partials, h->st, count_iter, cond, use_cond, s, only_if_revert);
+                                only_if_revert, Batch(), L.U2);
+  return launch_measure<R, 2>(h->geom, L.U, L.D, h->partials, h->st, count_iter, cond, use_cond, s, only_if_revert,
+                              Batch(), L.U2);
 }
 
 // Gauge-transform step of a lane given the divergence in L.D (from the last
@@ -233,8 +244,10 @@ template <typename R> cudaError_t enqueue_measure(lgf_ctx* h, Lane<R>& L, int co
 // nothing unless it has work), then the plain sequence with the multiplier.
 // 1D x 4: forward x, y, z; forward t, filter, inverse t; inverse z, y, x; g.
 // 3D + 1D: forward (x,y,z); t with the filter; inverse (x,y,z); g.
+// A fused lane runs K_UM (update and measurement in one kernel) in place of
+// K_UPD and K_MEAS.
 enum { K_A = 0, K_B, K_C, K_UPD, K_MEAS, K_REVERT, K_RESTORE, K_MLP,
-       K_F1X, K_F1Y, K_F1Z, K_T1, K_I1Z, K_I1Y, K_I1X, K_F3, K_I3, K_GD };
+       K_F1X, K_F1Y, K_F1Z, K_T1, K_I1Z, K_I1Y, K_I1X, K_F3, K_I3, K_GD, K_UM };
 
 template <typename R> int body_kernels(const lgf_ctx* h, const Lane<R>& L, int* ks) {
   int n = 0;
@@ -252,13 +265,18 @@ template <typename R> int body_kernels(const lgf_ctx* h, const Lane<R>& L, int* 
     ks[n++] = K_B;
     ks[n++] = K_C;
   }
-  ks[n++] = K_UPD;
-  ks[n++] = K_MEAS;
+  if (L.fused) {
+    ks[n++] = K_UM;
+  } else {
+    ks[n++] = K_UPD;
+    ks[n++] = K_MEAS;
+  }
   return n;
 }
 
 inline int kernel_category(int k) {
   if (k <= K_MEAS) return k;
+  if (k == K_UM) return K_UPD;
   if (k == K_F1X || k == K_F1Y || k == K_F1Z || k == K_F3) return 0;
   if (k == K_T1) return 1;
   if (k >= K_I1Z) return 2;
@@ -322,6 +340,10 @@ template <> cudaError_t enqueue_kernel<float>(lgf_ctx* h, Lane<float>& L, int k,
                           : launch_fft_xy_inv_gauge<float, float, 3>(g, L.plan, L.D, L.tw, L.pos, L.g, L.G, s,
                                                                      Batch(), exact_exp(h));
     case K_UPD: return L.grows == 2 ? launch_update<float, 2, 2>(g, L.U, L.g, s) : launch_update<float, 3, 3>(g, L.U, L.g, s);
+    case K_UM:
+      return L.grows == 2
+                 ? launch_update_measure<float, 2, 2>(g, L.U, L.U2, L.g, L.D, h->partials, h->st, cond, use_cond, s)
+                 : launch_update_measure<float, 3, 3>(g, L.U, L.U2, L.g, L.D, h->partials, h->st, cond, use_cond, s);
     case K_MEAS: return enqueue_measure<float>(h, L, 1, cond, use_cond, s);
     case K_REVERT:
       return L.grows == 2 ? launch_revert<float, 2, 2>(g, L.U, L.g, L.G, h->st, s)
@@ -683,6 +705,7 @@ lgf_status lgf_set_links(lgf_handle h, const double* U, int where) {
     } else {
       if (h->f.rows == 3) LGF_CK(h, (launch_links_from_aos<float, 3>(g, src, h->f.U, h->stream)));
       else LGF_CK(h, (launch_links_from_aos<float, 2>(g, src, h->f.U, h->stream)));
+      LGF_CK(h, cudaMemsetAsync(&h->st->ubuf, 0, sizeof(int), h->stream));  // the links are in buffer U
       if (h->f.G) LGF_CK(h, (launch_set_identity<float, 3>(g, h->f.G, h->stream)));
       if (h->prec == LGF_MIXED) {
         LGF_CK(h, cudaMemcpyAsync(h->U0, src, n * 8, cudaMemcpyDeviceToDevice, h->stream));
@@ -714,8 +737,11 @@ lgf_status lgf_get_links(lgf_handle h, double* U, int where) {
     if (h->d.rows == 3) LGF_CK(h, (launch_links_to_aos<double, 3>(g, h->d.U, dst, h->stream)));
     else LGF_CK(h, (launch_links_to_aos<double, 2>(g, h->d.U, dst, h->stream)));
   } else {
-    if (h->f.rows == 3) LGF_CK(h, (launch_links_to_aos<float, 3>(g, h->f.U, dst, h->stream)));
-    else LGF_CK(h, (launch_links_to_aos<float, 2>(g, h->f.U, dst, h->stream)));
+    s = sync_state(h);  // which buffer of a fused lane holds the current links
+    if (s != LGF_OK) return s;
+    const float2* cur = (h->f.fused && h->st_host->ubuf) ? h->f.U2 : h->f.U;
+    if (h->f.rows == 3) LGF_CK(h, (launch_links_to_aos<float, 3>(g, cur, dst, h->stream)));
+    else LGF_CK(h, (launch_links_to_aos<float, 2>(g, cur, dst, h->stream)));
   }
   return copy_out(h, dst, U, (size_t)4 * 18 * g.V, where);
 }
@@ -1085,6 +1111,32 @@ template <typename R> lgf_status tune_lane(lgf_ctx* h, Lane<R>& L, std::string& 
     trials.push_back({FFT_1D4, L.plan, 0.f});
     if (L.plan.fit_xyz) trials.push_back({FFT_3D1D, L.plan, 0.f});
   }
+  // a choice recorded in the LGF_AUTOTUNE_CACHE file is reused without timing
+  cudaDeviceProp prop;
+  LGF_CK(h, cudaGetDeviceProperties(&prop, h->device));
+  char kb[256];
+  std::snprintf(kb, sizeof(kb), "single,%d,%d,%d,%d,%s,rows=%d,learned=%d,%s", h->geom.L[0], h->geom.L[1],
+                h->geom.L[2], h->geom.L[3], sizeof(R) == 8 ? "fp64" : "fp32", L.rows, h->learned ? 1 : 0, prop.name);
+  std::string key = kb;
+  for (char& c : key)
+    if (c == ' ') c = '_';
+  TuneChoice tc;
+  if (std::getenv("LGF_AUTOTUNE_CACHE") && tune_cache_get(key, &tc)) {
+    for (size_t i = 0; i < trials.size(); ++i)
+      if (trials[i].decomp == tc.decomp && (tc.decomp != FFT_2D2D || tune_choice_matches(trials[i].plan, tc))) {
+        drop_graph(L);
+        L.plan = trials[i].plan;
+        L.decomp = trials[i].decomp;
+        char item[256];
+        std::snprintf(item, sizeof(item),
+                      "{\"cached\":true,\"chosen\":0,\"candidates\":[{\"decomposition\":\"%s\","
+                      "\"fields_per_cta_xy\":%d,\"x_columns_zt\":%d,\"threads\":[%d,%d,%d],\"ms\":null}]}",
+                      decomp_name(L.decomp), L.plan.fpb_xy, L.plan.xc, L.plan.threads_xy, L.plan.threads_zt,
+                      L.plan.threads_c);
+        rep += item;
+        return LGF_OK;
+      }
+  }
   int best = -1;
   for (size_t i = 0; i < trials.size(); ++i) {
     L.plan = trials[i].plan;
@@ -1095,8 +1147,9 @@ template <typename R> lgf_status tune_lane(lgf_ctx* h, Lane<R>& L, std::string& 
   drop_graph(L);
   L.plan = trials[best].plan;
   L.decomp = trials[best].decomp;
+  if (std::getenv("LGF_AUTOTUNE_CACHE")) tune_cache_put(key, tune_choice_of(L.plan, L.decomp));
   char item[256];
-  rep += "{\"chosen\":" + std::to_string(best) + ",\"candidates\":[";
+  rep += "{\"cached\":false,\"chosen\":" + std::to_string(best) + ",\"candidates\":[";
   for (size_t i = 0; i < trials.size(); ++i) {
     const Trial& t = trials[i];
     std::snprintf(item, sizeof(item),
@@ -1139,6 +1192,26 @@ lgf_status lgf_autotune(lgf_handle h, char* report, size_t len) {
     std::snprintf(report, len, "%s", rep.c_str());
     if (rep.size() >= len) return fail(h, LGF_E_ARG, "report buffer too small");
   }
+  return LGF_OK;
+}
+
+lgf_status lgf_set_fused_update(lgf_handle h, int32_t enable) {
+  lgf_status s = check_handle(h);
+  if (s != LGF_OK) return s;
+  Lane<float>& L = h->f;
+  if (!L.active) return LGF_OK;  // FP64 handles never fuse
+  if (enable && !L.U2) return fail(h, LGF_E_UNSUPPORTED, "the learned multiplier needs the unfused update");
+  if ((enable != 0) == L.fused) return LGF_OK;
+  if ((s = sync_state(h)) != LGF_OK) return s;
+  if (!enable && h->st_host->ubuf) {
+    // the unfused update works in place on U: move the current links there
+    LGF_CK(h, cudaMemcpyAsync(L.U, L.U2, sizeof(float2) * 4 * L.rows * 3 * h->geom.V, cudaMemcpyDeviceToDevice,
+                              h->stream));
+    LGF_CK(h, cudaMemsetAsync(&h->st->ubuf, 0, sizeof(int), h->stream));
+    LGF_CK(h, cudaStreamSynchronize(h->stream));
+  }
+  drop_graph(L);
+  L.fused = enable != 0;
   return LGF_OK;
 }
 

@@ -105,42 +105,15 @@ bool extent_ok(int L) {
 
 template <typename T> cudaError_t dalloc(T** p, size_t n) { return cudaMalloc((void**)p, n * sizeof(T)); }
 
-// ---- autotune cache -------------------------------------------------------
-
-std::mutex g_tune_mutex;
-std::map<std::string, FFTPlan> g_tune_cache;
+// ---- autotune cache key ----------------------------------------------------
 
 std::string tune_key(const Geom& g, int n, const char* dev) {
   char buf[256];
   std::snprintf(buf, sizeof(buf), "%d,%d,%d,%d,fp64,n=%d,%s", g.L[0], g.L[1], g.L[2], g.L[3], n, dev);
-  return buf;
-}
-
-void tune_cache_load() {
-  const char* path = std::getenv("LGF_AUTOTUNE_CACHE");
-  if (!path) return;
-  FILE* f = std::fopen(path, "r");
-  if (!f) return;
-  char key[256];
-  FFTPlan p{};
-  while (std::fscanf(f, "%255s %d %d %d %d %d", key, &p.fpb_xy, &p.xc, &p.threads_xy, &p.threads_zt, &p.threads_c) ==
-         6)
-    g_tune_cache.emplace(key, p);  // geometry fields are filled from the candidates on lookup
-  std::fclose(f);
-}
-
-void tune_cache_store(const std::string& key, const FFTPlan& p) {
-  const char* path = std::getenv("LGF_AUTOTUNE_CACHE");
-  if (!path) return;
-  FILE* f = std::fopen(path, "a");
-  if (!f) return;
-  std::fprintf(f, "%s %d %d %d %d %d\n", key.c_str(), p.fpb_xy, p.xc, p.threads_xy, p.threads_zt, p.threads_c);
-  std::fclose(f);
-}
-
-bool same_choice(const FFTPlan& a, const FFTPlan& b) {
-  return a.fpb_xy == b.fpb_xy && a.xc == b.xc && a.threads_xy == b.threads_xy && a.threads_zt == b.threads_zt &&
-         a.threads_c == b.threads_c;
+  std::string k = buf;
+  for (char& c : k)
+    if (c == ' ') c = '_';
+  return k;
 }
 
 // Device time of passes A, B and C of a class under a plan (best of 3).
@@ -177,21 +150,13 @@ lgf_status autotune(lgf_batch_ctx* b, ClassLane& C) {
   cudaDeviceProp prop;
   LGF_BCK(b, cudaGetDeviceProperties(&prop, b->device));
   const std::string key = tune_key(C.geom, C.n, prop.name);
-  {
-    std::lock_guard<std::mutex> lock(g_tune_mutex);
-    static bool loaded = false;
-    if (!loaded) {
-      tune_cache_load();
-      loaded = true;
-    }
-    auto it = g_tune_cache.find(key);
-    if (it != g_tune_cache.end())
-      for (const FFTPlan& p : cand)
-        if (same_choice(p, it->second)) {
-          C.plan = p;
-          return LGF_OK;
-        }
-  }
+  TuneChoice tc;
+  if (tune_cache_get(key, &tc))
+    for (const FFTPlan& p : cand)
+      if (tc.decomp == FFT_2D2D && tune_choice_matches(p, tc)) {
+        C.plan = p;
+        return LGF_OK;
+      }
   LGF_BCK(b, cudaMemsetAsync(C.D, 0, sizeof(double2) * 4 * C.geom.V * C.n, b->stream));
   float best = 1e30f;
   for (const FFTPlan& p : cand) {
@@ -203,9 +168,7 @@ lgf_status autotune(lgf_batch_ctx* b, ClassLane& C) {
     }
   }
   C.tuned_ms = best;
-  std::lock_guard<std::mutex> lock(g_tune_mutex);
-  g_tune_cache[key] = C.plan;
-  tune_cache_store(key, C.plan);
+  tune_cache_put(key, tune_choice_of(C.plan, FFT_2D2D));
   return LGF_OK;
 }
 

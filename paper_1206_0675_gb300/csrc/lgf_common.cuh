@@ -39,6 +39,16 @@ template <typename R> __device__ __forceinline__ C2<R> cmulc(C2<R> a, C2<R> b) {
 template <typename R> __device__ __forceinline__ C2<R> cconjmul(C2<R> a, C2<R> b) {
   return mkc<R>(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
 }
+// The same products with their rounding fixed by explicit fused
+// multiply-adds, whatever the compiler's contraction choices.  The link
+// update uses these, so that the fused update + measurement can recompute a
+// neighbour's updated link bit for bit.
+template <typename R> __device__ __forceinline__ C2<R> cmul_fx(C2<R> a, C2<R> b) {
+  return mkc<R>(fma(a.x, b.x, -(a.y * b.y)), fma(a.x, b.y, a.y * b.x));
+}
+template <typename R> __device__ __forceinline__ C2<R> cmulc_fx(C2<R> a, C2<R> b) {
+  return mkc<R>(fma(a.x, b.x, a.y * b.y), fma(a.y, b.x, -(a.x * b.y)));
+}
 // acc + a * b
 template <typename R> __device__ __forceinline__ C2<R> cfma(C2<R> a, C2<R> b, C2<R> acc) {
   return mkc<R>(fma(a.x, b.x, fma(-a.y, b.y, acc.x)), fma(a.x, b.y, fma(a.y, b.x, acc.y)));

@@ -14,6 +14,10 @@
 // shared-memory accesses are free of bank conflicts in every direction.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "lgf_internal.h"
@@ -803,6 +807,55 @@ void fft_plan_candidates(const int L[4], int real_bytes, std::vector<FFTPlan>& o
       }
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// autotune cache
+// ---------------------------------------------------------------------------
+
+static std::mutex g_tune_mutex;
+static std::map<std::string, TuneChoice> g_tune_cache;
+static bool g_tune_loaded = false;
+
+TuneChoice tune_choice_of(const FFTPlan& p, int decomp) {
+  return TuneChoice{decomp, p.fpb_xy, p.xc, p.threads_xy, p.threads_zt, p.threads_c};
+}
+
+bool tune_choice_matches(const FFTPlan& p, const TuneChoice& c) {
+  return p.fpb_xy == c.fpb_xy && p.xc == c.xc && p.threads_xy == c.threads_xy && p.threads_zt == c.threads_zt &&
+         p.threads_c == c.threads_c;
+}
+
+bool tune_cache_get(const std::string& key, TuneChoice* c) {
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  if (!g_tune_loaded) {
+    g_tune_loaded = true;
+    const char* path = std::getenv("LGF_AUTOTUNE_CACHE");
+    FILE* f = path ? std::fopen(path, "r") : nullptr;
+    if (f) {
+      char k[256];
+      TuneChoice t{};
+      while (std::fscanf(f, "%255s %d %d %d %d %d %d", k, &t.decomp, &t.fpb_xy, &t.xc, &t.threads_xy, &t.threads_zt,
+                         &t.threads_c) == 7)
+        g_tune_cache[k] = t;
+      std::fclose(f);
+    }
+  }
+  auto it = g_tune_cache.find(key);
+  if (it == g_tune_cache.end()) return false;
+  *c = it->second;
+  return true;
+}
+
+void tune_cache_put(const std::string& key, const TuneChoice& c) {
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  g_tune_cache[key] = c;
+  const char* path = std::getenv("LGF_AUTOTUNE_CACHE");
+  FILE* f = path ? std::fopen(path, "a") : nullptr;
+  if (!f) return;
+  std::fprintf(f, "%s %d %d %d %d %d %d\n", key.c_str(), c.decomp, c.fpb_xy, c.xc, c.threads_xy, c.threads_zt,
+               c.threads_c);
+  std::fclose(f);
 }
 
 template <typename K> static cudaError_t allow_smem(K kernel, size_t bytes) {

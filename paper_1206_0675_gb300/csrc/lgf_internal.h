@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
 #include <vector>
 
 #include "lgf_common.cuh"
@@ -29,6 +30,7 @@ struct DevState {
   int use_m;         // the running step multiplies the filter by the learned table
   int revert;        // the last learned step lowered F: undo it and redo it with the plain filter
   int n_fallback;    // learned steps rejected since the counter was reset
+  int ubuf;          // fused lanes: which of the two link buffers holds the current links
   double* F_hist;    // F after measurement number i (i = iter) if i < hist_cap
   double* theta_hist;
 };
@@ -62,10 +64,23 @@ inline int64_t measure_blocks(int64_t V) { return (V + MEASURE_THREADS - 1) / ME
 // body undoes the step and redoes it with the plain filter.
 // In batch mode (B->st set) each configuration's state is B->st[z] and its
 // last CTA sets that state's `done` instead of a graph condition.
+// links_alt (fused lanes): the second link buffer, read instead of links when st->ubuf is set.
 template <typename R, int ROWS>
 cudaError_t launch_measure(const Geom& g, const C2<R>* links, C2<R>* delta, double* partials, DevState* st,
                            int count_iter, unsigned long long cond_handle, int use_cond, cudaStream_t s,
-                           int only_if_revert = 0, const Batch& B = Batch());
+                           int only_if_revert = 0, const Batch& B = Batch(), const C2<R>* links_alt = nullptr);
+
+// Link update fused with the measurement that follows it: the links are read
+// from buffer st->ubuf of {U0, U1} and the updated links written to the other
+// buffer; the updated backward links U'_mu(x - mu^) = g(x - mu^) U_mu(x - mu^)
+// g^dag(x) are recomputed in registers instead of being read back, then
+// Delta, F and theta are formed and reduced as by launch_measure with
+// count_iter = 1, and the last CTA flips st->ubuf.  The result is
+// bit-identical to launch_update followed by launch_measure.
+template <typename R, int LROWS, int GROWS>
+cudaError_t launch_update_measure(const Geom& g, C2<R>* U0, C2<R>* U1, const C2<R>* gfield, C2<R>* delta,
+                                  double* partials, DevState* st, unsigned long long cond, int use_cond,
+                                  cudaStream_t s);
 
 // Undo of the last update when st->revert is set: U_mu(x) <- g^dag(x) U_mu(x)
 // g(x + mu^) and, when G is given (3 rows, precision R), G <- g^dag G.
@@ -192,6 +207,18 @@ cudaError_t launch_gauge_from_delta(const Geom& g, const C2<R>* data, C2<RG>* gf
                                     const Batch& B = Batch(), int exact_exp = 0);
 
 cudaError_t configure_fft_plan(const int L[4], int real_bytes, FFTPlan* p);
+
+// An autotuner's choice: the decomposition and the tile fields of the plan.
+struct TuneChoice {
+  int decomp, fpb_xy, xc, threads_xy, threads_zt, threads_c;
+};
+TuneChoice tune_choice_of(const FFTPlan& p, int decomp);
+bool tune_choice_matches(const FFTPlan& p, const TuneChoice& c);  // same tile fields
+// Autotune cache, kept for the process and, when the environment variable
+// LGF_AUTOTUNE_CACHE names a file, read from it on first use and appended to
+// (one "key decomposition fpb xc threads_xy threads_zt threads_c" line per choice).
+bool tune_cache_get(const std::string& key, TuneChoice* c);
+void tune_cache_put(const std::string& key, const TuneChoice& c);
 // All plans the autotuner may choose among for a lattice shape.
 void fft_plan_candidates(const int L[4], int real_bytes, std::vector<FFTPlan>& out);
 // Digit-reversal position tables of the four directions, concatenated

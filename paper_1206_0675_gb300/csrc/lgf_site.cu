@@ -61,59 +61,14 @@ __device__ __forceinline__ void block_sum2(double& a, double& b) {
   __syncthreads();
 }
 
-template <typename R, int ROWS>
-__global__ void __launch_bounds__(MEASURE_THREADS)
-measure_kernel(Geom g, MatField<R, ROWS> U, C2<R>* __restrict__ delta, double* __restrict__ partials,
-               DevState* __restrict__ st, int count_iter, unsigned long long cond, int use_cond, int only_if_revert,
-               Batch B) {
-  if (batch_skip(B)) return;
-  const bool batch = B.st != nullptr;
-  if (batch) {
-    const int cfg = blockIdx.z;
-    st = B.st + cfg;
-    U.p += cfg * B.s_links;
-    delta += cfg * B.s_delta;
-    partials += cfg * B.s_part;
-  }
-  if (only_if_revert && !st->revert) return;
-  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  // per-site sums in the link precision; warp sums likewise, everything
-  // beyond a warp in FP64
-  R fsum = 0, tsum = 0;
-  if (s < g.V) {
-    int c[4];
-    site_coords(g, s, c);
-    // W = sum_mu [U_mu(x - mu^) - U_mu(x)]; only the entries that enter its
-    // traceless anti-Hermitian part are accumulated.
-    R im0 = 0, im1 = 0, im2 = 0;           // Im W_ii
-    C2<R> w01 = mkc<R>(0, 0), w02 = mkc<R>(0, 0), w12 = mkc<R>(0, 0);  // W_ij - conj(W_ji)
-#pragma unroll
-    for (int mu = 0; mu < 4; ++mu) {
-      M3<R> u;
-      U.load_ro(mu, s, u);
-      fsum += u.e[0][0].x + u.e[1][1].x + u.e[2][2].x;
-      im0 -= u.e[0][0].y; im1 -= u.e[1][1].y; im2 -= u.e[2][2].y;
-      w01 = csub<R>(w01, csub<R>(u.e[0][1], cconj<R>(u.e[1][0])));
-      w02 = csub<R>(w02, csub<R>(u.e[0][2], cconj<R>(u.e[2][0])));
-      w12 = csub<R>(w12, csub<R>(u.e[1][2], cconj<R>(u.e[2][1])));
-      M3<R> b;
-      U.load_ro(mu, site_back(g, s, c, mu), b);
-      im0 += b.e[0][0].y; im1 += b.e[1][1].y; im2 += b.e[2][2].y;
-      w01 = cadd<R>(w01, csub<R>(b.e[0][1], cconj<R>(b.e[1][0])));
-      w02 = cadd<R>(w02, csub<R>(b.e[0][2], cconj<R>(b.e[2][0])));
-      w12 = cadd<R>(w12, csub<R>(b.e[1][2], cconj<R>(b.e[2][1])));
-    }
-    const R tr = (im0 + im1 + im2) * (R)(1.0 / 3.0);
-    const R a0 = im0 - tr, a1 = im1 - tr, a2 = im2 - tr;
-    const C2<R> d01 = cscale<R>(w01, (R)0.5), d02 = cscale<R>(w02, (R)0.5), d12 = cscale<R>(w12, (R)0.5);
-    delta[s] = mkc<R>(a0, a1);
-    delta[g.V + s] = d01;
-    delta[2 * g.V + s] = d02;
-    delta[3 * g.V + s] = d12;
-    // ||Delta_A||_F^2
-    tsum = a0 * a0 + a1 * a1 + a2 * a2 +
-           (R)2 * (d01.x * d01.x + d01.y * d01.y + d02.x * d02.x + d02.y * d02.y + d12.x * d12.x + d12.y * d12.y);
-  }
+// Reduction of the per-thread F and theta sums and, in the last CTA to
+// finish, the controller update: F and theta, the iteration count, the
+// history, the status word, the batch retirement flag or the graph's WHILE
+// condition; flip_ubuf != 0 also flips st->ubuf (after every CTA has read it).
+template <typename R>
+__device__ __forceinline__ void measure_tail(const Geom& g, R fsum, R tsum, double* __restrict__ partials,
+                                             DevState* __restrict__ st, int count_iter, unsigned long long cond,
+                                             int use_cond, bool batch, int flip_ubuf) {
   double fb, tb;
   block_sum2_warps<R>(warp_sum_r<R>(fsum), warp_sum_r<R>(tsum), fb, tb);
   __shared__ int is_last;
@@ -164,6 +119,7 @@ measure_kernel(Geom g, MatField<R, ROWS> U, C2<R>* __restrict__ delta, double* _
     }
     const bool finite = isfinite(F) && isfinite(th);
     if (!finite) st->status = ST_NONFINITE;
+    if (flip_ubuf) st->ubuf ^= 1;
     st->ticket = 0u;
     if (batch) st->done = !(finite && th >= st->tol && it < st->max_iter);
     if (use_cond) {
@@ -173,14 +129,186 @@ measure_kernel(Geom g, MatField<R, ROWS> U, C2<R>* __restrict__ delta, double* _
   }
 }
 
+// ||Delta_A||_F^2 of the packed components, as an explicit FMA chain (the
+// same rounding in every kernel that forms it).
+template <typename R>
+__device__ __forceinline__ R delta_norm2(R a0, R a1, R a2, C2<R> d01, C2<R> d02, C2<R> d12) {
+  R off = d01.x * d01.x;
+  off = fma(d01.y, d01.y, off);
+  off = fma(d02.x, d02.x, off);
+  off = fma(d02.y, d02.y, off);
+  off = fma(d12.x, d12.x, off);
+  off = fma(d12.y, d12.y, off);
+  R dia = a0 * a0;
+  dia = fma(a1, a1, dia);
+  dia = fma(a2, a2, dia);
+  return fma((R)2, off, dia);
+}
+
+template <typename R, int ROWS>
+__global__ void __launch_bounds__(MEASURE_THREADS)
+measure_kernel(Geom g, MatField<R, ROWS> U, const C2<R>* __restrict__ links_alt, C2<R>* __restrict__ delta,
+               double* __restrict__ partials, DevState* __restrict__ st, int count_iter, unsigned long long cond,
+               int use_cond, int only_if_revert, Batch B) {
+  if (batch_skip(B)) return;
+  const bool batch = B.st != nullptr;
+  if (batch) {
+    const int cfg = blockIdx.z;
+    st = B.st + cfg;
+    U.p += cfg * B.s_links;
+    delta += cfg * B.s_delta;
+    partials += cfg * B.s_part;
+  }
+  if (only_if_revert && !st->revert) return;
+  if (links_alt != nullptr && st->ubuf) U.p = const_cast<C2<R>*>(links_alt);  // ping-pong links of a fused lane
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // per-site sums in the link precision; warp sums likewise, everything
+  // beyond a warp in FP64
+  R fsum = 0, tsum = 0;
+  if (s < g.V) {
+    int c[4];
+    site_coords(g, s, c);
+    // W = sum_mu [U_mu(x - mu^) - U_mu(x)]; only the entries that enter its
+    // traceless anti-Hermitian part are accumulated.
+    R im0 = 0, im1 = 0, im2 = 0;           // Im W_ii
+    C2<R> w01 = mkc<R>(0, 0), w02 = mkc<R>(0, 0), w12 = mkc<R>(0, 0);  // W_ij - conj(W_ji)
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+      M3<R> u;
+      U.load_ro(mu, s, u);
+      fsum += u.e[0][0].x + u.e[1][1].x + u.e[2][2].x;
+      im0 -= u.e[0][0].y; im1 -= u.e[1][1].y; im2 -= u.e[2][2].y;
+      w01 = csub<R>(w01, csub<R>(u.e[0][1], cconj<R>(u.e[1][0])));
+      w02 = csub<R>(w02, csub<R>(u.e[0][2], cconj<R>(u.e[2][0])));
+      w12 = csub<R>(w12, csub<R>(u.e[1][2], cconj<R>(u.e[2][1])));
+      M3<R> b;
+      U.load_ro(mu, site_back(g, s, c, mu), b);
+      im0 += b.e[0][0].y; im1 += b.e[1][1].y; im2 += b.e[2][2].y;
+      w01 = cadd<R>(w01, csub<R>(b.e[0][1], cconj<R>(b.e[1][0])));
+      w02 = cadd<R>(w02, csub<R>(b.e[0][2], cconj<R>(b.e[2][0])));
+      w12 = cadd<R>(w12, csub<R>(b.e[1][2], cconj<R>(b.e[2][1])));
+    }
+    const R tr = (im0 + im1 + im2) * (R)(1.0 / 3.0);
+    const R a0 = im0 - tr, a1 = im1 - tr, a2 = im2 - tr;
+    const C2<R> d01 = cscale<R>(w01, (R)0.5), d02 = cscale<R>(w02, (R)0.5), d12 = cscale<R>(w12, (R)0.5);
+    delta[s] = mkc<R>(a0, a1);
+    delta[g.V + s] = d01;
+    delta[2 * g.V + s] = d02;
+    delta[3 * g.V + s] = d12;
+    // ||Delta_A||_F^2
+    tsum = delta_norm2<R>(a0, a1, a2, d01, d02, d12);
+  }
+  measure_tail<R>(g, fsum, tsum, partials, st, count_iter, cond, use_cond, batch, 0);
+}
+
 template <typename R, int ROWS>
 cudaError_t launch_measure(const Geom& g, const C2<R>* links, C2<R>* delta, double* partials, DevState* st,
                            int count_iter, unsigned long long cond_handle, int use_cond, cudaStream_t s,
-                           int only_if_revert, const Batch& B) {
+                           int only_if_revert, const Batch& B, const C2<R>* links_alt) {
   MatField<R, ROWS> U{const_cast<C2<R>*>(links), g.V};
   const int64_t nb = measure_blocks(g.V);
   measure_kernel<R, ROWS><<<dim3((unsigned)nb, 1, (unsigned)B.n), MEASURE_THREADS, 0, s>>>(
-      g, U, delta, partials, st, count_iter, cond_handle, use_cond, only_if_revert, B);
+      g, U, links_alt, delta, partials, st, count_iter, cond_handle, use_cond, only_if_revert, B);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// fused update + measure (ping-pong links, backward neighbours recomputed)
+// ---------------------------------------------------------------------------
+
+// o = g u h^dagger: rows 0, 1 by products, row 2 = (row0 x row1)^* -- the
+// same arithmetic as update_kernel, so that a recomputed neighbour link is
+// bit-identical to the one its own thread stores.
+template <typename R>
+__device__ __forceinline__ void gauge_product(const M3<R>& gl, const M3<R>& u, const M3<R>& h, M3<R>& o) {
+  C2<R> T[2][3];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      C2<R> acc = cmul_fx<R>(gl.e[i][0], u.e[0][j]);
+      acc = cfma<R>(gl.e[i][1], u.e[1][j], acc);
+      T[i][j] = cfma<R>(gl.e[i][2], u.e[2][j], acc);
+    }
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      C2<R> acc = cmulc_fx<R>(T[i][0], h.e[j][0]);
+      acc = cfmac<R>(T[i][1], h.e[j][1], acc);
+      o.e[i][j] = cfmac<R>(T[i][2], h.e[j][2], acc);
+    }
+  su3_third_row<R>(o.e[0], o.e[1], o.e[2]);
+}
+
+// Contribution of one link M to W = sum_mu [U_mu(x - mu^) - U_mu(x)]: the
+// entries that enter its traceless anti-Hermitian part, with sign sg.
+template <typename R>
+__device__ __forceinline__ void add_antiherm(const M3<R>& m, R sg, R& im0, R& im1, R& im2, C2<R>& w01, C2<R>& w02,
+                                             C2<R>& w12) {
+  im0 += sg * m.e[0][0].y;
+  im1 += sg * m.e[1][1].y;
+  im2 += sg * m.e[2][2].y;
+  const C2<R> a = csub<R>(m.e[0][1], cconj<R>(m.e[1][0]));
+  const C2<R> b = csub<R>(m.e[0][2], cconj<R>(m.e[2][0]));
+  const C2<R> c = csub<R>(m.e[1][2], cconj<R>(m.e[2][1]));
+  w01 = mkc<R>(w01.x + sg * a.x, w01.y + sg * a.y);
+  w02 = mkc<R>(w02.x + sg * b.x, w02.y + sg * b.y);
+  w12 = mkc<R>(w12.x + sg * c.x, w12.y + sg * c.y);
+}
+
+template <typename R, int LROWS, int GROWS>
+__global__ void __launch_bounds__(MEASURE_THREADS, 3)
+update_measure_kernel(Geom g, C2<R>* __restrict__ U0, C2<R>* __restrict__ U1, MatField<R, GROWS> Gf,
+                      C2<R>* __restrict__ delta, double* __restrict__ partials, DevState* __restrict__ st,
+                      unsigned long long cond, int use_cond) {
+  const int cur = st->ubuf;
+  const MatField<R, LROWS> Us{cur ? U1 : U0, g.V}, Ud{cur ? U0 : U1, g.V};
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  R fsum = 0, tsum = 0;
+  if (s < g.V) {
+    int c[4];
+    site_coords(g, s, c);
+    M3<R> gx;
+    Gf.load_ro(0, s, gx);
+    R im0 = 0, im1 = 0, im2 = 0;
+    C2<R> w01 = mkc<R>(0, 0), w02 = mkc<R>(0, 0), w12 = mkc<R>(0, 0);
+#pragma unroll 1
+    for (int mu = 0; mu < 4; ++mu) {
+      M3<R> u, h, o;
+      Us.load_ro(mu, s, u);
+      Gf.load_ro(0, site_fwd(g, s, c, mu), h);
+      gauge_product<R>(gx, u, h, o);
+      Ud.store(mu, s, o);
+      fsum += o.e[0][0].x + o.e[1][1].x + o.e[2][2].x;
+      add_antiherm<R>(o, (R)-1, im0, im1, im2, w01, w02, w12);
+      const int64_t sb = site_back(g, s, c, mu);
+      M3<R> b, gb, ob;
+      Us.load_ro(mu, sb, b);
+      Gf.load_ro(0, sb, gb);
+      gauge_product<R>(gb, b, gx, ob);
+      add_antiherm<R>(ob, (R)1, im0, im1, im2, w01, w02, w12);
+    }
+    const R tr = (im0 + im1 + im2) * (R)(1.0 / 3.0);
+    const R a0 = im0 - tr, a1 = im1 - tr, a2 = im2 - tr;
+    const C2<R> d01 = cscale<R>(w01, (R)0.5), d02 = cscale<R>(w02, (R)0.5), d12 = cscale<R>(w12, (R)0.5);
+    delta[s] = mkc<R>(a0, a1);
+    delta[g.V + s] = d01;
+    delta[2 * g.V + s] = d02;
+    delta[3 * g.V + s] = d12;
+    tsum = delta_norm2<R>(a0, a1, a2, d01, d02, d12);
+  }
+  measure_tail<R>(g, fsum, tsum, partials, st, 1, cond, use_cond, false, 1);
+}
+
+template <typename R, int LROWS, int GROWS>
+cudaError_t launch_update_measure(const Geom& g, C2<R>* U0, C2<R>* U1, const C2<R>* gfield, C2<R>* delta,
+                                  double* partials, DevState* st, unsigned long long cond, int use_cond,
+                                  cudaStream_t s) {
+  MatField<R, GROWS> Gf{const_cast<C2<R>*>(gfield), g.V};
+  const int64_t nb = measure_blocks(g.V);
+  update_measure_kernel<R, LROWS, GROWS><<<(unsigned)nb, MEASURE_THREADS, 0, s>>>(g, U0, U1, Gf, delta, partials,
+                                                                                  st, cond, use_cond);
   return cudaGetLastError();
 }
 
@@ -229,7 +357,7 @@ update_kernel(Geom g, MatField<R, LROWS> U, MatField<R, GROWS> Gf, Batch B) {
     for (int i = 0; i < 2; ++i)
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
-        C2<R> acc = cmul<R>(gx[i][0], u.e[0][j]);
+        C2<R> acc = cmul_fx<R>(gx[i][0], u.e[0][j]);
         acc = cfma<R>(gx[i][1], u.e[1][j], acc);
         T[i][j] = cfma<R>(gx[i][2], u.e[2][j], acc);
       }
@@ -239,7 +367,7 @@ update_kernel(Geom g, MatField<R, LROWS> U, MatField<R, GROWS> Gf, Batch B) {
     for (int i = 0; i < 2; ++i)
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
-        C2<R> acc = cmulc<R>(T[i][0], h.e[j][0]);
+        C2<R> acc = cmulc_fx<R>(T[i][0], h.e[j][0]);
         acc = cfmac<R>(T[i][1], h.e[j][1], acc);
         o.e[i][j] = cfmac<R>(T[i][2], h.e[j][2], acc);
       }
@@ -607,7 +735,8 @@ cudaError_t launch_project_sites_f32_to_f64(const Geom& g, const float2* G32, do
 
 #define LGF_INST_R_ROWS(R, ROWS)                                                                                     \
   template cudaError_t launch_measure<R, ROWS>(const Geom&, const C2<R>*, C2<R>*, double*, DevState*, int,           \
-                                               unsigned long long, int, cudaStream_t, int, const Batch&);           \
+                                               unsigned long long, int, cudaStream_t, int, const Batch&,            \
+                                               const C2<R>*);                                                       \
   template cudaError_t launch_links_from_aos<R, ROWS>(const Geom&, const double*, C2<R>*, cudaStream_t);            \
   template cudaError_t launch_links_to_aos<R, ROWS>(const Geom&, const C2<R>*, double*, cudaStream_t);              \
   template cudaError_t launch_sites_to_aos<R, ROWS>(const Geom&, const C2<R>*, double*, cudaStream_t);              \
@@ -631,6 +760,11 @@ template cudaError_t launch_update<double, 3, 3>(const Geom&, C2<double>*, const
 template cudaError_t launch_update<double, 2, 3>(const Geom&, C2<double>*, const C2<double>*, cudaStream_t, const Batch&);
 template cudaError_t launch_update<float, 2, 2>(const Geom&, C2<float>*, const C2<float>*, cudaStream_t, const Batch&);
 template cudaError_t launch_update<float, 3, 3>(const Geom&, C2<float>*, const C2<float>*, cudaStream_t, const Batch&);
+#define LGF_INST_UM(R, LR, GR)                                                                                     \
+  template cudaError_t launch_update_measure<R, LR, GR>(const Geom&, C2<R>*, C2<R>*, const C2<R>*, C2<R>*, double*, \
+                                                        DevState*, unsigned long long, int, cudaStream_t);
+LGF_INST_UM(float, 2, 2)
+LGF_INST_UM(float, 3, 3)
 template cudaError_t launch_delta_to_aos<double>(const Geom&, const C2<double>*, double*, cudaStream_t);
 template cudaError_t launch_delta_to_aos<float>(const Geom&, const C2<float>*, double*, cudaStream_t);
 template cudaError_t launch_filter_table<double>(const Geom&, const double*, int, double, double, int, double*,

@@ -76,31 +76,45 @@ def time_steps(lat, steps, warmup):
     return dt, ms
 
 
-def kernel_table(ext, U, steps=20, warmup=5, peak_gbs=None, decomps=("2d2d",)):
+def kernel_table(ext, U, steps=20, warmup=5, peak_gbs=None, decomps=("2d2d",), unfused=False):
     """Per-kernel CUDA-event times and compulsory-traffic GB/s of every precision/storage.
 
     With several decompositions of the 4D transform, every storage is timed
     with each of them; pass A / B / C then read "forward passes", "the pass
     with the filter" and "inverse passes + g" (the GB/s of the 2D + 2D passes
-    are left out for the others, whose traffic differs)."""
+    are left out for the others, whose traffic differs).  FP32 storages run
+    the fused update + measurement (reported under "update"); with unfused
+    they are also timed with the two kernels apart ("<storage>/unfused")."""
     V = int(np.prod(ext))
     out = {}
     for name, (prec, s12, rb, rows, grows) in STORAGES.items():
         byt = accounting.bytes_per_site(rb, rows, grows, k_bytes=rb)
-        for dec in decomps:
+        variants = [(dec, True) for dec in decomps]
+        if unfused and prec == "fp32":
+            variants.append(("2d2d", False))
+        for dec, fused in variants:
             key = name if dec == "2d2d" else f"{name}/{dec}"
+            if not fused:
+                key = f"{name}/unfused"
+            fused_here = fused and prec == "fp32"
             with lgf.Lattice(ext, prec, store12=s12) as lat:
                 try:
                     lat.set_fft_decomposition(dec)
                 except lgf.LgfError as e:
                     out[key] = {"unsupported": str(e)}
                     continue
+                if prec == "fp32":
+                    lat.set_fused_update(fused)
                 lat.set_links(U)
                 dt, ms = time_steps(lat, steps, warmup)
-            row = {"iters_per_s": 1.0 / dt, "ms_per_step": dt * 1e3, "kernels": {}}
+            row = {"iters_per_s": 1.0 / dt, "ms_per_step": dt * 1e3, "fused_update_measure": fused_here,
+                   "kernels": {}}
             for k, t in zip(accounting.KERNELS, ms):
                 own = dec == "2d2d" or k in ("update", "measure")
-                gbs = byt[k] * V / (t * 1e-3) / 1e9 if (t > 0 and own) else None
+                b = byt[k]
+                if fused_here and k == "update":
+                    b = accounting.fused_update_measure_bytes(rb, rows, grows)
+                gbs = b * V / (t * 1e-3) / 1e9 if (t > 0 and own) else None
                 row["kernels"][k] = {"ms": t, "gbs": gbs, "hbm_frac": gbs / peak_gbs if (gbs and peak_gbs) else None}
             out[key] = row
     return out
@@ -117,6 +131,8 @@ def main():
     ap.add_argument("--weights", default=DEFAULT_WEIGHTS)
     ap.add_argument("--extents", default=None, help="Lx,Ly,Lz,Lt (overrides --lattice)")
     ap.add_argument("--kernels", action="store_true", help="per-kernel table of every precision/storage")
+    ap.add_argument("--unfused", action="store_true",
+                    help="with --kernels: also time the FP32 storages with the update and measurement apart")
     ap.add_argument("--decomps", default="2d2d",
                     help="decompositions of the 4D transform for --kernels (2d2d,1d4,3d1d)")
     ap.add_argument("--switch", type=float, default=None, help="switch level of the mixed modes")
@@ -134,7 +150,8 @@ def main():
             pass
         U = fields.random_links(ext, args.eps, a)
         print(json.dumps({"extents": ext, "eps": args.eps, "seed": a, "peak_gbs": peak,
-                          "table": kernel_table(ext, U, peak_gbs=peak, decomps=args.decomps.split(","))}),
+                          "table": kernel_table(ext, U, peak_gbs=peak, decomps=args.decomps.split(","),
+                                                unfused=args.unfused)}),
               flush=True)
         return
     weights = np.load(args.weights)

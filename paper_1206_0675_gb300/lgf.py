@@ -60,6 +60,7 @@ SIGNATURES = [
     ("lgf_set_switch_theta", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
     ("lgf_set_fft_decomposition", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     ("lgf_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_size_t]),
+    ("lgf_set_fused_update", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     ("lgf_get_timing", ctypes.c_int, [ctypes.c_void_p, _c_dbl_p, ctypes.c_int32, _c_int_p]),
     ("lgf_measure_static", ctypes.c_int, [ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_void_p]),
@@ -497,6 +498,11 @@ class Lattice:
         code = {"2d2d": LGF_FFT_2D2D, "1d4": LGF_FFT_1D4, "3d1d": LGF_FFT_3D1D}[decomposition]
         _check(self.handle, load_library().lgf_set_fft_decomposition(ctypes.c_void_p(self.handle), code),
                "lgf_set_fft_decomposition")
+
+    def set_fused_update(self, enable: bool) -> None:
+        """FP32 phase: update and measurement as one kernel (default) or as two."""
+        _check(self.handle, load_library().lgf_set_fused_update(ctypes.c_void_p(self.handle), int(bool(enable))),
+               "lgf_set_fused_update")
 
     def autotune(self) -> dict:
         """Time every tile plan and decomposition of the transform, keep the fastest; returns the report."""

@@ -160,3 +160,29 @@ def test_autotune_keeps_results_and_reports(prec, store12):
             ref = O.fix(U, tol=1e-15, max_iter=6000, track_G=False)
             it, F, th, conv = lat.fix(1e-15, 6000, 0.08)
             assert conv and abs(F - ref["F"][-1]) < 1e-10
+
+
+def test_autotune_cache_file_reuses_the_choice(tmp_path, monkeypatch):
+    """With LGF_AUTOTUNE_CACHE set, the first tuning is recorded and a later
+    handle of the same shape applies it without timing."""
+    path = tmp_path / "tune.cache"
+    monkeypatch.setenv("LGF_AUTOTUNE_CACHE", str(path))
+    ext = (6, 8, 12, 4)
+    U = fields.random_links(ext, eps=0.6, seed=9)
+    with lgf.Lattice(ext, "fp64") as lat:
+        lat.set_links(U)
+        first = lat.autotune()["fp64"]
+    assert not first["cached"]
+    chosen = first["candidates"][first["chosen"]]
+    lines = path.read_text().splitlines()
+    assert any(l.startswith("single,6,8,12,4,fp64,rows=3,learned=0,") for l in lines)
+    with lgf.Lattice(ext, "fp64") as lat:
+        lat.set_links(U)
+        again = lat.autotune()["fp64"]
+        assert again["cached"]
+        c = again["candidates"][0]
+        for k in ("decomposition", "fields_per_cta_xy", "x_columns_zt", "threads"):
+            assert c[k] == chosen[k]
+        lat.step(0.08)
+        Uo, _ = O.fa_step(U, 0.08)
+        assert np.max(np.abs(lat.get_links() - Uo)) < 1e-12
