@@ -162,7 +162,7 @@ class ClockSampler:
 def oracle_iterations(U, n):
     """n bodies of Algorithm 1 with the CPU oracle; returns (seconds, cores used)."""
     from oracle import lgf_oracle as O
-    K = O.fa_filter(EXT, ALPHA)
+    K = O.fa_filter(O.extents_of(U), ALPHA)
     _, _, D = O.measure(U)
     r0 = resource.getrusage(resource.RUSAGE_SELF)
     t0 = time.perf_counter()
@@ -384,7 +384,11 @@ def run_lgf(args, rank, world, local_rank):
     if rank == 0 and world == 1 and not args.no_cpu:
         dt, cores, _ = oracle_iterations(U, args.cpu_iters)
         cpu = {"value": args.cpu_iters / dt, "unit": "iters/s", "cores": cores, "kind": "oracle",
-               "sample": f"{args.cpu_iters} oracle bodies of Algorithm 1 on the same 32^4 field (numpy FP64)"}
+               "sample": f"{args.cpu_iters} oracle bodies of Algorithm 1 on the same 32^4 field (numpy FP64)",
+               "seconds_per_iter": {"32^4": dt / args.cpu_iters}}
+        for L, n in ((8, 20), (16, 5)):     # the smaller lattices of the workload, a few seconds each
+            dts, _, _ = oracle_iterations(fields.random_links((L,) * 4, EPS, rank), n)
+            cpu["seconds_per_iter"][f"{L}^4"] = dts / n
 
     if rank == 0:
         line = {
@@ -400,6 +404,7 @@ def run_lgf(args, rank, world, local_rank):
             "gpu_launches": KERNELS_PER_STEP[decomp] * args.steps,
             "autotune": {"fft_decomposition": decomp, "fields_per_cta_xy": chosen["fields_per_cta_xy"],
                          "x_columns_zt": chosen["x_columns_zt"], "threads": chosen["threads"],
+                         "lines_x": chosen["lines_x"], "x_columns_line": chosen["x_columns_line"],
                          "transform_ms": chosen["ms"], "default_plan_transform_ms": default_ms,
                          "candidates": len(tune["candidates"]), "cached": tune["cached"],
                          "note": "lgf_autotune before the warm-up: every tile plan of the 2D+2D passes and the "

@@ -1108,7 +1108,13 @@ template <typename R> lgf_status tune_lane(lgf_ctx* h, Lane<R>& L, std::string& 
   std::vector<Trial> trials;
   for (const FFTPlan& p : cand) trials.push_back({FFT_2D2D, p, 0.f});
   if (!h->learned) {
-    trials.push_back({FFT_1D4, L.plan, 0.f});
+    // 1D x 4 with every tile of its passes: 8, 16 or 32 x-lines per CTA in
+    // the x pass, 4 to 32 x columns per CTA in the y, z, t passes
+    for (int nl : {8, 16, 32})
+      for (int xc : {4, 8, 16, 32}) {
+        FFTPlan p = L.plan;
+        if (set_line_tiles(h->geom.L, (int)sizeof(R), nl, xc, &p)) trials.push_back({FFT_1D4, p, 0.f});
+      }
     if (L.plan.fit_xyz) trials.push_back({FFT_3D1D, L.plan, 0.f});
   }
   // a choice recorded in the LGF_AUTOTUNE_CACHE file is reused without timing
@@ -1123,16 +1129,17 @@ template <typename R> lgf_status tune_lane(lgf_ctx* h, Lane<R>& L, std::string& 
   TuneChoice tc;
   if (std::getenv("LGF_AUTOTUNE_CACHE") && tune_cache_get(key, &tc)) {
     for (size_t i = 0; i < trials.size(); ++i)
-      if (trials[i].decomp == tc.decomp && (tc.decomp != FFT_2D2D || tune_choice_matches(trials[i].plan, tc))) {
+      if (trials[i].decomp == tc.decomp && tune_choice_matches(trials[i].plan, tc)) {
         drop_graph(L);
         L.plan = trials[i].plan;
         L.decomp = trials[i].decomp;
         char item[256];
         std::snprintf(item, sizeof(item),
                       "{\"cached\":true,\"chosen\":0,\"candidates\":[{\"decomposition\":\"%s\","
-                      "\"fields_per_cta_xy\":%d,\"x_columns_zt\":%d,\"threads\":[%d,%d,%d],\"ms\":null}]}",
+                      "\"fields_per_cta_xy\":%d,\"x_columns_zt\":%d,\"threads\":[%d,%d,%d],\"lines_x\":%d,"
+                      "\"x_columns_line\":%d,\"ms\":null}]}",
                       decomp_name(L.decomp), L.plan.fpb_xy, L.plan.xc, L.plan.threads_xy, L.plan.threads_zt,
-                      L.plan.threads_c);
+                      L.plan.threads_c, L.plan.nl_x, L.plan.xc_line);
         rep += item;
         return LGF_OK;
       }
@@ -1154,9 +1161,9 @@ template <typename R> lgf_status tune_lane(lgf_ctx* h, Lane<R>& L, std::string& 
     const Trial& t = trials[i];
     std::snprintf(item, sizeof(item),
                   "%s{\"decomposition\":\"%s\",\"fields_per_cta_xy\":%d,\"x_columns_zt\":%d,"
-                  "\"threads\":[%d,%d,%d],\"ms\":%.5f}",
+                  "\"threads\":[%d,%d,%d],\"lines_x\":%d,\"x_columns_line\":%d,\"ms\":%.5f}",
                   i ? "," : "", decomp_name(t.decomp), t.plan.fpb_xy, t.plan.xc, t.plan.threads_xy,
-                  t.plan.threads_zt, t.plan.threads_c, t.ms);
+                  t.plan.threads_zt, t.plan.threads_c, t.plan.nl_x, t.plan.xc_line, t.ms);
     rep += item;
   }
   rep += "]}";

@@ -153,7 +153,8 @@ lgf_status autotune(lgf_batch_ctx* b, ClassLane& C) {
   TuneChoice tc;
   if (tune_cache_get(key, &tc))
     for (const FFTPlan& p : cand)
-      if (tc.decomp == FFT_2D2D && tune_choice_matches(p, tc)) {
+      if (tc.decomp == FFT_2D2D && p.fpb_xy == tc.fpb_xy && p.xc == tc.xc && p.threads_xy == tc.threads_xy &&
+          p.threads_zt == tc.threads_zt && p.threads_c == tc.threads_c) {
         C.plan = p;
         return LGF_OK;
       }

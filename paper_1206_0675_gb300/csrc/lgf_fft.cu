@@ -711,6 +711,24 @@ static int threads_for(int points) {
 // in the x pass, up to 16 x columns in the y, z, t passes (runs of 16
 // elements), and the whole (x, y, z) slab of one field in the 3D pass when
 // it fits.
+// Tiles of the 1D passes: nl x-lines per CTA in the x pass, xc x columns in
+// the y, z, t passes.  False when they do not divide the lattice.
+bool set_line_tiles(const int L[4], int real_bytes, int nl, int xc, FFTPlan* p) {
+  const size_t cb = 2 * (size_t)real_bytes;
+  const int64_t xlines = (int64_t)L[1] * L[2] * L[3];
+  if (nl < 1 || xc < 1 || xlines % nl || L[0] % xc) return false;
+  p->nl_x = nl;
+  p->xc_line = xc;
+  for (int mu = 0; mu < 4; ++mu) {
+    const int lines = mu == 0 ? nl : xc;
+    const size_t hdr = (size_t)((L[mu] + 1) & ~1) * cb + (size_t)((L[mu] + 7) & ~7) * 2;
+    p->smem_line[mu] = hdr + (size_t)lines * (L[mu] + 1) * cb;
+    p->threads_line[mu] = threads_for(lines * L[mu]);
+    if (p->smem_line[mu] > 220 * 1024) return false;
+  }
+  return true;
+}
+
 static void configure_alt_passes(const int L[4], int real_bytes, FFTPlan* p) {
   const size_t cb = 2 * (size_t)real_bytes, maxsm = 220 * 1024;
   const int64_t V = (int64_t)L[0] * L[1] * L[2] * L[3];
@@ -718,16 +736,9 @@ static void configure_alt_passes(const int L[4], int real_bytes, FFTPlan* p) {
   int nl = 32;
   while (nl > 1 && (xlines % nl || smem_header_bytes<double>(L[0], 0) + (size_t)nl * (L[0] + 1) * cb > 64 * 1024))
     --nl;
-  p->nl_x = nl;
   int xc = 16;
   while (xc > 1 && L[0] % xc) --xc;
-  p->xc_line = xc;
-  for (int mu = 0; mu < 4; ++mu) {
-    const int lines = mu == 0 ? p->nl_x : p->xc_line;
-    const size_t hdr = (size_t)((L[mu] + 1) & ~1) * cb + (size_t)((L[mu] + 7) & ~7) * 2;
-    p->smem_line[mu] = hdr + (size_t)lines * (L[mu] + 1) * cb;
-    p->threads_line[mu] = threads_for(lines * L[mu]);
-  }
+  set_line_tiles(L, real_bytes, nl, xc, p);
   const size_t hxyz = (size_t)((L[0] + L[1] + L[2] + 1) & ~1) * cb + (size_t)((L[0] + L[1] + L[2] + 7) & ~7) * 2;
   p->smem_xyz = hxyz + (size_t)L[2] * L[1] * (L[0] + 1) * cb;
   p->fit_xyz = p->smem_xyz <= maxsm ? 1 : 0;
@@ -818,12 +829,12 @@ static std::map<std::string, TuneChoice> g_tune_cache;
 static bool g_tune_loaded = false;
 
 TuneChoice tune_choice_of(const FFTPlan& p, int decomp) {
-  return TuneChoice{decomp, p.fpb_xy, p.xc, p.threads_xy, p.threads_zt, p.threads_c};
+  return TuneChoice{decomp, p.fpb_xy, p.xc, p.threads_xy, p.threads_zt, p.threads_c, p.nl_x, p.xc_line};
 }
 
 bool tune_choice_matches(const FFTPlan& p, const TuneChoice& c) {
   return p.fpb_xy == c.fpb_xy && p.xc == c.xc && p.threads_xy == c.threads_xy && p.threads_zt == c.threads_zt &&
-         p.threads_c == c.threads_c;
+         p.threads_c == c.threads_c && p.nl_x == c.nl_x && p.xc_line == c.xc_line;
 }
 
 bool tune_cache_get(const std::string& key, TuneChoice* c) {
@@ -835,8 +846,8 @@ bool tune_cache_get(const std::string& key, TuneChoice* c) {
     if (f) {
       char k[256];
       TuneChoice t{};
-      while (std::fscanf(f, "%255s %d %d %d %d %d %d", k, &t.decomp, &t.fpb_xy, &t.xc, &t.threads_xy, &t.threads_zt,
-                         &t.threads_c) == 7)
+      while (std::fscanf(f, "%255s %d %d %d %d %d %d %d %d", k, &t.decomp, &t.fpb_xy, &t.xc, &t.threads_xy,
+                         &t.threads_zt, &t.threads_c, &t.nl_x, &t.xc_line) == 9)
         g_tune_cache[k] = t;
       std::fclose(f);
     }
@@ -853,8 +864,8 @@ void tune_cache_put(const std::string& key, const TuneChoice& c) {
   const char* path = std::getenv("LGF_AUTOTUNE_CACHE");
   FILE* f = path ? std::fopen(path, "a") : nullptr;
   if (!f) return;
-  std::fprintf(f, "%s %d %d %d %d %d %d\n", key.c_str(), c.decomp, c.fpb_xy, c.xc, c.threads_xy, c.threads_zt,
-               c.threads_c);
+  std::fprintf(f, "%s %d %d %d %d %d %d %d %d\n", key.c_str(), c.decomp, c.fpb_xy, c.xc, c.threads_xy, c.threads_zt,
+               c.threads_c, c.nl_x, c.xc_line);
   std::fclose(f);
 }
 

@@ -210,13 +210,17 @@ cudaError_t configure_fft_plan(const int L[4], int real_bytes, FFTPlan* p);
 
 // An autotuner's choice: the decomposition and the tile fields of the plan.
 struct TuneChoice {
-  int decomp, fpb_xy, xc, threads_xy, threads_zt, threads_c;
+  int decomp, fpb_xy, xc, threads_xy, threads_zt, threads_c, nl_x, xc_line;
 };
+// Tiles of the 1D passes (nl x-lines per CTA, xc x columns in the strided
+// passes); false if they do not divide the lattice or fit shared memory.
+bool set_line_tiles(const int L[4], int real_bytes, int nl, int xc, FFTPlan* p);
 TuneChoice tune_choice_of(const FFTPlan& p, int decomp);
 bool tune_choice_matches(const FFTPlan& p, const TuneChoice& c);  // same tile fields
 // Autotune cache, kept for the process and, when the environment variable
 // LGF_AUTOTUNE_CACHE names a file, read from it on first use and appended to
-// (one "key decomposition fpb xc threads_xy threads_zt threads_c" line per choice).
+// (one "key decomposition fpb xc threads_xy threads_zt threads_c nl_x xc_line"
+// line per choice).
 bool tune_cache_get(const std::string& key, TuneChoice* c);
 void tune_cache_put(const std::string& key, const TuneChoice& c);
 // All plans the autotuner may choose among for a lattice shape.
