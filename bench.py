@@ -206,6 +206,20 @@ def run_reference(args, rank, world):
 # GPU arm
 # ---------------------------------------------------------------------------
 
+def max_over_ranks(ms, device):
+    """The largest of the ranks' elapsed times (ms); the job is as slow as its slowest replica."""
+    import torch
+    import torch.distributed as tdist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(steps, world, max_ms):
+    """Steps per second of all replicas together: world * steps in the slowest rank's time."""
+    return world * steps / (max_ms / 1e3)
+
+
 def time_steps(torch, lat, K):
     st = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -253,11 +267,9 @@ def run_lgf(args, rank, world, local_rank):
     kms, nsteps = lat.get_timing()
     lat.set_timing(False)
     if dist:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, "cuda")
     ms_step = ms / args.steps
-    value = world * args.steps / (ms / 1e3)
+    value = whole_job_rate(args.steps, world, ms)
 
     ops = accounting.fp64_ops_per_site(EXT, rows=3, decomposition=decomp)
     byt = accounting.bytes_per_site(8, 3, 3, k_bytes=8, decomposition=decomp)
@@ -283,6 +295,8 @@ def run_lgf(args, rank, world, local_rank):
     # ---- end to end through host buffers ----------------------------------
     pinned = torch.from_numpy(U).pin_memory()
     Ke = min(args.steps, 20)
+    if dist:
+        tdist.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(Ke):
@@ -291,6 +305,8 @@ def run_lgf(args, rank, world, local_rank):
         lat.measure()
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
+    if dist:
+        e2e_s = max_over_ranks(e2e_s * 1e3, "cuda") / 1e3
     e2e = {"value": world * Ke / e2e_s, "unit": "iters/s", "h2d_bytes_per_step": int(U.nbytes),
            "d2h_bytes_per_step": 16,
            "note": "per step: lgf_set_links from pinned host memory (H2D copy, SU(3) check, layout conversion, "

@@ -1,0 +1,60 @@
+"""Writes the stored oracle trajectories under tests/golden/.
+
+Every value in the fixtures comes from the FP64 CPU oracle (oracle/, which
+follows Sec. 2 and Algorithm 1 of arXiv:1206.0675) on the seeded synthetic
+fields of paper_1206_0675_gb300/fields.py; nothing here calls the CUDA path.
+The fixtures guard the oracle against unintended changes and give the GPU
+tests stored expectations that need no oracle run.
+
+    python tests/golden/make_golden.py
+"""
+
+import json
+import os
+import sys
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+from oracle import lgf_oracle as O  # noqa: E402
+from paper_1206_0675_gb300 import fields  # noqa: E402
+
+CASES = [
+    # name, extents (Lx, Ly, Lz, Lt), eps, seed, alpha, iterations, exact_exp
+    ("fa_4x6x4x8_eps0.8_seed5", (4, 6, 4, 8), 0.8, 5, 0.08, 25, False),
+    ("fa_exp_6x4x4x6_eps1.0_seed2", (6, 4, 4, 6), 1.0, 2, 0.08, 25, True),
+    ("fa_3x4x6x9_eps0.5_seed0", (3, 4, 6, 9), 0.5, 0, 0.1, 25, False),
+]
+SAMPLE_SITES = [(0, 0, 0, 0), (1, 2, 3, 1), (3, 1, 0, 2)]  # (x, y, z, t), wrapped into the lattice
+
+
+def make(name, ext, eps, seed, alpha, n, exact_exp):
+    U = fields.random_links(ext, eps, seed)
+    res = O.fix(U, alpha=alpha, tol=0.0, max_iter=n, track_G=True, exact_exp=exact_exp)
+    lx, ly, lz, lt = ext
+    G = res["G"]
+    samples = []
+    for (x, y, z, t) in SAMPLE_SITES:
+        x, y, z, t = x % lx, y % ly, z % lz, t % lt
+        samples.append({"site": [x, y, z, t], "G_re": G[t, z, y, x].real.tolist(), "G_im": G[t, z, y, x].imag.tolist()})
+    return {
+        "source": "FP64 CPU oracle, Algorithm 1 of arXiv:1206.0675 (oracle/lgf_oracle.py fix); fields from "
+                  "paper_1206_0675_gb300/fields.py random_links",
+        "extents": list(ext), "eps": eps, "seed": seed, "alpha": alpha, "exact_exp": exact_exp,
+        "iterations": n, "F": res["F"].tolist(), "theta": res["theta"].tolist(),
+        "plaquette": O.plaquette(U), "G_samples": samples,
+    }
+
+
+def main():
+    for name, *args in CASES:
+        path = os.path.join(HERE, name + ".json")
+        with open(path, "w") as f:
+            json.dump(make(name, *args), f, indent=1)
+        print("wrote", path)
+
+
+if __name__ == "__main__":
+    main()
