@@ -11,6 +11,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/lgf.h"
 #include "lgf_internal.h"
 #include "lgf_mlp.h"
@@ -65,6 +67,17 @@ struct TimingRing {
   bool enabled = false;
 };
 
+}  // namespace
+
+namespace {
+// NVTX range over one library call or phase (visible in Nsight timelines;
+// no cost when no tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 }  // namespace
 
 struct lgf_ctx {
@@ -675,6 +688,7 @@ lgf_status lgf_create(const int32_t extents[4], lgf_precision prec, uint32_t fla
 }
 
 lgf_status lgf_set_links(lgf_handle h, const double* U, int where) {
+  NvtxRange nvtx_("lgf_set_links");
   lgf_status s = check_handle(h);
   if (s != LGF_OK) return s;
   if (!U || (where != LGF_HOST && where != LGF_DEVICE)) return fail(h, LGF_E_ARG, "bad links pointer or location");
@@ -727,6 +741,7 @@ lgf_status lgf_set_links(lgf_handle h, const double* U, int where) {
 }
 
 lgf_status lgf_get_links(lgf_handle h, double* U, int where) {
+  NvtxRange nvtx_("lgf_get_links");
   lgf_status s = check_handle(h);
   if (s != LGF_OK) return s;
   if (!U || (where != LGF_HOST && where != LGF_DEVICE)) return fail(h, LGF_E_ARG, "bad links pointer or location");
@@ -747,6 +762,7 @@ lgf_status lgf_get_links(lgf_handle h, double* U, int where) {
 }
 
 lgf_status lgf_step(lgf_handle h, double alpha) {
+  NvtxRange nvtx_("lgf_step");
   lgf_status s = check_handle(h);
   if (s != LGF_OK) return s;
   if (!h->have_links) return fail(h, LGF_E_STATE, "no links set");
@@ -759,6 +775,7 @@ lgf_status lgf_step(lgf_handle h, double alpha) {
 }
 
 lgf_status lgf_measure(lgf_handle h, double* F, double* theta) {
+  NvtxRange nvtx_("lgf_measure");
   lgf_status s = check_handle(h);
   if (s != LGF_OK) return s;
   if (!h->have_links) return fail(h, LGF_E_STATE, "no links set");
@@ -773,12 +790,14 @@ lgf_status lgf_measure(lgf_handle h, double* F, double* theta) {
 
 lgf_status lgf_fix(lgf_handle h, double theta_tol, int32_t max_iter, double alpha, int32_t* iters, double* F,
                    double* theta) {
+  NvtxRange nvtx_("lgf_fix");
   lgf_status s = check_handle(h);
   if (s != LGF_OK) return s;
   if (!h->have_links) return fail(h, LGF_E_STATE, "no links set");
   if (!(theta_tol >= 0.0) || max_iter < 0 || !std::isfinite(alpha)) return fail(h, LGF_E_ARG, "bad fix arguments");
   if (h->learned && !h->mlp_w) return fail(h, LGF_E_STATE, "LGF_LEARNED handle without a loaded preconditioner");
   if (h->phase == 32) {
+    NvtxRange phase32("FP32 phase");
     if ((s = ensure_filter<float>(h, h->f, alpha)) != LGF_OK) return s;
     const double tol1 = h->prec == LGF_MIXED ? std::max(theta_tol, h->switch_theta) : theta_tol;
     if ((s = run_loop<float>(h, h->f, tol1, max_iter, 1)) != LGF_OK) return s;
@@ -792,6 +811,7 @@ lgf_status lgf_fix(lgf_handle h, double theta_tol, int32_t max_iter, double alph
     LGF_CK(h, launch_set_state(h->st, theta_tol, max_iter, 1, h->hist_cap, h->hist_F, h->hist_T, h->stream));
   }
   if (h->phase == 64) {
+    NvtxRange phase64("FP64 phase");
     if ((s = ensure_filter<double>(h, h->d, alpha)) != LGF_OK) return s;
     if ((s = run_loop<double>(h, h->d, theta_tol, max_iter, 0)) != LGF_OK) return s;
     h->have_g = h->have_g || h->st_host->iter > 0;
@@ -1175,6 +1195,7 @@ template <typename R> lgf_status tune_lane(lgf_ctx* h, Lane<R>& L, std::string& 
 extern "C" {
 
 lgf_status lgf_autotune(lgf_handle h, char* report, size_t len) {
+  NvtxRange nvtx_("lgf_autotune");
   lgf_status s = check_handle(h);
   if (s != LGF_OK) return s;
   std::string rep = "{";
