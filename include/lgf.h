@@ -259,8 +259,8 @@ lgf_status lgf_set_switch_theta(lgf_handle h, double theta);
  *     inverse (x,y,z) pass, then g -- three passes plus g; only where one
  *     field's (x,y,z) slab fits in shared memory (up to 16^3 in FP64, 24^3
  *     in FP32), else LGF_E_UNSUPPORTED.
- * All three give the same result up to rounding.  With LGF_LEARNED only
- * LGF_FFT_2D2D is accepted (LGF_E_UNSUPPORTED).  Synchronises. */
+ * All three give the same result up to rounding (the learned multiplier is
+ * applied in the pass that carries the filter in each).  Synchronises. */
 enum { LGF_FFT_2D2D = 0, LGF_FFT_1D4 = 1, LGF_FFT_3D1D = 2 };
 lgf_status lgf_set_fft_decomposition(lgf_handle h, int32_t decomposition);
 
@@ -277,8 +277,8 @@ lgf_status lgf_set_fused_update(lgf_handle h, int32_t enable);
 /* Autotuner of a handle: times the transform and g of one step (CUDA events,
  * best of 3 after a warm-up) under every tile plan of the 2D + 2D passes
  * (fields per CTA of the (x,y) passes, x columns of the (z,t) pass, CTA
- * sizes) and under LGF_FFT_1D4 and LGF_FFT_3D1D where they apply (not with
- * LGF_LEARNED), for each precision the handle runs in, and keeps the fastest
+ * sizes) and under LGF_FFT_1D4 (with its tiles) and LGF_FFT_3D1D where it
+ * fits, for each precision the handle runs in, and keeps the fastest
  * for the following steps.  report (may be NULL): receives a JSON object
  * {"fp64": {"chosen": i, "candidates": [{"decomposition", "fields_per_cta_xy",
  * "x_columns_zt", "threads", "ms"}, ...]}, "fp32": ...}; LGF_E_ARG if len is

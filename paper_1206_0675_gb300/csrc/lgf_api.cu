@@ -305,7 +305,7 @@ template <typename R> cudaError_t enqueue_alt_fft(lgf_ctx* h, Lane<R>& L, int k,
     case K_F1X: return launch_fft_line<R>(g, L.plan, 0, L.D, L.tw, L.pos, L.K, -1, 4, s);
     case K_F1Y: return launch_fft_line<R>(g, L.plan, 1, L.D, L.tw, L.pos, L.K, -1, 4, s);
     case K_F1Z: return launch_fft_line<R>(g, L.plan, 2, L.D, L.tw, L.pos, L.K, -1, 4, s);
-    case K_T1: return launch_fft_line<R>(g, L.plan, 3, L.D, L.tw, L.pos, L.K, 0, 4, s);
+    case K_T1: return launch_fft_line<R>(g, L.plan, 3, L.D, L.tw, L.pos, L.K, 0, 4, s, Batch(), L.mtab, &h->st->use_m);
     case K_I1Z: return launch_fft_line<R>(g, L.plan, 2, L.D, L.tw, L.pos, L.K, +1, 4, s);
     case K_I1Y: return launch_fft_line<R>(g, L.plan, 1, L.D, L.tw, L.pos, L.K, +1, 4, s);
     case K_I1X: return launch_fft_line<R>(g, L.plan, 0, L.D, L.tw, L.pos, L.K, +1, 4, s);
@@ -1127,16 +1127,14 @@ template <typename R> lgf_status tune_lane(lgf_ctx* h, Lane<R>& L, std::string& 
   struct Trial { int decomp; FFTPlan plan; float ms; };
   std::vector<Trial> trials;
   for (const FFTPlan& p : cand) trials.push_back({FFT_2D2D, p, 0.f});
-  if (!h->learned) {
-    // 1D x 4 with every tile of its passes: 8, 16 or 32 x-lines per CTA in
-    // the x pass, 4 to 32 x columns per CTA in the y, z, t passes
-    for (int nl : {8, 16, 32})
-      for (int xc : {4, 8, 16, 32}) {
-        FFTPlan p = L.plan;
-        if (set_line_tiles(h->geom.L, (int)sizeof(R), nl, xc, &p)) trials.push_back({FFT_1D4, p, 0.f});
-      }
-    if (L.plan.fit_xyz) trials.push_back({FFT_3D1D, L.plan, 0.f});
-  }
+  // 1D x 4 with every tile of its passes: 8, 16 or 32 x-lines per CTA in
+  // the x pass, 4 to 32 x columns per CTA in the y, z, t passes
+  for (int nl : {8, 16, 32})
+    for (int xc : {4, 8, 16, 32}) {
+      FFTPlan p = L.plan;
+      if (set_line_tiles(h->geom.L, (int)sizeof(R), nl, xc, &p)) trials.push_back({FFT_1D4, p, 0.f});
+    }
+  if (L.plan.fit_xyz) trials.push_back({FFT_3D1D, L.plan, 0.f});
   // a choice recorded in the LGF_AUTOTUNE_CACHE file is reused without timing
   cudaDeviceProp prop;
   LGF_CK(h, cudaGetDeviceProperties(&prop, h->device));
@@ -1248,8 +1246,6 @@ lgf_status lgf_set_fft_decomposition(lgf_handle h, int32_t decomposition) {
   if (s != LGF_OK) return s;
   if (decomposition != LGF_FFT_2D2D && decomposition != LGF_FFT_1D4 && decomposition != LGF_FFT_3D1D)
     return fail(h, LGF_E_ARG, "unknown decomposition");
-  if (decomposition != LGF_FFT_2D2D && h->learned)
-    return fail(h, LGF_E_UNSUPPORTED, "the learned multiplier runs with the 2D + 2D decomposition only");
   if (decomposition == LGF_FFT_3D1D && ((h->d.active && !h->d.plan.fit_xyz) || (h->f.active && !h->f.plan.fit_xyz)))
     return fail(h, LGF_E_UNSUPPORTED, "the (x, y, z) slab does not fit in shared memory");
   LGF_CK(h, cudaStreamSynchronize(h->stream));

@@ -337,10 +337,16 @@ struct LinePass {
 
 // mode -1: forward DFT; +1: inverse DFT (unnormalised); 0: forward DFT,
 // multiplication by K (same layout as the field), inverse DFT.
+// mtab (mode 0, may be NULL): learned multiplier per momentum class, applied
+// when *use_m != 0; the class of momentum k is (min(k_mu, L_mu - k_mu))_mu in
+// a table of H.x * H.y * H.z * H.w classes.
 template <typename R>
-__global__ void __launch_bounds__(512) fft_line_kernel(LinePass lp, FFTDir d, int64_t V, C2<R>* __restrict__ data,
+__global__ void __launch_bounds__(512) fft_line_kernel(LinePass lp, FFTDir d, Geom g, C2<R>* __restrict__ data,
                                                        const C2<R>* __restrict__ twg, const short* __restrict__ posg,
-                                                       const R* __restrict__ K, int mode, Lines ln, Batch B) {
+                                                       const R* __restrict__ K, int mode, Lines ln,
+                                                       const float* __restrict__ mtab, const int* __restrict__ use_m,
+                                                       int4 H, Batch B) {
+  const int64_t V = g.V;
   if (batch_skip(B)) return;
   data += blockIdx.z * B.s_delta;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -376,9 +382,17 @@ __global__ void __launch_bounds__(512) fft_line_kernel(LinePass lp, FFTDir d, in
     fft_lines_dif<R, +1>(tile, ln, d, tw);
   } else {
     fft_lines_dit<R, -1>(tile, ln, d, tw);
+    const bool learned = mtab != nullptr && *use_m != 0;
     for (int i = threadIdx.x; i < n_el; i += blockDim.x) {
       LGF_LINE_IDX(i)
-      const R k = __ldg(&K[site]);
+      R k = __ldg(&K[site]);
+      if (learned) {
+        int c[4];
+        site_coords(g, site, c);
+        const int fx = min(c[0], g.L[0] - c[0]), fy = min(c[1], g.L[1] - c[1]);
+        const int fz = min(c[2], g.L[2] - c[2]), ft = min(c[3], g.L[3] - c[3]);
+        k *= (R)__ldg(&mtab[((ft * H.z + fz) * H.y + fy) * H.x + fx]);
+      }
       C2<R>& e = tile[l * RS + n];
       e = mkc<R>(e.x * k, e.y * k);
     }
@@ -915,7 +929,8 @@ cudaError_t launch_fft_zt(const Geom& g, const FFTPlan& p, C2<R>* data, const C2
 
 template <typename R>
 cudaError_t launch_fft_line(const Geom& g, const FFTPlan& p, int mu, C2<R>* data, const C2<R>* tw, const short* pos,
-                            const R* K, int mode, int nfields, cudaStream_t s, const Batch& B) {
+                            const R* K, int mode, int nfields, cudaStream_t s, const Batch& B, const float* mtab,
+                            const int* use_m) {
   const int N = g.L[mu];
   LinePass lp;
   lp.N = N;
@@ -931,8 +946,9 @@ cudaError_t launch_fft_line(const Geom& g, const FFTPlan& p, int mu, C2<R>* data
   if (e != cudaSuccess) return e;
   const int off = mu == 0 ? 0 : mu == 1 ? g.L[0] : mu == 2 ? g.L[0] + g.L[1] : g.L[0] + g.L[1] + g.L[2];
   const Lines ln = make_lines(lp.nl, lp.nl, N + 1, 0, 1);
+  const int4 H = make_int4(g.L[0] / 2 + 1, g.L[1] / 2 + 1, g.L[2] / 2 + 1, g.L[3] / 2 + 1);
   fft_line_kernel<R><<<dim3((unsigned)blocks, (unsigned)nfields, (unsigned)B.n), p.threads_line[mu], smem, s>>>(
-      lp, p.d[mu], g.V, data, tw + off, pos + off, K, mode, ln, B);
+      lp, p.d[mu], g, data, tw + off, pos + off, K, mode, ln, mtab, use_m, H, B);
   return cudaGetLastError();
 }
 
@@ -1025,7 +1041,8 @@ LGF_INST_G(float, float, 2)
 LGF_INST_G(float, float, 3)
 #define LGF_INST_ALT(R)                                                                                         \
   template cudaError_t launch_fft_line<R>(const Geom&, const FFTPlan&, int, C2<R>*, const C2<R>*, const short*, \
-                                          const R*, int, int, cudaStream_t, const Batch&);                      \
+                                          const R*, int, int, cudaStream_t, const Batch&, const float*,         \
+                                          const int*);                                                          \
   template cudaError_t launch_fft_xyz<R>(const Geom&, const FFTPlan&, C2<R>*, const C2<R>*, const short*, int,  \
                                          int, cudaStream_t, const Batch&);
 LGF_INST_ALT(double)

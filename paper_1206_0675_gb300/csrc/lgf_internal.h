@@ -192,10 +192,12 @@ cudaError_t launch_fft_xy_inv_gauge(const Geom& g, const FFTPlan& p, C2<R>* data
                                     int exact_exp = 0);
 
 // 1D pass along mu (0..3) over nfields fields: mode -1 forward, +1 inverse,
-// 0 forward, multiply by K, inverse.
+// 0 forward, multiply by K (and by the learned table mtab when *use_m != 0),
+// inverse.
 template <typename R>
 cudaError_t launch_fft_line(const Geom& g, const FFTPlan& p, int mu, C2<R>* data, const C2<R>* tw, const short* pos,
-                            const R* K, int mode, int nfields, cudaStream_t s, const Batch& B = Batch());
+                            const R* K, int mode, int nfields, cudaStream_t s, const Batch& B = Batch(),
+                            const float* mtab = nullptr, const int* use_m = nullptr);
 // 3D DFT over every (x, y, z) slab (requires p.fit_xyz); sign -1 / +1.
 template <typename R>
 cudaError_t launch_fft_xyz(const Geom& g, const FFTPlan& p, C2<R>* data, const C2<R>* tw, const short* pos, int sign,

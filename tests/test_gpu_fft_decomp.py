@@ -126,10 +126,30 @@ def test_unsupported_combinations():
             lat.set_fft_decomposition("3d1d")   # a 32^3 FP64 slab is 540 KB
         assert e.value.status == lgf.LGF_E_UNSUPPORTED
         lat.set_fft_decomposition("1d4")
-    with lgf.Lattice((8, 8, 8, 8), "fp64", learned=True) as lat:
-        with pytest.raises(lgf.LgfError) as e:
-            lat.set_fft_decomposition("1d4")
-        assert e.value.status == lgf.LGF_E_UNSUPPORTED
+
+
+@pytest.mark.parametrize("decomp", ["1d4", "3d1d"])
+def test_learned_multiplier_in_the_filter_pass(decomp):
+    """With LGF_LEARNED the t pass of 1D x 4 and 3D + 1D applies the network's
+    multiplier exactly where pass B of 2D + 2D does: the same trajectory up to
+    the transforms' rounding, and the same fallbacks."""
+    from paper_1206_0675_gb300.preconditioner import DEFAULT_WEIGHTS
+    weights = np.load(DEFAULT_WEIGHTS)
+    ext = (8, 8, 8, 8)
+    U = fields.random_links(ext, eps=1.0, seed=21)
+    runs = {}
+    for d in ("2d2d", decomp):
+        with lgf.Lattice(ext, "fp64", learned=True) as lat:
+            lat.load_preconditioner(weights)
+            lat.set_fft_decomposition(d)
+            lat.set_links(U)
+            Fh, Th = lat.set_trace(41)
+            lat.fix(0.0, 40, 0.08)
+            runs[d] = (Fh.copy(), Th.copy(), lat.fallbacks())
+    (F0, T0, n0), (F1, T1, n1) = runs["2d2d"], runs[decomp]
+    assert n0 == n1
+    assert np.allclose(F1, F0, rtol=1e-10, atol=0)
+    assert np.allclose(T1, T0, rtol=1e-8, atol=0)
 
 
 @pytest.mark.parametrize("prec,store12", [("fp64", False), ("mixed", True)])
