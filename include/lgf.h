@@ -165,16 +165,20 @@ lgf_status lgf_set_trace(lgf_handle h, double* F_hist, double* theta_hist, int32
 lgf_status lgf_fft4(lgf_handle h, double* data, int32_t nfields, int32_t sign, int where);
 
 /* Per-kernel timing of lgf_step.  enable != 0 starts recording CUDA events
- * on the handle's stream around each of the five kernels of every
- * subsequent lgf_step (not inside lgf_fix's graph) and clears the
- * accumulators; enable = 0 stops.  Synchronises. */
+ * on the handle's stream around each kernel of every subsequent lgf_step
+ * (not inside lgf_fix's graph) and clears the accumulators; enable = 0
+ * stops.  Synchronises. */
 lgf_status lgf_set_timing(lgf_handle h, int32_t enable);
 
-/* Mean device time in milliseconds of each kernel of the lgf_step calls
- * since timing was enabled: ms[0] pass A (forward (x,y) DFT), ms[1] pass B
- * ((z,t) DFT, filter, inverse), ms[2] pass C (inverse (x,y) DFT and g),
- * ms[3] link update, ms[4] measurement; nkernels <= 5 entries are written.
- * nsteps (may be NULL) receives the number of steps averaged.  Synchronises. */
+/* Mean device time in milliseconds per step of each stage of the lgf_step
+ * calls since timing was enabled: ms[0] pass A (forward (x,y) DFT), ms[1]
+ * pass B ((z,t) DFT, filter, inverse), ms[2] pass C (inverse (x,y) DFT and
+ * g), ms[3] link update, ms[4] measurement; nkernels <= 5 entries are
+ * written.  With LGF_FFT_1D4 or LGF_FFT_3D1D, ms[0] holds the forward
+ * passes, ms[1] the pass carrying the filter and ms[2] the inverse passes
+ * and g; in a fused FP32 phase (lgf_set_fused_update) ms[3] holds the fused
+ * update + measurement and ms[4] is 0.  nsteps (may be NULL) receives the
+ * number of steps averaged.  Synchronises. */
 lgf_status lgf_get_timing(lgf_handle h, double* ms, int32_t nkernels, int32_t* nsteps);
 /* (ms[5], with nkernels = 6: the learned extras -- undo of a rejected step,
  * its re-measurement and the network inference -- of LGF_LEARNED handles.) */

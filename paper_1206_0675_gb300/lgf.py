@@ -516,7 +516,9 @@ class Lattice:
         lgf_set_timing(self.handle, enable)
 
     def get_timing(self) -> tuple[list[float], int]:
-        """Mean ms per kernel [pass A, pass B, pass C+g, update, measure] and the step count."""
+        """Mean ms per step of [pass A, pass B, pass C+g, update, measure] and the step count
+        (for 1D x 4 / 3D + 1D: forward passes, filter pass, inverse passes + g; a fused FP32
+        update + measurement is reported under update)."""
         return lgf_get_timing(self.handle)
 
     def load_preconditioner(self, weights_bf16) -> None:
