@@ -579,10 +579,11 @@ __global__ void su3_defect_kernel(const double2* __restrict__ aos, int64_t nmat,
     for (int r = 0; r < 3; ++r)
 #pragma unroll
       for (int c = 0; c < 3; ++c) m[r][c] = __ldg(&aos[i * 9 + r * 3 + c]);
+    // U U^dag is Hermitian: its upper triangle holds every distinct entry
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
+      for (int c = r; c < 3; ++c) {
         double2 acc = mkc<double>(0.0, 0.0);
 #pragma unroll
         for (int k = 0; k < 3; ++k) acc = cfmac<double>(m[r][k], m[c][k], acc);
