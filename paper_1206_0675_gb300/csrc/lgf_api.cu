@@ -56,7 +56,9 @@ template <typename R> struct Lane {
 // With the 1D x 4 or 3D + 1D decompositions, category 0 holds the forward
 // passes, 1 the pass with the filter and 2 the inverse passes and g.
 struct TimingRing {
-  static constexpr int kSlots = 64, kMaxK = 12, kCat = 6;
+  // kMaxK: the longest body -- the three learned extras, the eight kernels
+  // of the 1D x 4 transform and g, update and measurement (13)
+  static constexpr int kSlots = 64, kMaxK = 16, kCat = 6;
   cudaEvent_t ev[kSlots][kMaxK + 1] = {};
   int cat[kSlots][kMaxK] = {};
   int nk[kSlots] = {};
@@ -262,6 +264,10 @@ template <typename R> cudaError_t enqueue_measure(lgf_ctx* h, Lane<R>& L, int co
 enum { K_A = 0, K_B, K_C, K_UPD, K_MEAS, K_REVERT, K_RESTORE, K_MLP,
        K_F1X, K_F1Y, K_F1Z, K_T1, K_I1Z, K_I1Y, K_I1X, K_F3, K_I3, K_GD, K_UM };
 
+constexpr int kLongestBody = 3 + 8 + 2;
+static_assert(TimingRing::kMaxK >= kLongestBody, "the timing ring must hold the longest body");
+
+// ks must hold TimingRing::kMaxK entries.
 template <typename R> int body_kernels(const lgf_ctx* h, const Lane<R>& L, int* ks) {
   int n = 0;
   if (h->learned) {
