@@ -331,7 +331,7 @@ def run_lgf(args, rank, world, local_rank):
     b32["measure"] = 0
     ops32 = accounting.fp32_path_fp64_ops_per_site()
     fp32 = {"iters_per_s": args.steps / (ms32 / 1e3), "ms_per_step": ms32 / args.steps,
-            "fft_decomposition": decomp32,
+            "fft_decomposition": decomp32, "autotune": tune32["candidates"][tune32["chosen"]],
             "fused_update_measure": True,
             "per_kernel": {k: {"ms": t, "gbs": b32[k] * V / (t * 1e-3) / 1e9 if t > 0 else None,
                                "fp64_tflops": 2 * ops32[k] * V / (t * 1e-3) / 1e12 if t > 0 else None}
