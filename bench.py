@@ -286,7 +286,7 @@ def run_lgf(args, rank, world, local_rank):
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": ncu_traffic(dom),
                 "note": "FP64 pipe: every FP64 instruction counted as one FMA (2 flops); peak = 152 SMs x 2 "
                         "FP64 inst/clk x 2070 MHz; per-launch time from CUDA events on the launching stream"}
-    b_alg = accounting.survey_b_alg(8, 3)
+    b_alg = accounting.b_alg_per_site(8, 3)
     step_hbm = {"b_alg_bytes_per_site": b_alg, "achieved_gbs": b_alg * V / (ms_step * 1e-3) / 1e9,
                 "peak_gbs": hbm_peak, "peak_kind": peak_kind,
                 "frac": b_alg * V / (ms_step * 1e-3) / 1e9 / hbm_peak,
@@ -336,7 +336,7 @@ def run_lgf(args, rank, world, local_rank):
             "per_kernel": {k: {"ms": t, "gbs": b32[k] * V / (t * 1e-3) / 1e9 if t > 0 else None,
                                "fp64_tflops": 2 * ops32[k] * V / (t * 1e-3) / 1e12 if t > 0 else None}
                            for k, t in zip(accounting.KERNELS, kms32)},
-            "hbm_frac_b_alg": accounting.survey_b_alg(4, 2) * V / (ms32 / args.steps * 1e-3) / 1e9 / hbm_peak}
+            "hbm_frac_b_alg": accounting.b_alg_per_site(4, 2) * V / (ms32 / args.steps * 1e-3) / 1e9 / hbm_peak}
 
     # ---- time to theta < 1e-15: plain FP64 vs mixed -------------------------
     ttt = None

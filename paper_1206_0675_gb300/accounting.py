@@ -120,7 +120,7 @@ def fused_update_measure_bytes(real_bytes: int, rows: int, g_rows: int) -> int:
     return 2 * link + g_rows * 3 * 2 * real_bytes + 4 * 2 * real_bytes
 
 
-def survey_b_alg(real_bytes: int, rows: int) -> int:
+def b_alg_per_site(real_bytes: int, rows: int) -> int:
     """B_alg = 2 (4 S_L) + 2 S_g + 4 S_Delta: links read and written once, g written
     and read once, the divergence swept four times (a fused update+measure schedule)."""
     S_L = rows * 3 * 2 * real_bytes
