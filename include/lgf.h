@@ -64,7 +64,7 @@ typedef enum {
   LGF_E_NONFINITE = 5,    /* non-finite input links, F or theta */
   LGF_E_NOTCONV = 6,      /* lgf_fix reached max_iter with theta >= tol */
   LGF_E_TIMEOUT = 7,      /* a bounded device wait gave up */
-  LGF_E_UNSUPPORTED = 8   /* extents or options this build does not handle */
+  LGF_E_UNSUPPORTED = 8   /* extents or options the library does not handle */
 } lgf_status;
 
 typedef enum {
