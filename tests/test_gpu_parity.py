@@ -144,6 +144,23 @@ def test_one_step_parity_fp64(ext, store12):
     assert rel(th, tho) < 1e-11
 
 
+@pytest.mark.parametrize("ext", [(96, 2, 3, 2), (2, 2, 2, 128), (4, 3, 128, 2), (96, 96, 2, 2)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+def test_extreme_extents_one_step(ext, prec, tol):
+    """The largest accepted extents: 96 along x and y, 128 along z and t.  A
+    96 x 96 (x,y) plane holds one field in shared memory but not four, so
+    that lattice takes the unfused inverse pass and the separate g kernel."""
+    U = fields.random_links(ext, eps=0.8, seed=17)
+    with lgf.Lattice(ext, prec) as lat:
+        lat.set_links(U)
+        lat.step(0.08)
+        g = lat.get_gauge()
+        U1 = lat.get_links()
+    Uo, go = O.fa_step(U, 0.08)
+    assert np.max(np.abs(g - go)) < tol
+    assert np.max(np.abs(U1 - Uo)) < tol
+
+
 def test_one_step_plain_sd_fp64():
     ext = (4, 6, 4, 8)
     U = fields.random_links(ext, eps=0.8, seed=8)
