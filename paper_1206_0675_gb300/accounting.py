@@ -131,11 +131,20 @@ def b_alg_per_site(real_bytes: int, rows: int) -> int:
 
 def table1_counts(rows: int) -> dict[str, tuple[int, int]]:
     """Reals loaded/stored per thread by k2, k5, k6 (the paper's Table 1 convention):
-    k2 reads the 4 links at x and the 4 backward links; k5 reads and writes one matrix;
-    k6 reads 4 links, g(x) and the 4 forward g(x+mu), and writes the 4 links."""
+    k2 reads the 4 links at x and the 4 backward links and stores Delta(x) in the
+    link storage plus the two partial sums (F and theta); k5 reads and writes one
+    matrix; k6 reads 4 links, g(x) and the 4 forward g(x+mu), and writes the 4 links."""
     r = rows * 6
     return {
-        "k2": (8 * r, None),
+        "k2": (8 * r, r + 2),
         "k5": (r, r),
         "k6": (4 * r + 5 * r, 4 * r),
     }
+
+
+def paper_fft_flops_per_site(extents) -> float:
+    """The paper's flop count of one 2D + 2D FFT per site, 5 (log2(nx ny) + log2(nz nt))
+    (Sec. 3.2, before Table 1)."""
+    import math
+    lx, ly, lz, lt = extents
+    return 5.0 * (math.log2(lx * ly) + math.log2(lz * lt))
