@@ -12,7 +12,7 @@ import pytest
 from oracle import lgf_oracle as O
 from paper_1206_0675_gb300 import fields
 
-GOLDEN = sorted(glob.glob(os.path.join(os.path.dirname(__file__), "golden", "*.json")))
+GOLDEN = sorted(glob.glob(os.path.join(os.path.dirname(__file__), "golden", "fa_*.json")))
 
 
 def load(path):

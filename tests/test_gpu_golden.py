@@ -13,7 +13,7 @@ from paper_1206_0675_gb300 import lgf
 
 pytestmark = pytest.mark.gpu
 
-GOLDEN = sorted(glob.glob(os.path.join(os.path.dirname(__file__), "golden", "*.json")))
+GOLDEN = sorted(glob.glob(os.path.join(os.path.dirname(__file__), "golden", "fa_*.json")))
 
 
 @pytest.fixture(scope="module", autouse=True)
