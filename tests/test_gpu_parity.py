@@ -92,6 +92,21 @@ def test_fft4_against_numpy_and_inverse(ext):
     assert np.max(np.abs(back / V - f)) < 1e-13
 
 
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("fp32", 2e-6)])
+def test_fft4_against_cufft_32x4(prec, tol):
+    """Cross-check at the full 32^4 size against cuFFT (through torch.fft on
+    the device): the library's own passes must give the same 4D DFT."""
+    import torch
+    ext = (32, 32, 32, 32)
+    rng = np.random.default_rng(31)
+    f = rng.standard_normal((4, 32, 32, 32, 32)) + 1j * rng.standard_normal((4, 32, 32, 32, 32))
+    with lgf.Lattice(ext, prec) as lat:
+        ours = lat.fft4(f, -1)
+    ref = torch.fft.fftn(torch.from_numpy(f).cuda(), dim=(1, 2, 3, 4)).cpu().numpy()
+    scale = np.max(np.abs(ref))
+    assert np.max(np.abs(ours - ref)) < tol * scale
+
+
 def test_fft4_defining_sum_tiny():
     """Against the defining sum, written out for a 2x3x2x3 lattice."""
     ext = (2, 3, 2, 3)
