@@ -6,7 +6,13 @@ fields of paper_1206_0675_gb300/fields.py; nothing here calls the CUDA path.
 The fixtures guard the oracle against unintended changes and give the GPU
 tests stored expectations that need no oracle run.
 
-    python tests/golden/make_golden.py
+    python tests/golden/make_golden.py              # the small fa_*.json cases
+    python tests/golden/make_golden.py --headline   # the 32^4 cases (minutes per case)
+
+The 32^4 cases are the 32^4 workload of the benchmark: U_mu(x) = h(x)
+exp(i eps sum_a c_a lambda_a/2) h^dag(x+mu) with eps = 1.0, seed 0 (a 50-step
+trajectory) and eps = 0.5, seeds 0-3 (fixed to theta < 1e-15), alpha = 0.08.
+They run as separate processes (multiprocessing, spawn), one per case.
 """
 
 import json
@@ -29,6 +35,17 @@ CASES = [
 ]
 SAMPLE_SITES = [(0, 0, 0, 0), (1, 2, 3, 1), (3, 1, 0, 2)]  # (x, y, z, t), wrapped into the lattice
 
+HEADLINE_EXT = (32, 32, 32, 32)
+HEADLINE_CASES = [
+    # name, eps, seed, tol, max_iter: tol = 0 runs exactly max_iter steps
+    ("headline_32x4_eps1.0_seed0_50steps", 1.0, 0, 0.0, 50),
+    ("headline_32x4_eps0.5_seed0_tol1e-15", 0.5, 0, 1e-15, 3000),
+    ("headline_32x4_eps0.5_seed1_tol1e-15", 0.5, 1, 1e-15, 3000),
+    ("headline_32x4_eps0.5_seed2_tol1e-15", 0.5, 2, 1e-15, 3000),
+    ("headline_32x4_eps0.5_seed3_tol1e-15", 0.5, 3, 1e-15, 3000),
+]
+HEADLINE_SITES = [(0, 0, 0, 0), (5, 17, 30, 11), (31, 31, 31, 31), (16, 2, 9, 27)]
+
 
 def make(name, ext, eps, seed, alpha, n, exact_exp):
     U = fields.random_links(ext, eps, seed)
@@ -48,7 +65,34 @@ def make(name, ext, eps, seed, alpha, n, exact_exp):
     }
 
 
+def make_headline(case):
+    name, eps, seed, tol, max_iter = case
+    U = fields.random_links(HEADLINE_EXT, eps, seed)
+    res = O.fix(U, alpha=0.08, tol=tol, max_iter=max_iter, track_G=True)
+    G = res["G"]
+    samples = [{"site": [x, y, z, t], "G_re": G[t, z, y, x].real.tolist(), "G_im": G[t, z, y, x].imag.tolist()}
+               for (x, y, z, t) in HEADLINE_SITES]
+    out = {
+        "source": "FP64 CPU oracle, Algorithm 1 of arXiv:1206.0675 (oracle/lgf_oracle.py fix); fields from "
+                  "paper_1206_0675_gb300/fields.py random_links",
+        "extents": list(HEADLINE_EXT), "eps": eps, "seed": seed, "alpha": 0.08, "exact_exp": False,
+        "tol": tol, "max_iter": max_iter, "iterations": int(res["iters"]), "converged": bool(res["converged"]),
+        "F": res["F"].tolist(), "theta": res["theta"].tolist(), "plaquette": O.plaquette(U),
+        "G_samples": samples,
+    }
+    path = os.path.join(HERE, name + ".json")
+    with open(path, "w") as f:
+        json.dump(out, f, indent=1)
+    return path
+
+
 def main():
+    if "--headline" in sys.argv[1:]:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(len(HEADLINE_CASES)) as pool:
+            for path in pool.imap_unordered(make_headline, HEADLINE_CASES):
+                print("wrote", path, flush=True)
+        return
     for name, *args in CASES:
         path = os.path.join(HERE, name + ".json")
         with open(path, "w") as f:

@@ -1,0 +1,178 @@
+"""The 32^4 workload of the benchmark against stored FP64 oracle values.
+
+The fixtures tests/golden/headline_32x4_*.json were written by
+tests/golden/make_golden.py from the CPU oracle alone (Sec. 2 and
+Algorithm 1 of arXiv:1206.0675) on the seeded fields of
+paper_1206_0675_gb300.fields:
+
+* eps = 1.0, seed 0: the first 50 steps (F and theta after every step,
+  sampled entries of the accumulated transform G);
+* eps = 0.5, seeds 0-3: the whole fix to theta < 1e-15 (about 50 steps).
+
+Tolerances, all against the oracle:
+
+* FP64, per-iteration F: 1e-11 relative.
+* FP64, per-iteration theta: the larger of 1e-11 and 100 u / sqrt(theta)
+  relative, u = 2^-53.  Each of the eight real components of Delta_A is a
+  signed sum of sixteen entries of unit-norm link rows, so either code
+  carries an absolute error of a few u in it whatever the size of theta;
+  with |Delta_A| of order sqrt(theta) the relative error of
+  theta ~ sum |Delta_A|^2 is of order u / sqrt(theta).  The bound equals
+  1e-11 at theta = 1.2e-6 and allows 3.5e-7 at theta = 1e-15.  The largest
+  deviation seen along each trajectory is printed next to the check.
+* FP32 12-real storage: F and theta within 1e-5 relative over the 50 steps.
+* Iterations to theta < 1e-15 within 2% (at least one step), final F
+  within 1e-10, in FP64 and in the mixed FP32 -> FP64 mode.
+"""
+
+import glob
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_1206_0675_gb300 import fields
+from paper_1206_0675_gb300 import lgf
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+U_ROUND = 2.0 ** -53
+
+
+def load(name):
+    with open(os.path.join(HERE, "golden", name + ".json")) as f:
+        return json.load(f)
+
+
+TRAJ = "headline_32x4_eps1.0_seed0_50steps"
+FIXES = [f"headline_32x4_eps0.5_seed{s}_tol1e-15" for s in range(4)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _library():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    lgf.load_library()
+
+
+_FIELDS = {}
+
+
+def field(g):
+    key = (g["eps"], g["seed"])
+    if key not in _FIELDS:
+        _FIELDS.clear()   # one 32^4 field (604 MB) held at a time
+        _FIELDS[key] = fields.random_links(tuple(g["extents"]), g["eps"], g["seed"])
+    return _FIELDS[key]
+
+
+def theta_tol(theta):
+    return np.maximum(1e-11, 100.0 * U_ROUND / np.sqrt(np.asarray(theta)))
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return np.abs(a - b) / np.abs(b)
+
+
+def check_G(G, g, tol):
+    for s in g["G_samples"]:
+        x, y, z, t = s["site"]
+        want = np.array(s["G_re"]) + 1j * np.array(s["G_im"])
+        assert np.max(np.abs(G[t, z, y, x] - want)) < tol, s["site"]
+
+
+@pytest.mark.parametrize("plan", ["2d2d", "1d4", "autotune"])
+def test_trajectory_50_fp64_32x4(plan):
+    g = load(TRAJ)
+    U = field(g)
+    n = g["iterations"]
+    with lgf.Lattice(tuple(g["extents"]), "fp64", track_G=True) as lat:
+        lat.set_links(U)
+        if plan == "autotune":
+            lat.autotune()        # the bench's plan choice
+            lat.set_links(U)
+        else:
+            lat.set_fft_decomposition(plan)
+        Fh, Th = lat.set_trace(n + 1)
+        it, F, th, conv = lat.fix(0.0, n, g["alpha"])
+        G = lat.get_transform()
+    assert it == n
+    rF, rT = rel(Fh, g["F"]), rel(Th, g["theta"])
+    print(f"max rel dev F {rF.max():.2e}, theta {rT.max():.2e} (theta from {g['theta'][0]:.3e} to "
+          f"{g['theta'][-1]:.3e})")
+    assert np.all(rF < 1e-11), int(np.argmax(rF))
+    assert np.all(rT < theta_tol(g["theta"])), int(np.argmax(rT / theta_tol(g["theta"])))
+    check_G(G, g, 1e-10)
+
+
+def test_trajectory_50_fp32_12real_32x4():
+    """The bench's FP32 configuration: 12-real storage, fused update + measure, autotuned plan."""
+    g = load(TRAJ)
+    U = field(g)
+    n = g["iterations"]
+    with lgf.Lattice(tuple(g["extents"]), "fp32", store12=True, track_G=True) as lat:
+        lat.set_links(U)
+        lat.autotune()
+        lat.set_links(U)
+        Fh, Th = lat.set_trace(n + 1)
+        it, F, th, conv = lat.fix(0.0, n, g["alpha"])
+        G = lat.get_transform()
+    assert it == n
+    rF, rT = rel(Fh, g["F"]), rel(Th, g["theta"])
+    print(f"max rel dev F {rF.max():.2e}, theta {rT.max():.2e}")
+    assert np.all(rF < 1e-5), int(np.argmax(rF))
+    assert np.all(rT < 1e-5), int(np.argmax(rT))
+    check_G(G, g, 1e-4)
+
+
+@pytest.mark.parametrize("name", FIXES)
+def test_iterations_to_1e15_fp64_32x4(name):
+    g = load(name)
+    assert g["converged"]
+    U = field(g)
+    with lgf.Lattice(tuple(g["extents"]), "fp64", track_G=True) as lat:
+        lat.set_links(U)
+        lat.autotune()
+        lat.set_links(U)
+        Fh, Th = lat.set_trace(g["max_iter"] + 1)
+        it, F, th, conv = lat.fix(g["tol"], g["max_iter"], g["alpha"])
+        G = lat.get_transform()
+    ref_it = g["iterations"]
+    assert conv and th < g["tol"]
+    assert abs(it - ref_it) <= max(1, 0.02 * ref_it)
+    assert abs(F - g["F"][-1]) < 1e-10
+    n = min(it, ref_it) + 1
+    rF, rT = rel(Fh[:n], g["F"][:n]), rel(Th[:n], g["theta"][:n])
+    print(f"{it} vs {ref_it} iterations; max rel dev F {rF.max():.2e}, theta {rT.max():.2e} "
+          f"(at theta {g['theta'][int(np.argmax(rT))]:.2e})")
+    assert np.all(rF < 1e-11)
+    assert np.all(rT < theta_tol(g["theta"][:n])), int(np.argmax(rT / theta_tol(g["theta"][:n])))
+    check_G(G, g, 1e-9)
+
+
+@pytest.mark.parametrize("name", FIXES)
+def test_iterations_to_1e15_mixed_32x4(name):
+    """The same fields in the mixed mode (FP32 12-real until theta < 1e-9, then FP64)."""
+    g = load(name)
+    U = field(g)
+    with lgf.Lattice(tuple(g["extents"]), "mixed", store12=True, track_G=True) as lat:
+        lat.set_links(U)
+        lat.autotune()
+        lat.set_links(U)
+        it, F, th, conv = lat.fix(g["tol"], g["max_iter"], g["alpha"])
+        assert lat.phase == 64
+        G = lat.get_transform()
+    ref_it = g["iterations"]
+    print(f"mixed: {it} vs {ref_it} iterations, F {F!r} vs {g['F'][-1]!r}")
+    assert conv and th < g["tol"]
+    assert abs(it - ref_it) <= max(1, 0.02 * ref_it)
+    assert abs(F - g["F"][-1]) < 1e-10
+    check_G(G, g, 1e-9)
+
+
+def test_fixtures_cover_the_workload():
+    names = sorted(os.path.basename(p)[:-5] for p in glob.glob(os.path.join(HERE, "golden", "headline_32x4_*.json")))
+    assert names == sorted([TRAJ] + FIXES)
