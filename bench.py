@@ -53,10 +53,10 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 KERNELS_PER_STEP = {"2d2d": 5, "1d4": 10, "3d1d": 6}
 
 
-# DRAM bytes (read + write) per launch from the committed ncu capture of the
-# FP64 update kernel at 32^4 (profiles/update_kernel_fp64_32x4.md), valid only
+# DRAM bytes (read + write) per launch of the FP64 update kernel at 32^4 from
+# one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum), valid only
 # while the kernel's source text and the shared device header are unchanged
-# (sha256 prefixes).
+# (sha256 prefixes); reported as null otherwise.
 NCU_TRAFFIC = {
     "update": {"bytes": 771.562496e6 + 578.467328e6, "kernel_sha": "c545c54676518b65",
                "common_sha": "4f2fa65c52b10e5d"},
@@ -159,6 +159,80 @@ class ClockSampler:
 # CPU oracle (cpu_baseline leg and --impl reference)
 # ---------------------------------------------------------------------------
 
+def host_cores():
+    """Cores this process may run on (the box's nproc unless an affinity mask is set)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def mem_available_gb():
+    try:
+        with open("/proc/meminfo") as f:
+            for ln in f:
+                if ln.startswith("MemAvailable:"):
+                    return int(ln.split()[1]) / 1e6
+    except OSError:
+        pass
+    return None
+
+
+# Resident memory of one oracle replica at 32^4 (links, divergence, FFTs and
+# temporaries of numpy's whole-array operations), with a margin.
+ORACLE_GB_PER_REPLICA_32X4 = 4.5
+
+
+def _oracle_replica(ext, eps, seed, n, barrier, out):
+    """One oracle replica in its own (spawned, single-threaded) process: build
+    its field, wait for the others, then time n bodies of Algorithm 1."""
+    from oracle import lgf_oracle as O
+    U = fields.random_links(ext, eps, seed)
+    K = O.fa_filter(O.extents_of(U), ALPHA)
+    _, _, D = O.measure(U)
+    barrier.wait()
+    t0 = time.perf_counter()
+    c0 = time.process_time()
+    for _ in range(n):
+        U, _ = O.fa_step(U, ALPHA, K, D)
+        _, _, D = O.measure(U)
+    out.put((seed, time.perf_counter() - t0, time.process_time() - c0))
+
+
+def oracle_all_cores(ext, n, replicas=None):
+    """The oracle as it stands on every host core: one single-threaded replica
+    (its own seeded field, n bodies) per core, all started together after
+    their fields are built.  Returns (iterations/s of all replicas together,
+    replicas, wall seconds, per-replica seconds)."""
+    import multiprocessing as mp
+    P = replicas or host_cores()
+    avail = mem_available_gb()
+    if avail is not None:
+        P = max(1, min(P, int(avail * 0.8 // ORACLE_GB_PER_REPLICA_32X4)))
+    ctx = mp.get_context("spawn")
+    barrier, out = ctx.Barrier(P + 1), ctx.Queue()
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    try:
+        procs = [ctx.Process(target=_oracle_replica, args=(ext, EPS, 100 + i, n, barrier, out)) for i in range(P)]
+        for p in procs:
+            p.start()
+        barrier.wait()
+        t0 = time.perf_counter()
+        res = [out.get() for _ in range(P)]
+        wall = time.perf_counter() - t0
+        for p in procs:
+            p.join()
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return P * n / wall, P, wall, sorted(r[1] for r in res)
+
+
 def oracle_iterations(U, n):
     """n bodies of Algorithm 1 with the CPU oracle; returns (seconds, cores used)."""
     from oracle import lgf_oracle as O
@@ -179,20 +253,19 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     U = fields.random_links(EXT, EPS, 0)
-    # one warm-up body sizes the run so that it ends within a few minutes
+    # one warm-up body on one core sizes the run so that it ends within a few minutes
     t1, _, U = oracle_iterations(U, 1)
-    budget = 150.0
-    W = min(args.warmup, max(0, int(budget * 0.1 / t1)))
+    budget = 120.0
+    W = 1
     K = max(1, min(args.steps, int(budget / t1)))
-    if W:
-        _, _, U = oracle_iterations(U, W)
-    dt, cores, _ = oracle_iterations(U, K)
-    value = K / dt
-    sample = (f"{K} oracle bodies of Algorithm 1 (FFT, filter, IFFT, g, update, measure) on the 32^4 field, "
-              f"after {W + 1} warm-up bodies")
+    value, cores, wall, _ = oracle_all_cores(EXT, K)
+    dt = wall
+    sample = (f"{cores} single-threaded oracle replicas (one per host core, own seeded 32^4 field each), "
+              f"{K} bodies of Algorithm 1 (FFT, filter, IFFT, g, update, measure) each, timed together after "
+              f"one warm-up body on one core")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world,
-        "steps": K, "warmup": W + 1, "ms_per_step": 1e3 * dt / K, "higher_is_better": True, "scaling": "weak",
+        "steps": K, "warmup": W, "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload_desc(), "lattice": list(EXT), "precision": "fp64", "storage": "18-real",
                    "engine": "CPU oracle (numpy FP64)"},
@@ -218,6 +291,12 @@ def max_over_ranks(ms, device):
 def whole_job_rate(steps, world, max_ms):
     """Steps per second of all replicas together: world * steps in the slowest rank's time."""
     return world * steps / (max_ms / 1e3)
+
+
+def time_region(torch, lat, K, reps):
+    """Median over reps timed regions of K steps each (ms), and all of them."""
+    t = [time_steps(torch, lat, K) for _ in range(reps)]
+    return float(np.median(t)), t
 
 
 def time_steps(torch, lat, K):
@@ -256,16 +335,19 @@ def run_lgf(args, rank, world, local_rank):
     for _ in range(args.warmup):
         lat.step(ALPHA)
     torch.cuda.synchronize()
-    lat.set_timing(True)
     sampler = ClockSampler(local_rank)
     sampler.start()
     if dist:
         tdist.barrier()
     torch.cuda.synchronize()
-    ms = time_steps(torch, lat, args.steps)
-    clocks = sampler.stop()
+    # the headline: median of args.reps regions of K steps, no per-kernel events
+    ms, ms_regions = time_region(torch, lat, args.steps, args.reps)
+    # per-kernel split: one more region of K steps with CUDA events around every kernel
+    lat.set_timing(True)
+    ms_split = time_steps(torch, lat, args.steps)
     kms, nsteps = lat.get_timing()
     lat.set_timing(False)
+    clocks = sampler.stop()
     if dist:
         ms = max_over_ranks(ms, "cuda")
     ms_step = ms / args.steps
@@ -321,9 +403,11 @@ def run_lgf(args, rank, world, local_rank):
     decomp32 = tune32["candidates"][tune32["chosen"]]["decomposition"]
     for _ in range(args.warmup):
         lat32.step(ALPHA)
+    ms32, _ = time_region(torch, lat32, args.steps, args.reps)
     lat32.set_timing(True)
-    ms32 = time_steps(torch, lat32, args.steps)
+    time_steps(torch, lat32, args.steps)
     kms32, _ = lat32.get_timing()
+    lat32.set_timing(False)
     lat32.close()
     b32 = accounting.bytes_per_site(4, 2, 2, k_bytes=4, decomposition=decomp32)
     # FP32 lanes fuse the update with the measurement: "update" carries both
@@ -398,10 +482,18 @@ def run_lgf(args, rank, world, local_rank):
     # ---- CPU oracle on the host cores (rank 0, N = 1 only) ------------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        dt, cores, _ = oracle_iterations(U, args.cpu_iters)
-        cpu = {"value": args.cpu_iters / dt, "unit": "iters/s", "cores": cores, "kind": "oracle",
-               "sample": f"{args.cpu_iters} oracle bodies of Algorithm 1 on the same 32^4 field (numpy FP64)",
-               "seconds_per_iter": {"32^4": dt / args.cpu_iters}}
+        # every host core: one single-threaded oracle replica per core
+        v_all, P, wall, per = oracle_all_cores(EXT, args.cpu_iters)
+        # one core, on the bench's own field
+        dt, cores1, _ = oracle_iterations(U, args.cpu_iters)
+        cpu = {"value": v_all, "unit": "iters/s", "cores": P, "kind": "oracle", "nproc": host_cores(),
+               "sample": f"{P} single-threaded replicas of the oracle (numpy FP64), one per host core, each "
+                         f"{args.cpu_iters} bodies of Algorithm 1 on its own seeded 32^4 field (eps={EPS}), "
+                         f"started together; value = {P * args.cpu_iters} bodies / {wall:.1f} s wall",
+               "single_core": {"value": args.cpu_iters / dt, "unit": "iters/s", "cores": cores1,
+                               "sample": f"{args.cpu_iters} oracle bodies on the bench's 32^4 field"},
+               "seconds_per_iter": {"32^4": dt / args.cpu_iters, "32^4_all_cores_per_replica": float(np.median(per))
+                                    / args.cpu_iters}}
         for L, n in ((8, 20), (16, 5)):     # the smaller lattices of the workload, a few seconds each
             dts, _, _ = oracle_iterations(fields.random_links((L,) * 4, EPS, rank), n)
             cpu["seconds_per_iter"][f"{L}^4"] = dts / n
@@ -410,6 +502,11 @@ def run_lgf(args, rank, world, local_rank):
         line = {
             "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "timing": {"regions": args.reps, "steps_per_region": args.steps, "ms_per_region": ms_regions,
+                       "statistic": "median of the regions (no per-kernel events inside them)",
+                       "per_kernel_region_ms": ms_split,
+                       "note": "per-kernel times come from one further region with CUDA events around every "
+                               "kernel"},
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_desc(), "lattice": list(EXT), "precision": "fp64",
                        "storage": "18-real", "alpha": ALPHA, "parallelism": "replicas" if world > 1 else "single",
@@ -417,7 +514,7 @@ def run_lgf(args, rank, world, local_rank):
             "site_updates_per_s": value * V,
             "per_kernel": per_kernel, "roofline": roofline, "step_hbm": step_hbm, "fp32_12": fp32,
             "time_to_tol": ttt, "batch64": batch, "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
-            "gpu_launches": KERNELS_PER_STEP[decomp] * args.steps,
+            "gpu_launches": KERNELS_PER_STEP[decomp] * args.steps * args.reps,
             "autotune": {"fft_decomposition": decomp, "fields_per_cta_xy": chosen["fields_per_cta_xy"],
                          "x_columns_zt": chosen["x_columns_zt"], "threads": chosen["threads"],
                          "lines_x": chosen["lines_x"], "x_columns_line": chosen["x_columns_line"],
@@ -438,7 +535,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="lgf", choices=["lgf", "reference"])
     ap.add_argument("--max-iter", type=int, default=20000)
-    ap.add_argument("--cpu-iters", type=int, default=3)
+    ap.add_argument("--reps", type=int, default=5, help="timed regions of --steps steps (median reported)")
+    ap.add_argument("--cpu-iters", type=int, default=2)
     ap.add_argument("--no-tol", action="store_true", help="skip the time-to-threshold runs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-configuration batch")

@@ -101,7 +101,9 @@ lgf_status lgf_create(const int32_t extents[4], lgf_precision prec, uint32_t fla
 /* Free the handle and its device memory.  NULL is accepted. */
 lgf_status lgf_destroy(lgf_handle h);
 
-/* Copy links in (layout above) and make them the current configuration.
+/* Copy links in (layout above) and make them the current configuration:
+ * the U_mu(x) on which the gauge transformation of Sec. 2, eq. 2,
+ * U_mu(x) -> g(x) U_mu(x) g^dag(x + mu^), acts.
  * Resets G = 1 and the iteration counter, and measures F and theta.
  * Links must be finite (else LGF_E_NONFINITE) and in SU(3):
  * max(|U U^dag - 1|, |det U - 1|) <= 1e-10 (else LGF_E_ARG).
@@ -116,8 +118,11 @@ lgf_status lgf_get_links(lgf_handle h, double* U, int where);
  * inverse FFT, g = reunitarize(1 + Delta'), U -> g U g^dag(x+mu), then the
  * measurement of Delta, F and theta.  Asynchronous (enqueued on the stream),
  * except with LGF_LEARNED, where it synchronises to redo a rejected step
- * with the plain filter.  In LGF_MIXED mode the step runs in the phase the
- * handle is in. */
+ * with the plain filter, and for an LGF_MIXED handle in its FP32 phase,
+ * where it synchronises to read theta: when theta of the current links is
+ * below the switch level (lgf_set_switch_theta) the handle first switches to
+ * FP64 exactly as lgf_fix does, so that every step below that level runs in
+ * FP64. */
 lgf_status lgf_step(lgf_handle h, double alpha);
 
 /* F and theta of the current links (Sec. 2, eq. 3 and the theta formula).
@@ -137,9 +142,11 @@ lgf_status lgf_measure(lgf_handle h, double* F, double* theta);
 lgf_status lgf_fix(lgf_handle h, double theta_tol, int32_t max_iter, double alpha, int32_t* iters, double* F,
                    double* theta);
 
-/* Copy out the accumulated transform G(x) (site layout, FP64), such that the
- * current links equal G(x) U_in(x) G^dag(x+mu) for the links given to
- * lgf_set_links.  LGF_E_STATE unless the handle tracks G.  Synchronises. */
+/* Copy out the accumulated transform G(x) = g_k(x) ... g_1(x) (site layout,
+ * FP64): the product of the gauge transformations of Sec. 2, eq. 2, applied
+ * by the steps since lgf_set_links, so that the current links equal
+ * G(x) U_in(x) G^dag(x+mu) for the links U_in given to lgf_set_links.
+ * LGF_E_STATE unless the handle tracks G.  Synchronises. */
 lgf_status lgf_get_transform(lgf_handle h, double* G, int where);
 
 /* Copy out the gauge transformation g(x) of the last step (site layout,

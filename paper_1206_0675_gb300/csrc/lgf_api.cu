@@ -774,6 +774,13 @@ lgf_status lgf_step(lgf_handle h, double alpha) {
   if (!h->have_links) return fail(h, LGF_E_STATE, "no links set");
   if (!std::isfinite(alpha)) return fail(h, LGF_E_ARG, "alpha must be finite");
   if (h->learned && !h->mlp_w) return fail(h, LGF_E_STATE, "LGF_LEARNED handle without a loaded preconditioner");
+  if (h->prec == LGF_MIXED && h->phase == 32) {
+    // every step from links with theta below the switch level runs in FP64,
+    // as in lgf_fix
+    if ((s = sync_state(h)) != LGF_OK) return s;
+    const double th = h->st_host->theta;
+    if (std::isfinite(th) && th < h->switch_theta && (s = switch_to_fp64(h)) != LGF_OK) return s;
+  }
   s = h->phase == 64 ? step_lane<double>(h, h->d, alpha) : step_lane<float>(h, h->f, alpha);
   if (s != LGF_OK) return s;
   h->have_g = true;

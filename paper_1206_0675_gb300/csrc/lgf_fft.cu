@@ -456,30 +456,47 @@ __global__ void __launch_bounds__(512) fft_xyz_kernel(Geom g, FFTDir dx, FFTDir 
 // Gram-Schmidt on rows 1-2, row 3 = (a x b)^* as in Sec. 3.2)
 // ---------------------------------------------------------------------------
 
+// 1/sqrt(x) in FP64 for finite x > 0: the hardware estimate of PTX
+// rsqrt.approx.ftz.f64 refined by one third-order Householder step for
+// f(y) = y^-2 - x.  With e = 1 - x y0^2 the exact value is
+// y0 (1 - e)^(-1/2) = y0 (1 + e/2 + 3e^2/8 + 5e^3/16 + ...); keeping the
+// terms to e^2 leaves a relative error of (5/16) e^3, below 2^-60 for an
+// estimate within 2^-20, so the result is within rounding of 1/sqrt(x).
+// Five FP64 operations after the estimate.
+__device__ __forceinline__ double rsqrt_fp64(double x) {
+  double y;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  const double e = fma(-(x * y), y, 1.0);
+  return fma(y * e, fma(0.375, e, 0.5), y);
+}
+
 // f0 = (Im D11, Im D22), f1 = D12, f2 = D13, f3 = D23 of the filtered field.
+// Rows of 1 + X: r1 = (1 + i a, f1, f2) and r2 = (-conj f1, 1 + i d, f3)
+// with a = Re f0, d = Im f0.  Gram-Schmidt: u = r1 / |r1| and
+// v = w / |w| with w = r2 - <u, r2> u = r2 - (c / |r1|^2) r1, where
+// c = <r1, r2> = sum_j conj(r1_j) r2_j = (a + d)(Im f1 + i Re f1) + conj(f2) f3
+// (the two terms in f1 combine).  All of it in FP64.
 __device__ __forceinline__ void gauge_from_packed(double2 f0, double2 f1, double2 f2, double2 f3, double2 u[3],
                                                   double2 v[3]) {
-  // row 1 of 1 + X: (1 + i a, b, c)
   const double a = f0.x, d = f0.y;
   const double n1 = fma(f2.x, f2.x, fma(f2.y, f2.y, fma(f1.x, f1.x, fma(f1.y, f1.y, fma(a, a, 1.0)))));
-  const double i1 = rsqrt(n1);
+  const double i1 = rsqrt_fp64(n1);
+  const double s = a + d;
+  const double q = i1 * i1;  // 1 / |r1|^2
+  const double kx = q * fma(f2.x, f3.x, fma(f2.y, f3.y, s * f1.y));
+  const double ky = q * fma(f2.x, f3.y, fma(-f2.y, f3.x, s * f1.x));
+  // w = r2 - k r1
+  const double2 w0 = make_double2(fma(ky, a, -f1.x - kx), fma(-kx, a, f1.y - ky));
+  const double2 w1 = make_double2(fma(ky, f1.y, fma(-kx, f1.x, 1.0)), fma(-ky, f1.x, fma(-kx, f1.y, d)));
+  const double2 w2 = make_double2(fma(ky, f2.y, fma(-kx, f2.x, f3.x)), fma(-ky, f2.x, fma(-kx, f2.y, f3.y)));
+  const double n2 = fma(w2.x, w2.x, fma(w2.y, w2.y, fma(w1.x, w1.x, fma(w1.y, w1.y, fma(w0.x, w0.x, w0.y * w0.y)))));
+  const double i2 = rsqrt_fp64(n2);
   u[0] = make_double2(i1, a * i1);
   u[1] = make_double2(f1.x * i1, f1.y * i1);
   u[2] = make_double2(f2.x * i1, f2.y * i1);
-  // row 2 of 1 + X: (-conj(b), 1 + i d, e)
-  const double2 r0 = make_double2(-f1.x, f1.y), r1 = make_double2(1.0, d), r2 = f3;
-  double2 ip = cconjmul<double>(u[0], r0);
-  ip = cadd<double>(ip, cconjmul<double>(u[1], r1));
-  ip = cadd<double>(ip, cconjmul<double>(u[2], r2));
-  const double2 nip = make_double2(-ip.x, -ip.y);
-  v[0] = cfma<double>(nip, u[0], r0);
-  v[1] = cfma<double>(nip, u[1], r1);
-  v[2] = cfma<double>(nip, u[2], r2);
-  const double n2 = cnorm2<double>(v[0]) + cnorm2<double>(v[1]) + cnorm2<double>(v[2]);
-  const double i2 = rsqrt(n2);
-  v[0] = cscale<double>(v[0], i2);
-  v[1] = cscale<double>(v[1], i2);
-  v[2] = cscale<double>(v[2], i2);
+  v[0] = cscale<double>(w0, i2);
+  v[1] = cscale<double>(w1, i2);
+  v[2] = cscale<double>(w2, i2);
 }
 
 // Rows 1 and 2 of g = exp(X) (the exponential of Eq. (eq:gx) evaluated

@@ -21,29 +21,6 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-template <typename R> __device__ __forceinline__ R warp_sum_r(R v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Block sum of per-thread values given as warp sums already formed in
-// precision R (lane 0 of each warp holds its warp's sum); the sum over warps
-// is in FP64 and fixed order.  Result valid in thread 0.
-template <typename R> __device__ __forceinline__ void block_sum2_warps(R wa, R wb, double& a, double& b) {
-  __shared__ double sa[32], sb[32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-  if (lane == 0) { sa[warp] = (double)wa; sb[warp] = (double)wb; }
-  __syncthreads();
-  if (warp == 0) {
-    a = lane < nw ? sa[lane] : 0.0;
-    b = lane < nw ? sb[lane] : 0.0;
-    a = warp_sum(a);
-    b = warp_sum(b);
-  }
-  __syncthreads();
-}
-
 // Block sum of two values in a fixed order; result valid in thread 0.
 __device__ __forceinline__ void block_sum2(double& a, double& b) {
   __shared__ double sa[32], sb[32];
@@ -65,12 +42,13 @@ __device__ __forceinline__ void block_sum2(double& a, double& b) {
 // finish, the controller update: F and theta, the iteration count, the
 // history, the status word, the batch retirement flag or the graph's WHILE
 // condition; flip_ubuf != 0 also flips st->ubuf (after every CTA has read it).
-template <typename R>
-__device__ __forceinline__ void measure_tail(const Geom& g, R fsum, R tsum, double* __restrict__ partials,
+// fsum and tsum are one site's sums, already in FP64; every sum above a
+// site (warp, CTA, grid) is FP64 in a fixed order.
+__device__ __forceinline__ void measure_tail(const Geom& g, double fsum, double tsum, double* __restrict__ partials,
                                              DevState* __restrict__ st, int count_iter, unsigned long long cond,
                                              int use_cond, bool batch, int flip_ubuf) {
-  double fb, tb;
-  block_sum2_warps<R>(warp_sum_r<R>(fsum), warp_sum_r<R>(tsum), fb, tb);
+  double fb = fsum, tb = tsum;
+  block_sum2(fb, tb);
   __shared__ int is_last;
   if (threadIdx.x == 0) {
     partials[2 * blockIdx.x] = fb;
@@ -162,9 +140,9 @@ measure_kernel(Geom g, MatField<R, ROWS> U, const C2<R>* __restrict__ links_alt,
   if (only_if_revert && !st->revert) return;
   if (links_alt != nullptr && st->ubuf) U.p = const_cast<C2<R>*>(links_alt);  // ping-pong links of a fused lane
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  // per-site sums in the link precision; warp sums likewise, everything
-  // beyond a warp in FP64
-  R fsum = 0, tsum = 0;
+  // Re Tr of one link in the link precision; every sum above one link (the
+  // site's F and theta terms, warp, CTA and grid sums) in FP64
+  double fsum = 0, tsum = 0;
   if (s < g.V) {
     int c[4];
     site_coords(g, s, c);
@@ -176,7 +154,7 @@ measure_kernel(Geom g, MatField<R, ROWS> U, const C2<R>* __restrict__ links_alt,
     for (int mu = 0; mu < 4; ++mu) {
       M3<R> u;
       U.load_ro(mu, s, u);
-      fsum += u.e[0][0].x + u.e[1][1].x + u.e[2][2].x;
+      fsum += (double)(u.e[0][0].x + u.e[1][1].x + u.e[2][2].x);
       im0 -= u.e[0][0].y; im1 -= u.e[1][1].y; im2 -= u.e[2][2].y;
       w01 = csub<R>(w01, csub<R>(u.e[0][1], cconj<R>(u.e[1][0])));
       w02 = csub<R>(w02, csub<R>(u.e[0][2], cconj<R>(u.e[2][0])));
@@ -196,9 +174,9 @@ measure_kernel(Geom g, MatField<R, ROWS> U, const C2<R>* __restrict__ links_alt,
     delta[2 * g.V + s] = d02;
     delta[3 * g.V + s] = d12;
     // ||Delta_A||_F^2
-    tsum = delta_norm2<R>(a0, a1, a2, d01, d02, d12);
+    tsum = (double)delta_norm2<R>(a0, a1, a2, d01, d02, d12);
   }
-  measure_tail<R>(g, fsum, tsum, partials, st, count_iter, cond, use_cond, batch, 0);
+  measure_tail(g, fsum, tsum, partials, st, count_iter, cond, use_cond, batch, 0);
 }
 
 template <typename R, int ROWS>
@@ -265,7 +243,7 @@ update_measure_kernel(Geom g, C2<R>* __restrict__ U0, C2<R>* __restrict__ U1, Ma
   const int cur = st->ubuf;
   const MatField<R, LROWS> Us{cur ? U1 : U0, g.V}, Ud{cur ? U0 : U1, g.V};
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  R fsum = 0, tsum = 0;
+  double fsum = 0, tsum = 0;  // as in measure_kernel: FP64 above one link
   if (s < g.V) {
     int c[4];
     site_coords(g, s, c);
@@ -280,7 +258,7 @@ update_measure_kernel(Geom g, C2<R>* __restrict__ U0, C2<R>* __restrict__ U1, Ma
       Gf.load_ro(0, site_fwd(g, s, c, mu), h);
       gauge_product<R>(gx, u, h, o);
       Ud.store(mu, s, o);
-      fsum += o.e[0][0].x + o.e[1][1].x + o.e[2][2].x;
+      fsum += (double)(o.e[0][0].x + o.e[1][1].x + o.e[2][2].x);
       add_antiherm<R>(o, (R)-1, im0, im1, im2, w01, w02, w12);
       const int64_t sb = site_back(g, s, c, mu);
       M3<R> b, gb, ob;
@@ -296,9 +274,9 @@ update_measure_kernel(Geom g, C2<R>* __restrict__ U0, C2<R>* __restrict__ U1, Ma
     delta[g.V + s] = d01;
     delta[2 * g.V + s] = d02;
     delta[3 * g.V + s] = d12;
-    tsum = delta_norm2<R>(a0, a1, a2, d01, d02, d12);
+    tsum = (double)delta_norm2<R>(a0, a1, a2, d01, d02, d12);
   }
-  measure_tail<R>(g, fsum, tsum, partials, st, 1, cond, use_cond, false, 1);
+  measure_tail(g, fsum, tsum, partials, st, 1, cond, use_cond, false, 1);
 }
 
 template <typename R, int LROWS, int GROWS>

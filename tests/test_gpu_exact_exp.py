@@ -139,5 +139,5 @@ def test_fp32_step_and_mixed_to_1e15():
         G = lat.get_transform()
     assert conv and th < 1e-15
     assert abs(F - ref["F"][-1]) < 1e-10
-    assert abs(it - ref["iters"]) <= max(2, 0.05 * ref["iters"])
+    assert abs(it - ref["iters"]) <= max(1, 0.02 * ref["iters"])
     assert np.max(np.abs(O.apply_gauge(U, G) - U1)) < 1e-11

@@ -86,7 +86,7 @@ def test_fused_fix_against_oracle_and_mixed():
         it, F, th, conv = lat.fix(1e-15, 6000, 0.08)
         U1 = lat.get_links()
     assert conv and abs(F - ref2["F"][-1]) < 1e-10
-    assert abs(it - ref2["iters"]) <= max(2, 0.05 * ref2["iters"])
+    assert abs(it - ref2["iters"]) <= max(1, 0.02 * ref2["iters"])
     assert abs(O.plaquette(U1) - O.plaquette(U)) < 1e-12
 
 

@@ -157,6 +157,8 @@ def test_one_step_parity_fp64(ext, store12):
     assert np.max(np.abs(U1 - Uo)) < 1e-12
     assert rel(F, Fo) < 1e-13
     assert rel(th, tho) < 1e-11
+    # the FP64 reunitarisation leaves g unitary to rounding
+    assert O.unitarity_defect(g) < 4e-15
 
 
 @pytest.mark.parametrize("ext", [(96, 2, 3, 2), (2, 2, 2, 128), (4, 3, 128, 2), (96, 96, 2, 2)])
@@ -278,13 +280,39 @@ def test_mixed_reaches_1e15_and_keeps_gauge_invariants(store12, switch):
         G = lat.get_transform()
     assert conv and th < 1e-15
     assert abs(F - ref["F"][-1]) < 1e-10
-    assert abs(it - ref["iters"]) <= max(2, 0.05 * ref["iters"])
+    assert abs(it - ref["iters"]) <= max(1, 0.02 * ref["iters"])
     assert abs(O.plaquette(U1) - O.plaquette(U)) < 1e-12
     assert np.max(np.abs(O.polyakov_loops(U1) - O.polyakov_loops(U))) < 1e-12
     assert np.max(np.abs(O.apply_gauge(U, G) - U1)) < 1e-11
     assert O.unitarity_defect(U1) < 5e-13
     Fo, tho, _ = O.measure(U1)
     assert rel(F, Fo) < 1e-13 and tho < 1e-15
+
+
+def test_mixed_steps_switch_like_fix():
+    """lgf_step on a mixed handle: a step taken from links whose theta is below
+    the switch level runs in FP64, so stepping by hand gives the same result,
+    bit for bit, as lgf_fix over the same number of updates."""
+    ext = (8, 8, 8, 8)
+    U = fields.random_links(ext, eps=0.5, seed=0)
+    n, switched_at = 0, None
+    with lgf.Lattice(ext, "mixed", store12=True) as lat:
+        lat.set_links(U)
+        while n < 80:
+            F, th = lat.measure()
+            if th < 1e-13:
+                break
+            lat.step(0.08)
+            n += 1
+            assert lat.phase == (64 if th < 1e-9 else 32), (n, th)
+            if lat.phase == 64 and switched_at is None:
+                switched_at = n
+        Fs, ths = lat.measure()
+    assert switched_at is not None and switched_at < n
+    with lgf.Lattice(ext, "mixed", store12=True) as lat:
+        lat.set_links(U)
+        it, F, th, conv = lat.fix(0.0, n, 0.08)
+    assert it == n and F == Fs and th == ths
 
 
 # ---------------------------------------------------------------------------
@@ -375,7 +403,7 @@ def test_full_size_32x4_one_step(prec, store12, tol):
     assert rel(F0, Fo0) < (1e-13 if prec == "fp64" else 1e-6)
     assert rel(th0, tho0) < (1e-12 if prec == "fp64" else 1e-5)
     assert rel(F1, Fo1) < (1e-12 if prec == "fp64" else 1e-5)
-    assert rel(th1, tho1) < (1e-11 if prec == "fp64" else 1e-4)
+    assert rel(th1, tho1) < (1e-11 if prec == "fp64" else 1e-5)
     # sampled sites: every link of 64 random sites
     rng = np.random.default_rng(0)
     idx = tuple(rng.integers(0, 32, size=(4, 64)))
@@ -410,5 +438,5 @@ def test_anisotropic_48x3_96_one_step(aniso_case, prec, store12):
     assert abs(F0 - Fo0) < (1e-13 if f64 else 1e-6) * abs(Fo0)
     assert rel(th0, tho0) < (1e-12 if f64 else 1e-5)
     assert abs(F1 - Fo1) < (1e-13 if f64 else 1e-6) * abs(Fo1)
-    assert rel(th1, tho1) < (1e-11 if f64 else 1e-4)
+    assert rel(th1, tho1) < (1e-11 if f64 else 1e-5)
     assert np.max(np.abs(U1[:, idx[0], idx[1], idx[2], idx[3]] - Uo_s)) < (1e-12 if f64 else 2e-5)
