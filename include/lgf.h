@@ -22,7 +22,9 @@
  * Ownership: the caller owns every buffer it passes; the library copies in
  *   and out and never keeps a caller pointer beyond the call, except the
  *   history buffers registered with lgf_set_trace.  The library owns its
- *   device workspace (allocated in lgf_create, freed in lgf_destroy).
+ *   device workspace (allocated in lgf_create, freed in lgf_destroy), taken
+ *   from CUDA's stream-ordered allocator or from a caller-supplied allocator
+ *   (lgf_create_with_allocator).
  * Streams: all device work of a handle runs on the stream given to
  *   lgf_create (NULL = the legacy default stream).  lgf_step is asynchronous;
  *   every call that returns numbers to the host synchronises that stream.
@@ -94,9 +96,34 @@ enum { LGF_HOST = 0, LGF_DEVICE = 1 };
  *   LGF_PLAIN_SD, LGF_LEARNED, LGF_EXACT_EXP (LGF_MIXED always tracks G);
  *   any other bit gives LGF_E_ARG.
  * cuda_stream: a cudaStream_t or NULL.  out: receives the handle.
- * Allocates all device workspace up front (LGF_E_NOMEM if it does not fit). */
+ * Allocates all device workspace up front, stream-ordered on cuda_stream
+ * (cudaMallocAsync; LGF_E_NOMEM if it does not fit), and synchronises that
+ * stream before returning. */
 lgf_status lgf_create(const int32_t extents[4], lgf_precision prec, uint32_t flags, void* cuda_stream,
                       lgf_handle* out);
+
+/* Device memory supplied by the caller (for example from the caching
+ * allocator of the framework the library runs under).  alloc returns `bytes`
+ * bytes of device memory on the handle's device, at least 256-byte aligned,
+ * usable by work enqueued on cuda_stream, or NULL on failure; free returns a
+ * buffer that alloc gave, with the same size and stream.  Both are called
+ * only from the thread that calls the library, with ctx passed through. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* cuda_stream, void* ctx);
+  void (*free)(void* ptr, size_t bytes, void* cuda_stream, void* ctx);
+  void* ctx;
+} lgf_allocator;
+
+/* lgf_create with every device buffer of the handle taken from the caller's
+ * allocator instead of CUDA's stream-ordered allocator (which lgf_create
+ * uses: cudaMallocAsync / cudaFreeAsync on the handle's stream).  The
+ * buffers are requested in this call and in lgf_set_trace,
+ * lgf_load_preconditioner and lgf_set_mode_log, and all returned by
+ * lgf_destroy.  allocator may be NULL (same as lgf_create); a non-NULL
+ * allocator needs both functions (else LGF_E_ARG).  LGF_E_NOMEM when alloc
+ * returns NULL, LGF_E_ARG when it returns memory not 256-byte aligned. */
+lgf_status lgf_create_with_allocator(const int32_t extents[4], lgf_precision prec, uint32_t flags,
+                                     void* cuda_stream, const lgf_allocator* allocator, lgf_handle* out);
 
 /* Free the handle and its device memory.  NULL is accepted. */
 lgf_status lgf_destroy(lgf_handle h);
@@ -163,6 +190,46 @@ lgf_status lgf_get_divergence(lgf_handle h, double* D, int where);
  * entry k = after update k), up to cap entries.  cap = 0 unregisters.
  * The arrays must stay valid until lgf_fix returns. */
 lgf_status lgf_set_trace(lgf_handle h, double* F_hist, double* theta_hist, int32_t cap);
+
+/* Trace flags, one int32 per measurement (lgf_set_trace_ex).  Entry k > 0
+ * describes update k and the measurement after it; entry 0 the measurement
+ * before the first update (LGF_TRACE_FP64 only). */
+enum {
+  LGF_TRACE_FP64 = 1,      /* the update and the measurement ran in FP64 (else FP32) */
+  LGF_TRACE_LEARNED = 2,   /* the update's filter was multiplied by the learned table */
+  LGF_TRACE_REDO = 4,      /* the update redid a rejected learned step with the plain filter */
+  LGF_TRACE_REPAIRED = 8   /* the links were reunitarised before the update (lgf_set_defect_bound) */
+};
+
+/* lgf_set_trace with two more per-measurement arrays (either may be NULL):
+ * flags_hist receives the LGF_TRACE_* bits, defect_hist the sampled link
+ * unitarity defect of the measured links (see lgf_set_defect_bound). */
+lgf_status lgf_set_trace_ex(lgf_handle h, double* F_hist, double* theta_hist, int32_t* flags_hist,
+                            double* defect_hist, int32_t cap);
+
+/* Guard against loss of unitarity (an addition; no step of the paper's
+ * Algorithm 1 reunitarises the links, so rounding drift accumulates, and far
+ * from the fixed point -- e.g. with alpha above its convergent range -- the
+ * rebuild of row 3 from rows 1-2 compounds it until F overflows).  Every
+ * measurement also forms, over one link in sixteen (every fourth warp of
+ * sites, one direction each, all four directions covered), the largest of
+ * | |a|^2 - 1 |, | |b|^2 - 1 | and |<a, b>| over the stored rows a, b, in the
+ * link precision.  When it exceeds the bound of the running phase, lgf_fix
+ * stops the device loop, reunitarises every link by Gram-Schmidt (rows 1-2,
+ * row 3 = (a x b)^*), re-measures and continues; the step after a repair is
+ * flagged LGF_TRACE_REPAIRED.  A repair is not a gauge transformation: it
+ * moves the links by about the defect, so G then reproduces them only to
+ * that level.  Defaults: 1e-10 for FP64 phases (the input tolerance of
+ * lgf_set_links, so valid inputs never trigger it) and 1e-4 for FP32
+ * phases; 0 disables the check.  LGF_E_ARG for negative bounds.  lgf_fix
+ * returns LGF_E_NONFINITE if the bound is passed again within one step of a
+ * repair. */
+lgf_status lgf_set_defect_bound(lgf_handle h, double bound_fp64, double bound_fp32);
+
+/* The sampled link defect of the last measurement, and the number of
+ * reunitarisations in the last lgf_fix (either pointer may be NULL).
+ * Synchronises. */
+lgf_status lgf_get_link_defect(lgf_handle h, double* defect, int32_t* repairs);
 
 /* The library's own 4D DFT of nfields = 4 complex fields in place, in the
  * handle's precision: data[f][t][z][y][x][re, im] (FP64 on the user side).

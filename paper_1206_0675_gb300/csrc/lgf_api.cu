@@ -15,6 +15,7 @@
 
 #include "../../include/lgf.h"
 #include "lgf_internal.h"
+#include "lgf_mem.h"
 #include "lgf_mlp.h"
 
 using namespace lgf;
@@ -94,6 +95,7 @@ struct lgf_ctx {
   bool have_links = false;
   bool have_g = false;
   int phase = 64;  // arithmetic of the current configuration
+  DeviceMemory mem;               // every device buffer of the handle
   Lane<double> d;
   Lane<float> f;
   double* U0 = nullptr;           // FP64 AoS copy of the input (LGF_MIXED)
@@ -108,9 +110,16 @@ struct lgf_ctx {
   double p2max = 0;
   double* hist_F = nullptr;
   double* hist_T = nullptr;
+  int* hist_flags = nullptr;
+  double* hist_defect = nullptr;
   int hist_cap = 0;
   double* user_F = nullptr;
   double* user_T = nullptr;
+  int32_t* user_flags = nullptr;
+  double* user_defect = nullptr;
+  double defect_bound64 = 1e-10;  // link unitarity defect that makes lgf_fix reunitarise (FP64 phases)
+  double defect_bound32 = 1e-4;   // the same for FP32 phases
+  int repairs = 0;                // reunitarisations of the links during the last lgf_fix
   TimingRing timing;
   double switch_theta = 1e-9;     // FP32 -> FP64 switch level of LGF_MIXED
   bool learned = false;           // LGF_LEARNED
@@ -149,7 +158,6 @@ bool extent_ok(int L) {
   return L == 1;
 }
 
-template <typename T> cudaError_t dalloc(T** p, size_t n) { return cudaMalloc((void**)p, n * sizeof(T)); }
 
 template <typename R> void drop_graph(Lane<R>& L) {
   if (L.exec) cudaGraphExecDestroy(L.exec);
@@ -165,10 +173,11 @@ template <typename R> void set_decomp(Lane<R>& L, int decomposition) {
   L.decomp = decomposition;
 }
 
-template <typename R> void free_lane(Lane<R>& L) {
+template <typename R> void free_lane(lgf_ctx* h, Lane<R>& L) {
   drop_graph(L);
-  cudaFree(L.U); cudaFree(L.U2); cudaFree(L.g); cudaFree(L.D); cudaFree(L.K); cudaFree(L.tw); cudaFree(L.pos); cudaFree(L.G);
-  cudaFree(L.mtab); cudaFree(L.p2f); cudaFree(L.Dlog); cudaFree(L.Dprev);
+  for (void* p : {(void*)L.U, (void*)L.U2, (void*)L.g, (void*)L.D, (void*)L.K, (void*)L.tw, (void*)L.pos,
+                  (void*)L.G, (void*)L.mtab, (void*)L.p2f, (void*)L.Dlog, (void*)L.Dprev})
+    h->mem.put(p);
   L = Lane<R>();
 }
 
@@ -176,20 +185,20 @@ template <typename R> lgf_status alloc_lane(lgf_ctx* h, Lane<R>& L, int rows, in
   const int64_t V = h->geom.V;
   L.rows = rows;
   L.grows = grows;
-  LGF_CK(h, dalloc(&L.U, (size_t)4 * rows * 3 * V));
+  LGF_CK(h, h->mem.get(&L.U, (size_t)4 * rows * 3 * V));
   // FP32 lanes stream HBM in the update and the measurement: fuse them
   // (not with the learned multiplier, whose undo of a rejected step
   // transforms the links in place)
   if (sizeof(R) == sizeof(float) && !h->learned) {
-    LGF_CK(h, dalloc(&L.U2, (size_t)4 * rows * 3 * V));
+    LGF_CK(h, h->mem.get(&L.U2, (size_t)4 * rows * 3 * V));
     L.fused = true;
   }
-  LGF_CK(h, dalloc(&L.g, (size_t)grows * 3 * V));
-  LGF_CK(h, dalloc(&L.D, (size_t)4 * V));
-  LGF_CK(h, dalloc(&L.K, (size_t)V));
+  LGF_CK(h, h->mem.get(&L.g, (size_t)grows * 3 * V));
+  LGF_CK(h, h->mem.get(&L.D, (size_t)4 * V));
+  LGF_CK(h, h->mem.get(&L.K, (size_t)V));
   const int nt = h->geom.L[0] + h->geom.L[1] + h->geom.L[2] + h->geom.L[3];
-  LGF_CK(h, dalloc(&L.tw, (size_t)nt));
-  if (withG) LGF_CK(h, dalloc(&L.G, (size_t)9 * V));
+  LGF_CK(h, h->mem.get(&L.tw, (size_t)nt));
+  if (withG) LGF_CK(h, h->mem.get(&L.G, (size_t)9 * V));
   if (configure_fft_plan(h->geom.L, (int)sizeof(R), &L.plan) != cudaSuccess)
     return fail(h, LGF_E_UNSUPPORTED, "lattice planes do not fit the shared-memory FFT passes");
   // twiddles W_N^m = exp(-2 pi i m/N), computed in FP64 on the host
@@ -203,11 +212,11 @@ template <typename R> lgf_status alloc_lane(lgf_ctx* h, Lane<R>& L, int rows, in
     }
     off += N;
   }
-  LGF_CK(h, cudaMemcpy(L.tw, tw.data(), nt * sizeof(C2<R>), cudaMemcpyHostToDevice));
+  LGF_CK(h, cudaMemcpyAsync(L.tw, tw.data(), nt * sizeof(C2<R>), cudaMemcpyHostToDevice, h->stream));
   std::vector<short> pos(nt);
   fft_positions(L.plan, pos.data());
-  LGF_CK(h, dalloc(&L.pos, (size_t)nt));
-  LGF_CK(h, cudaMemcpy(L.pos, pos.data(), nt * sizeof(short), cudaMemcpyHostToDevice));
+  LGF_CK(h, h->mem.get(&L.pos, (size_t)nt));
+  LGF_CK(h, cudaMemcpyAsync(L.pos, pos.data(), nt * sizeof(short), cudaMemcpyHostToDevice, h->stream));
   // momentum classes and their per-direction p2 = 4 sin^2(pi f / L), f <= L/2
   std::vector<float> p2;
   L.mg.nclass = 1;
@@ -223,9 +232,9 @@ template <typename R> lgf_status alloc_lane(lgf_ctx* h, Lane<R>& L, int rows, in
   }
   L.mg.m_lo = 0.25f;
   L.mg.m_hi = 1.25f;
-  LGF_CK(h, dalloc(&L.p2f, p2.size()));
-  LGF_CK(h, cudaMemcpy(L.p2f, p2.data(), p2.size() * sizeof(float), cudaMemcpyHostToDevice));
-  if (h->learned) LGF_CK(h, dalloc(&L.mtab, (size_t)L.mg.nclass));
+  LGF_CK(h, h->mem.get(&L.p2f, p2.size()));
+  LGF_CK(h, cudaMemcpyAsync(L.p2f, p2.data(), p2.size() * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+  if (h->learned) LGF_CK(h, h->mem.get(&L.mtab, (size_t)L.mg.nclass));
   L.active = true;
   return LGF_OK;
 }
@@ -495,17 +504,43 @@ lgf_status copy_out(lgf_ctx* h, const double* dev_src, double* dst, size_t n_dou
   return LGF_OK;
 }
 
+// Gram-Schmidt reunitarisation of the lane's current links after a measured
+// unitarity defect passed the bound, then a fresh measurement of them.
+template <typename R> lgf_status repair_links(lgf_ctx* h, Lane<R>& L) {
+  C2<R>* cur = (L.fused && h->st_host->ubuf) ? L.U2 : L.U;
+  if (L.rows == 3) LGF_CK(h, (launch_reunitarize_links<R, 3>(h->geom, cur, h->st, h->stream)));
+  else LGF_CK(h, (launch_reunitarize_links<R, 2>(h->geom, cur, h->st, h->stream)));
+  LGF_CK(h, enqueue_measure<R>(h, L, 0, 0, 0, h->stream));
+  h->repairs += 1;
+  return sync_state(h);
+}
+
 template <typename R> lgf_status run_loop(lgf_ctx* h, Lane<R>& L, double tol, int max_iter, int reset) {
-  LGF_CK(h, launch_set_state(h->st, tol, max_iter, reset, h->hist_cap, h->hist_F, h->hist_T, h->stream));
+  const bool f64 = sizeof(R) == sizeof(double);
+  LGF_CK(h, launch_set_state(h->st, tol, max_iter, reset, h->hist_cap, h->hist_F, h->hist_T, h->stream,
+                             h->hist_flags, h->hist_defect, f64 ? h->defect_bound64 : h->defect_bound32,
+                             f64 ? TRACE_FP64 : 0));
   lgf_status s = sync_state(h);
   if (s != LGF_OK) return s;
-  const DevState& S = *h->st_host;
-  if (!(std::isfinite(S.F) && std::isfinite(S.theta))) return LGF_OK;
-  if (S.theta < tol || S.iter >= max_iter) return LGF_OK;
-  s = ensure_graph<R>(h, L);
-  if (s != LGF_OK) return s;
-  LGF_CK(h, cudaGraphLaunch(L.exec, h->stream));
-  return sync_state(h);
+  int last_repair_iter = -1;
+  for (;;) {
+    const DevState& S = *h->st_host;
+    if (S.status == ST_DEFECT) {
+      // the links drifted from SU(3) (rounding compounded over many steps far
+      // from the fixed point): reunitarise them and carry on
+      if (S.iter == last_repair_iter)
+        return fail(h, LGF_E_NONFINITE, "link unitarity is lost within one step of a reunitarisation");
+      last_repair_iter = S.iter;
+      if ((s = repair_links<R>(h, L)) != LGF_OK) return s;
+      continue;
+    }
+    if (!(std::isfinite(S.F) && std::isfinite(S.theta))) return LGF_OK;
+    if (S.theta < tol || S.iter >= max_iter) return LGF_OK;
+    s = ensure_graph<R>(h, L);
+    if (s != LGF_OK) return s;
+    LGF_CK(h, cudaGraphLaunch(L.exec, h->stream));
+    if ((s = sync_state(h)) != LGF_OK) return s;
+  }
 }
 
 // Mode log of one step: D^ of the divergence just measured, compared with the
@@ -596,25 +631,30 @@ lgf_status lgf_destroy(lgf_handle h) {
   if (!h) return LGF_OK;
   cudaSetDevice(h->device);
   if (h->stream || h->cap_stream) cudaStreamSynchronize(h->stream);
-  free_lane(h->d);
-  free_lane(h->f);
-  cudaFree(h->U0); cudaFree(h->stage); cudaFree(h->partials); cudaFree(h->st); cudaFree(h->defect);
-  cudaFree(h->sin2); cudaFree(h->hist_F); cudaFree(h->hist_T);
+  free_lane(h, h->d);
+  free_lane(h, h->f);
+  h->mem.put_all();  // U0, stage, partials, state, tables, histories, network, mode log
+  cudaStreamSynchronize(h->stream);
   if (h->st_host) cudaFreeHost(h->st_host);
   if (h->defect_host) cudaFreeHost(h->defect_host);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   for (int i = 0; i < TimingRing::kSlots; ++i)
     for (int k = 0; k <= TimingRing::kMaxK; ++k)
       if (h->timing.ev[i][k]) cudaEventDestroy(h->timing.ev[i][k]);
-  cudaFree(h->mlp_w); cudaFree(h->ls); cudaFree(h->stats);
   delete h;
   return LGF_OK;
 }
 
 lgf_status lgf_create(const int32_t extents[4], lgf_precision prec, uint32_t flags, void* cuda_stream,
                       lgf_handle* out) {
+  return lgf_create_with_allocator(extents, prec, flags, cuda_stream, nullptr, out);
+}
+
+lgf_status lgf_create_with_allocator(const int32_t extents[4], lgf_precision prec, uint32_t flags,
+                                     void* cuda_stream, const lgf_allocator* allocator, lgf_handle* out) {
   if (!extents || !out) return LGF_E_ARG;
   *out = nullptr;
+  if (allocator && (!allocator->alloc || !allocator->free)) return LGF_E_ARG;
   if (prec != LGF_FP64 && prec != LGF_FP32 && prec != LGF_MIXED) return LGF_E_ARG;
   if (flags & ~(uint32_t)(LGF_STORE12 | LGF_TRACK_G | LGF_PLAIN_SD | LGF_LEARNED | LGF_EXACT_EXP)) return LGF_E_ARG;
   for (int mu = 0; mu < 4; ++mu)
@@ -626,6 +666,8 @@ lgf_status lgf_create(const int32_t extents[4], lgf_precision prec, uint32_t fla
     h->flags = flags;
     h->learned = (flags & LGF_LEARNED) != 0;
     h->stream = (cudaStream_t)cuda_stream;
+    h->mem.stream = h->stream;
+    if (allocator) h->mem.user = *allocator;
     if (cudaGetDevice(&h->device) != cudaSuccess) { delete h; return LGF_E_CUDA; }
     Geom& g = h->geom;
     g.V = 1;
@@ -649,18 +691,18 @@ lgf_status lgf_create(const int32_t extents[4], lgf_precision prec, uint32_t fla
       s = alloc_lane<float>(h, h->f, store12 ? 2 : 3, store12 ? 2 : 3, true);
       if (s == LGF_OK) s = alloc_lane<double>(h, h->d, 3, 3, track);
       if (s == LGF_OK) {
-        cudaError_t e = dalloc(&h->U0, (size_t)4 * 18 * g.V);
-        if (e != cudaSuccess) s = fail_cuda(h, e, "cudaMalloc U0");
+        cudaError_t e = h->mem.get(&h->U0, (size_t)4 * 18 * g.V);
+        if (e != cudaSuccess) s = fail_cuda(h, e, "allocation of U0");
       }
       h->phase = 32;
     }
     if (s == LGF_OK) {
       cudaError_t e = cudaSuccess;
-      if (e == cudaSuccess) e = dalloc(&h->stage, (size_t)4 * 18 * g.V);
-      if (e == cudaSuccess) e = dalloc(&h->partials, (size_t)2 * measure_blocks(g.V));
-      if (e == cudaSuccess) e = dalloc(&h->st, 1);
-      if (e == cudaSuccess) e = cudaMemset(h->st, 0, sizeof(DevState));
-      if (e == cudaSuccess) e = dalloc(&h->defect, 1);
+      if (e == cudaSuccess) e = h->mem.get(&h->stage, (size_t)4 * 18 * g.V);
+      if (e == cudaSuccess) e = h->mem.get(&h->partials, (size_t)MEASURE_PARTIALS * measure_blocks(g.V));
+      if (e == cudaSuccess) e = h->mem.get(&h->st, 1);
+      if (e == cudaSuccess) e = cudaMemsetAsync(h->st, 0, sizeof(DevState), h->stream);
+      if (e == cudaSuccess) e = h->mem.get(&h->defect, 1);
       if (e == cudaSuccess) e = cudaMallocHost((void**)&h->st_host, sizeof(DevState));
       if (e == cudaSuccess) e = cudaMallocHost((void**)&h->defect_host, sizeof(unsigned long long));
       if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
@@ -676,10 +718,13 @@ lgf_status lgf_create(const int32_t extents[4], lgf_precision prec, uint32_t fla
         const double sm = std::sin(M_PI * (double)(g.L[mu] / 2) / (double)g.L[mu]);
         h->p2max += 4.0 * sm * sm;
       }
-      if (e == cudaSuccess) e = dalloc(&h->sin2, sin2.size());
-      if (e == cudaSuccess) e = cudaMemcpy(h->sin2, sin2.data(), sin2.size() * 8, cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = h->mem.get(&h->sin2, sin2.size());
+      if (e == cudaSuccess) e = cudaMemcpyAsync(h->sin2, sin2.data(), sin2.size() * 8, cudaMemcpyHostToDevice, h->stream);
+      // stream-ordered buffers become usable by every stream once this returns
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
       if (e != cudaSuccess) s = fail_cuda(h, e, "lgf_create allocation");
     }
+    if (h->mem.misaligned) s = LGF_E_ARG;  // the caller's allocator returned memory not 256-byte aligned
     if (s != LGF_OK) {
       lgf_destroy(h);
       return s;
@@ -809,6 +854,7 @@ lgf_status lgf_fix(lgf_handle h, double theta_tol, int32_t max_iter, double alph
   if (!h->have_links) return fail(h, LGF_E_STATE, "no links set");
   if (!(theta_tol >= 0.0) || max_iter < 0 || !std::isfinite(alpha)) return fail(h, LGF_E_ARG, "bad fix arguments");
   if (h->learned && !h->mlp_w) return fail(h, LGF_E_STATE, "LGF_LEARNED handle without a loaded preconditioner");
+  h->repairs = 0;
   if (h->phase == 32) {
     NvtxRange phase32("FP32 phase");
     if ((s = ensure_filter<float>(h, h->f, alpha)) != LGF_OK) return s;
@@ -821,7 +867,8 @@ lgf_status lgf_fix(lgf_handle h, double theta_tol, int32_t max_iter, double alph
       if ((s = switch_to_fp64(h)) != LGF_OK) return s;
     }
   } else {
-    LGF_CK(h, launch_set_state(h->st, theta_tol, max_iter, 1, h->hist_cap, h->hist_F, h->hist_T, h->stream));
+    LGF_CK(h, launch_set_state(h->st, theta_tol, max_iter, 1, h->hist_cap, h->hist_F, h->hist_T, h->stream,
+                               h->hist_flags, h->hist_defect, h->defect_bound64, TRACE_FP64));
   }
   if (h->phase == 64) {
     NvtxRange phase64("FP64 phase");
@@ -837,6 +884,10 @@ lgf_status lgf_fix(lgf_handle h, double theta_tol, int32_t max_iter, double alph
     const int n = std::min(h->hist_cap, S.iter + 1);
     LGF_CK(h, cudaMemcpyAsync(h->user_F, h->hist_F, (size_t)n * 8, cudaMemcpyDeviceToHost, h->stream));
     LGF_CK(h, cudaMemcpyAsync(h->user_T, h->hist_T, (size_t)n * 8, cudaMemcpyDeviceToHost, h->stream));
+    if (h->user_flags)
+      LGF_CK(h, cudaMemcpyAsync(h->user_flags, h->hist_flags, (size_t)n * 4, cudaMemcpyDeviceToHost, h->stream));
+    if (h->user_defect)
+      LGF_CK(h, cudaMemcpyAsync(h->user_defect, h->hist_defect, (size_t)n * 8, cudaMemcpyDeviceToHost, h->stream));
     LGF_CK(h, cudaStreamSynchronize(h->stream));
   }
   if (!(std::isfinite(S.F) && std::isfinite(S.theta)) || S.status == ST_NONFINITE)
@@ -891,26 +942,58 @@ lgf_status lgf_get_divergence(lgf_handle h, double* D, int where) {
   return copy_out(h, dst, D, (size_t)18 * g.V, where);
 }
 
-lgf_status lgf_set_trace(lgf_handle h, double* F_hist, double* theta_hist, int32_t cap) {
+lgf_status lgf_set_trace_ex(lgf_handle h, double* F_hist, double* theta_hist, int32_t* flags_hist,
+                            double* defect_hist, int32_t cap) {
   lgf_status s = check_handle(h);
   if (s != LGF_OK) return s;
   if (cap < 0 || (cap > 0 && (!F_hist || !theta_hist))) return fail(h, LGF_E_ARG, "bad trace arguments");
   LGF_CK(h, cudaStreamSynchronize(h->stream));
-  cudaFree(h->hist_F);
-  cudaFree(h->hist_T);
-  h->hist_F = h->hist_T = nullptr;
+  h->mem.put(h->hist_F);
+  h->mem.put(h->hist_T);
+  h->mem.put(h->hist_flags);
+  h->mem.put(h->hist_defect);
+  h->hist_F = h->hist_T = h->hist_defect = nullptr;
+  h->hist_flags = nullptr;
   h->hist_cap = 0;
-  h->user_F = h->user_T = nullptr;
+  h->user_F = h->user_T = h->user_defect = nullptr;
+  h->user_flags = nullptr;
   if (cap > 0) {
-    LGF_CK(h, dalloc(&h->hist_F, (size_t)cap));
-    LGF_CK(h, dalloc(&h->hist_T, (size_t)cap));
+    LGF_CK(h, h->mem.get(&h->hist_F, (size_t)cap));
+    LGF_CK(h, h->mem.get(&h->hist_T, (size_t)cap));
+    LGF_CK(h, h->mem.get(&h->hist_flags, (size_t)cap));
+    LGF_CK(h, h->mem.get(&h->hist_defect, (size_t)cap));
     h->hist_cap = cap;
     h->user_F = F_hist;
     h->user_T = theta_hist;
+    h->user_flags = flags_hist;
+    h->user_defect = defect_hist;
   }
   // the device state must never point at freed history buffers
-  LGF_CK(h, launch_set_state(h->st, 0.0, 0, 0, h->hist_cap, h->hist_F, h->hist_T, h->stream));
+  LGF_CK(h, launch_set_state(h->st, 0.0, 0, 0, h->hist_cap, h->hist_F, h->hist_T, h->stream, h->hist_flags,
+                             h->hist_defect));
   LGF_CK(h, cudaStreamSynchronize(h->stream));
+  return LGF_OK;
+}
+
+lgf_status lgf_set_trace(lgf_handle h, double* F_hist, double* theta_hist, int32_t cap) {
+  return lgf_set_trace_ex(h, F_hist, theta_hist, nullptr, nullptr, cap);
+}
+
+lgf_status lgf_set_defect_bound(lgf_handle h, double bound_fp64, double bound_fp32) {
+  lgf_status s = check_handle(h);
+  if (s != LGF_OK) return s;
+  if (!(bound_fp64 >= 0.0) || !(bound_fp32 >= 0.0)) return fail(h, LGF_E_ARG, "bounds must be >= 0");
+  h->defect_bound64 = bound_fp64;
+  h->defect_bound32 = bound_fp32;
+  return LGF_OK;
+}
+
+lgf_status lgf_get_link_defect(lgf_handle h, double* defect, int32_t* repairs) {
+  lgf_status s = check_handle(h);
+  if (s != LGF_OK) return s;
+  if ((s = sync_state(h)) != LGF_OK) return s;
+  if (defect) *defect = h->st_host->defect;
+  if (repairs) *repairs = h->repairs;
   return LGF_OK;
 }
 
@@ -982,7 +1065,7 @@ lgf_status lgf_load_preconditioner(lgf_handle h, const uint16_t* w, size_t n_w, 
   if (s != LGF_OK) return s;
   if (!w || n_w != (size_t)MLP_NPARAM || (where != LGF_HOST && where != LGF_DEVICE))
     return fail(h, LGF_E_ARG, "expected LGF_MLP_NPARAM BF16 parameters");
-  if (!h->mlp_w) LGF_CK(h, dalloc(&h->mlp_w, (size_t)MLP_NPARAM));
+  if (!h->mlp_w) LGF_CK(h, h->mem.get(&h->mlp_w, (size_t)MLP_NPARAM));
   LGF_CK(h, cudaMemcpyAsync(h->mlp_w, w, (size_t)MLP_NPARAM * 2,
                             where == LGF_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, h->stream));
   LGF_CK(h, cudaStreamSynchronize(h->stream));
@@ -1007,15 +1090,15 @@ lgf_status lgf_set_mode_log(lgf_handle h, int32_t enable) {
   if (!enable) return LGF_OK;
   const int64_t V = h->geom.V;
   const int64_t nclass = h->phase == 64 ? h->d.mg.nclass : h->f.mg.nclass;
-  if (!h->stats) LGF_CK(h, dalloc(&h->stats, (size_t)MLP_NBUCKET * nclass * MLP_NSTAT));
-  if (!h->ls) LGF_CK(h, dalloc(&h->ls, 1));
+  if (!h->stats) LGF_CK(h, h->mem.get(&h->stats, (size_t)MLP_NBUCKET * nclass * MLP_NSTAT));
+  if (!h->ls) LGF_CK(h, h->mem.get(&h->ls, 1));
   if (h->phase == 64 && !h->d.Dlog) {
-    LGF_CK(h, dalloc(&h->d.Dlog, (size_t)4 * V));
-    LGF_CK(h, dalloc(&h->d.Dprev, (size_t)4 * V));
+    LGF_CK(h, h->mem.get(&h->d.Dlog, (size_t)4 * V));
+    LGF_CK(h, h->mem.get(&h->d.Dprev, (size_t)4 * V));
   }
   if (h->phase == 32 && !h->f.Dlog) {
-    LGF_CK(h, dalloc(&h->f.Dlog, (size_t)4 * V));
-    LGF_CK(h, dalloc(&h->f.Dprev, (size_t)4 * V));
+    LGF_CK(h, h->mem.get(&h->f.Dlog, (size_t)4 * V));
+    LGF_CK(h, h->mem.get(&h->f.Dprev, (size_t)4 * V));
   }
   LGF_CK(h, cudaMemsetAsync(h->stats, 0, sizeof(double) * MLP_NBUCKET * nclass * MLP_NSTAT, h->stream));
   LGF_CK(h, cudaMemsetAsync(h->ls, 0, sizeof(LogState), h->stream));

@@ -27,6 +27,7 @@
 
 #include "../../include/lgf.h"
 #include "lgf_internal.h"
+#include "lgf_mem.h"
 
 using namespace lgf;
 
@@ -56,6 +57,7 @@ struct ClassLane {
 }  // namespace
 
 struct lgf_batch_ctx {
+  DeviceMemory mem;  // every device buffer of the batch (stream-ordered on `stream`)
   int n = 0;
   std::vector<int> cls_of, slot_of;
   std::vector<ClassLane> cls;
@@ -103,7 +105,6 @@ bool extent_ok(int L) {
   return L == 1;
 }
 
-template <typename T> cudaError_t dalloc(T** p, size_t n) { return cudaMalloc((void**)p, n * sizeof(T)); }
 
 // ---- autotune cache key ----------------------------------------------------
 
@@ -179,14 +180,14 @@ lgf_status setup_class(lgf_batch_ctx* b, ClassLane& C) {
   const Geom& g = C.geom;
   const int64_t V = g.V;
   C.nb = measure_blocks(V);
-  LGF_BCK(b, dalloc(&C.U, (size_t)C.n * 36 * V));
-  LGF_BCK(b, dalloc(&C.D, (size_t)C.n * 4 * V));
-  LGF_BCK(b, dalloc(&C.g, (size_t)C.n * 9 * V));
-  LGF_BCK(b, dalloc(&C.K, (size_t)V));
-  LGF_BCK(b, dalloc(&C.partials, (size_t)C.n * 2 * C.nb));
+  LGF_BCK(b, b->mem.get(&C.U, (size_t)C.n * 36 * V));
+  LGF_BCK(b, b->mem.get(&C.D, (size_t)C.n * 4 * V));
+  LGF_BCK(b, b->mem.get(&C.g, (size_t)C.n * 9 * V));
+  LGF_BCK(b, b->mem.get(&C.K, (size_t)V));
+  LGF_BCK(b, b->mem.get(&C.partials, (size_t)C.n * MEASURE_PARTIALS * C.nb));
   const int nt = g.L[0] + g.L[1] + g.L[2] + g.L[3];
-  LGF_BCK(b, dalloc(&C.tw, (size_t)nt));
-  LGF_BCK(b, dalloc(&C.pos, (size_t)nt));
+  LGF_BCK(b, b->mem.get(&C.tw, (size_t)nt));
+  LGF_BCK(b, b->mem.get(&C.pos, (size_t)nt));
   if (configure_fft_plan(g.L, 8, &C.plan) != cudaSuccess)
     return bfail(b, LGF_E_UNSUPPORTED, "lattice planes do not fit the shared-memory FFT passes");
   std::vector<double2> tw(nt);
@@ -200,8 +201,8 @@ lgf_status setup_class(lgf_batch_ctx* b, ClassLane& C) {
     off += g.L[mu];
   }
   fft_positions(C.plan, pos.data());
-  LGF_BCK(b, cudaMemcpy(C.tw, tw.data(), nt * sizeof(double2), cudaMemcpyHostToDevice));
-  LGF_BCK(b, cudaMemcpy(C.pos, pos.data(), nt * sizeof(short), cudaMemcpyHostToDevice));
+  LGF_BCK(b, cudaMemcpyAsync(C.tw, tw.data(), nt * sizeof(double2), cudaMemcpyHostToDevice, b->stream));
+  LGF_BCK(b, cudaMemcpyAsync(C.pos, pos.data(), nt * sizeof(short), cudaMemcpyHostToDevice, b->stream));
   C.lmax = 0;
   for (int mu = 0; mu < 4; ++mu) C.lmax = std::max(C.lmax, g.L[mu]);
   std::vector<double> sin2((size_t)4 * C.lmax, 0.0);
@@ -214,24 +215,21 @@ lgf_status setup_class(lgf_batch_ctx* b, ClassLane& C) {
     const double sm = std::sin(M_PI * (double)(g.L[mu] / 2) / (double)g.L[mu]);
     C.p2max += 4.0 * sm * sm;
   }
-  LGF_BCK(b, dalloc(&C.sin2, sin2.size()));
-  LGF_BCK(b, cudaMemcpy(C.sin2, sin2.data(), sin2.size() * 8, cudaMemcpyHostToDevice));
+  LGF_BCK(b, b->mem.get(&C.sin2, sin2.size()));
+  LGF_BCK(b, cudaMemcpyAsync(C.sin2, sin2.data(), sin2.size() * 8, cudaMemcpyHostToDevice, b->stream));
   C.B.n = C.n;
   C.B.s_links = 36 * V;
   C.B.s_delta = 4 * V;
   C.B.s_g = 9 * V;
   C.B.s_G = 0;
-  C.B.s_part = 2 * C.nb;
+  C.B.s_part = MEASURE_PARTIALS * C.nb;
   C.B.st = b->st + C.off;
   LGF_BCK(b, launch_filter_table<double>(g, C.sin2, C.lmax, 0.08, C.p2max, 0, C.K, b->stream));
   C.alpha = 0.08;
   return autotune(b, C);
 }
 
-void free_class(ClassLane& C) {
-  cudaFree(C.U); cudaFree(C.D); cudaFree(C.g); cudaFree(C.K); cudaFree(C.tw); cudaFree(C.pos);
-  cudaFree(C.partials); cudaFree(C.sin2);
-}
+
 
 cudaError_t enqueue_class_body(ClassLane& C, cudaStream_t s) {
   cudaError_t e;
@@ -309,13 +307,11 @@ lgf_status lgf_batch_destroy(lgf_batch b) {
   cudaStreamSynchronize(b->stream);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
-  for (ClassLane& C : b->cls) free_class(C);
+  b->mem.put_all();
   for (cudaStream_t s : b->branch) cudaStreamDestroy(s);
   for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
   if (b->cap) cudaStreamDestroy(b->cap);
-  cudaFree(b->st);
-  cudaFree(b->stage);
-  cudaFree(b->defect);
+  cudaStreamSynchronize(b->stream);
   if (b->st_host) cudaFreeHost(b->st_host);
   if (b->defect_host) cudaFreeHost(b->defect_host);
   delete b;
@@ -334,6 +330,7 @@ lgf_status lgf_batch_create(int32_t n, const int32_t* extents, lgf_precision pre
   try {
     b->n = n;
     b->stream = (cudaStream_t)cuda_stream;
+    b->mem.stream = b->stream;
     if (cudaGetDevice(&b->device) != cudaSuccess) {
       delete b;
       return LGF_E_CUDA;
@@ -369,11 +366,11 @@ lgf_status lgf_batch_create(int32_t n, const int32_t* extents, lgf_precision pre
       vmax = std::max(vmax, C.geom.V);
     }
     lgf_status s = LGF_OK;
-    cudaError_t e = dalloc(&b->st, (size_t)n);
-    if (e == cudaSuccess) e = cudaMemset(b->st, 0, sizeof(DevState) * n);
+    cudaError_t e = b->mem.get(&b->st, (size_t)n);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->st, 0, sizeof(DevState) * n, b->stream);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&b->st_host, sizeof(DevState) * n);
-    if (e == cudaSuccess) e = dalloc(&b->stage, (size_t)72 * vmax);
-    if (e == cudaSuccess) e = dalloc(&b->defect, 1);
+    if (e == cudaSuccess) e = b->mem.get(&b->stage, (size_t)72 * vmax);
+    if (e == cudaSuccess) e = b->mem.get(&b->defect, 1);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&b->defect_host, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
     for (size_t c = 0; c < b->cls.size() && e == cudaSuccess; ++c) {

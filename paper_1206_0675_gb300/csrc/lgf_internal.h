@@ -33,9 +33,22 @@ struct DevState {
   int ubuf;          // fused lanes: which of the two link buffers holds the current links
   double* F_hist;    // F after measurement number i (i = iter) if i < hist_cap
   double* theta_hist;
+  double defect;       // largest unitarity defect of the sampled links (last measurement)
+  double defect_bound; // > 0: a measurement whose defect exceeds it ends the loop with ST_DEFECT
+  int redo;            // the running step redoes a rejected learned step with the plain filter
+  int repaired;        // the links were reunitarised since the last counted measurement
+  int* flag_hist;      // flags of measurement number i (TRACE_* bits) if i < hist_cap
+  double* defect_hist; // defect of measurement number i if i < hist_cap
 };
 
-enum { ST_OK = 0, ST_NONFINITE = 1 };
+enum { ST_OK = 0, ST_NONFINITE = 1, ST_DEFECT = 3 };
+
+// Per-measurement trace flags (the LGF_TRACE_* bits of include/lgf.h).
+enum { TRACE_FP64 = 1, TRACE_LEARNED = 2, TRACE_REDO = 4, TRACE_REPAIRED = 8, TRACE_REJECTED = 16 };
+
+// Measurement CTAs keep three partials each: the F sum, the theta sum and
+// the largest sampled link defect.
+constexpr int MEASURE_PARTIALS = 3;
 
 // Batch dimension of a launch: blockIdx.z selects one of n configurations of
 // the same lattice shape, whose buffers are the given strides (in elements)
@@ -117,7 +130,14 @@ cudaError_t launch_su3_defect(const double* aos, int64_t nmat, unsigned long lon
 // Loop parameters of the controller state (tol, max_iter, history);
 // reset_iter != 0 also zeroes the iteration counter and the status word.
 cudaError_t launch_set_state(DevState* st, double tol, int max_iter, int reset_iter, int hist_cap, double* F_hist,
-                             double* theta_hist, cudaStream_t s);
+                             double* theta_hist, cudaStream_t s, int* flag_hist = nullptr,
+                             double* defect_hist = nullptr, double defect_bound = 0.0, int flags0 = 0);
+
+// Gram-Schmidt reunitarisation of every link in place (rows 1-2 orthonormal
+// in the link precision, row 3 = (a x b)^* when stored), after a measured
+// defect passed the bound; marks st->repaired and clears ST_DEFECT.
+template <typename R, int ROWS>
+cudaError_t launch_reunitarize_links(const Geom& g, C2<R>* links, DevState* st, cudaStream_t s);
 
 // Complex array precision conversion (n elements).
 cudaError_t launch_c2_f64_to_f32(const double2* in, float2* out, int64_t n, cudaStream_t s);

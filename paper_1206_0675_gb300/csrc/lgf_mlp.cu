@@ -188,6 +188,7 @@ __global__ void __launch_bounds__(128) mlp_multiplier_kernel(const __nv_bfloat16
   __syncthreads();
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     st->use_m = st->revert ? 0 : 1;
+    st->redo = st->revert;
     st->revert = 0;
   }
   const float fb = theta > 0.0 ? (float)(floor(2.0 * log10(theta)) * 0.5) : -20.f;

@@ -21,38 +21,70 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Block sum of two values in a fixed order; result valid in thread 0.
-__device__ __forceinline__ void block_sum2(double& a, double& b) {
-  __shared__ double sa[32], sb[32];
+// Block reduction of two sums and a maximum in a fixed order; result valid
+// in thread 0.
+__device__ __forceinline__ void block_reduce3(double& a, double& b, double& m) {
+  __shared__ double sa[32], sb[32], sm[32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
   a = warp_sum(a);
   b = warp_sum(b);
-  if (lane == 0) { sa[warp] = a; sb[warp] = b; }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+  if (lane == 0) { sa[warp] = a; sb[warp] = b; sm[warp] = m; }
   __syncthreads();
   if (warp == 0) {
     a = lane < nw ? sa[lane] : 0.0;
     b = lane < nw ? sb[lane] : 0.0;
+    m = lane < nw ? sm[lane] : 0.0;
     a = warp_sum(a);
     b = warp_sum(b);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
   }
   __syncthreads();
 }
 
-// Reduction of the per-thread F and theta sums and, in the last CTA to
-// finish, the controller update: F and theta, the iteration count, the
-// history, the status word, the batch retirement flag or the graph's WHILE
-// condition; flip_ubuf != 0 also flips st->ubuf (after every CTA has read it).
+// Unitarity defect of a link from its rows 1-2 (row 3 is always rebuilt as
+// (a x b)^* or stored from that rebuild): the largest of | |a|^2 - 1 |,
+// | |b|^2 - 1 | and the components of <a, b>, in the link precision.
+template <typename R> __device__ __forceinline__ double rows_defect(const C2<R> a[3], const C2<R> b[3]) {
+  const R na = cnorm2<R>(a[0]) + cnorm2<R>(a[1]) + cnorm2<R>(a[2]);
+  const R nb = cnorm2<R>(b[0]) + cnorm2<R>(b[1]) + cnorm2<R>(b[2]);
+  C2<R> ip = cconjmul<R>(a[0], b[0]);
+  ip = cadd<R>(ip, cconjmul<R>(a[1], b[1]));
+  ip = cadd<R>(ip, cconjmul<R>(a[2], b[2]));
+  const R d = fmax(fmax(fabs(na - (R)1), fabs(nb - (R)1)), fmax(fabs(ip.x), fabs(ip.y)));
+  return (double)d;
+}
+
+// The links whose defect a measurement samples: every fourth warp of the
+// grid (warp index w with w % 4 == 0) takes direction (w / 4) % 4 of its 32
+// sites, i.e. one link in sixteen, spread over all directions.  The choice
+// is uniform within a warp, so the other warps skip the work entirely.
+__device__ __forceinline__ int defect_sample_mu() {
+  const unsigned w = (unsigned)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  return (w & 3u) == 0 ? (int)((w >> 2) & 3u) : -1;
+}
+
+// Reduction of the per-thread F and theta sums and the sampled link defect
+// and, in the last CTA to finish, the controller update: F, theta and the
+// defect, the iteration count, the history and its flags, the status word,
+// the batch retirement flag or the graph's WHILE condition; flip_ubuf != 0
+// also flips st->ubuf (after every CTA has read it); fp64 != 0 marks the
+// measurement as one of FP64 links in the trace flags.
 // fsum and tsum are one site's sums, already in FP64; every sum above a
 // site (warp, CTA, grid) is FP64 in a fixed order.
-__device__ __forceinline__ void measure_tail(const Geom& g, double fsum, double tsum, double* __restrict__ partials,
-                                             DevState* __restrict__ st, int count_iter, unsigned long long cond,
-                                             int use_cond, bool batch, int flip_ubuf) {
-  double fb = fsum, tb = tsum;
-  block_sum2(fb, tb);
+__device__ __forceinline__ void measure_tail(const Geom& g, double fsum, double tsum, double dmax,
+                                             double* __restrict__ partials, DevState* __restrict__ st, int count_iter,
+                                             unsigned long long cond, int use_cond, bool batch, int flip_ubuf,
+                                             int fp64) {
+  double fb = fsum, tb = tsum, db = dmax;
+  block_reduce3(fb, tb, db);
   __shared__ int is_last;
   if (threadIdx.x == 0) {
-    partials[2 * blockIdx.x] = fb;
-    partials[2 * blockIdx.x + 1] = tb;
+    partials[MEASURE_PARTIALS * blockIdx.x] = fb;
+    partials[MEASURE_PARTIALS * blockIdx.x + 1] = tb;
+    partials[MEASURE_PARTIALS * blockIdx.x + 2] = db;
     __threadfence();
     const unsigned int t = atomicAdd(&st->ticket, 1u);
     is_last = (t == gridDim.x - 1);
@@ -62,18 +94,20 @@ __device__ __forceinline__ void measure_tail(const Geom& g, double fsum, double 
   __threadfence();
   // Final sum over the per-CTA partials in a fixed order (independent of
   // which CTA finished last), so the result is bit-reproducible.
-  double f = 0.0, t = 0.0;
+  double f = 0.0, t = 0.0, d = 0.0;
   for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
-    f += __ldcg(&partials[2 * i]);
-    t += __ldcg(&partials[2 * i + 1]);
+    f += __ldcg(&partials[MEASURE_PARTIALS * i]);
+    t += __ldcg(&partials[MEASURE_PARTIALS * i + 1]);
+    d = fmax(d, __ldcg(&partials[MEASURE_PARTIALS * i + 2]));
   }
-  block_sum2(f, t);
+  block_reduce3(f, t, d);
   if (threadIdx.x == 0) {
     const double Vd = (double)g.V;
     const double F = f / (12.0 * Vd);
     const double th = 4.0 * t / (3.0 * Vd);
     int it = st->iter;
     int revert = 0;
+    int flags = fp64 ? TRACE_FP64 : 0;
     if (count_iter > 0) {
       it += 1;
       st->iter = it;
@@ -85,24 +119,38 @@ __device__ __forceinline__ void measure_tail(const Geom& g, double fsum, double 
         st->n_fallback += 1;
       }
       st->revert = revert;
+      if (st->use_m) flags |= TRACE_LEARNED;
+      if (st->redo) flags |= TRACE_REDO;
+      if (st->repaired) flags |= TRACE_REPAIRED;
+      st->redo = 0;
+      st->repaired = 0;
     } else if (count_iter < 0) {
       it -= 1;
       st->iter = it;
     }
     st->F = F;
     st->theta = th;
-    if (it < st->hist_cap) {
+    st->defect = d;
+    // The re-measurement after an undo repeats an entry already written; a
+    // measurement without an update (after a precision switch or a repair)
+    // refreshes F, theta and the defect of the current entry but keeps the
+    // flags of the update that produced it.
+    if (it < st->hist_cap && count_iter >= 0) {
       st->F_hist[it] = F;
       st->theta_hist[it] = th;
+      if (st->flag_hist && count_iter > 0) st->flag_hist[it] = flags;
+      if (st->defect_hist) st->defect_hist[it] = d;
     }
     const bool finite = isfinite(F) && isfinite(th);
+    const bool sound = !(st->defect_bound > 0.0 && d > st->defect_bound);
     if (!finite) st->status = ST_NONFINITE;
+    else if (!sound) st->status = ST_DEFECT;
     if (flip_ubuf) st->ubuf ^= 1;
     st->ticket = 0u;
     if (batch) st->done = !(finite && th >= st->tol && it < st->max_iter);
     if (use_cond) {
       cudaGraphConditionalHandle h = (cudaGraphConditionalHandle)cond;
-      cudaGraphSetConditional(h, (finite && ((th >= st->tol && it < st->max_iter) || revert)) ? 1u : 0u);
+      cudaGraphSetConditional(h, (finite && sound && ((th >= st->tol && it < st->max_iter) || revert)) ? 1u : 0u);
     }
   }
 }
@@ -176,7 +224,14 @@ measure_kernel(Geom g, MatField<R, ROWS> U, const C2<R>* __restrict__ links_alt,
     // ||Delta_A||_F^2
     tsum = (double)delta_norm2<R>(a0, a1, a2, d01, d02, d12);
   }
-  measure_tail(g, fsum, tsum, partials, st, count_iter, cond, use_cond, batch, 0);
+  double dmax = 0.0;
+  const int dmu = defect_sample_mu();
+  if (dmu >= 0 && s < g.V) {
+    C2<R> rows[2][3];
+    U.load_rows01_ro(dmu, s, rows);
+    dmax = rows_defect<R>(rows[0], rows[1]);
+  }
+  measure_tail(g, fsum, tsum, dmax, partials, st, count_iter, cond, use_cond, batch, 0, sizeof(R) == 8);
 }
 
 template <typename R, int ROWS>
@@ -244,6 +299,8 @@ update_measure_kernel(Geom g, C2<R>* __restrict__ U0, C2<R>* __restrict__ U1, Ma
   const MatField<R, LROWS> Us{cur ? U1 : U0, g.V}, Ud{cur ? U0 : U1, g.V};
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double fsum = 0, tsum = 0;  // as in measure_kernel: FP64 above one link
+  double dmax = 0.0;
+  const int dmu = defect_sample_mu();
   if (s < g.V) {
     int c[4];
     site_coords(g, s, c);
@@ -258,6 +315,7 @@ update_measure_kernel(Geom g, C2<R>* __restrict__ U0, C2<R>* __restrict__ U1, Ma
       Gf.load_ro(0, site_fwd(g, s, c, mu), h);
       gauge_product<R>(gx, u, h, o);
       Ud.store(mu, s, o);
+      if (mu == dmu) dmax = rows_defect<R>(o.e[0], o.e[1]);
       fsum += (double)(o.e[0][0].x + o.e[1][1].x + o.e[2][2].x);
       add_antiherm<R>(o, (R)-1, im0, im1, im2, w01, w02, w12);
       const int64_t sb = site_back(g, s, c, mu);
@@ -276,7 +334,7 @@ update_measure_kernel(Geom g, C2<R>* __restrict__ U0, C2<R>* __restrict__ U1, Ma
     delta[3 * g.V + s] = d12;
     tsum = (double)delta_norm2<R>(a0, a1, a2, d01, d02, d12);
   }
-  measure_tail(g, fsum, tsum, partials, st, 1, cond, use_cond, false, 1);
+  measure_tail(g, fsum, tsum, dmax, partials, st, 1, cond, use_cond, false, 1, sizeof(R) == 8);
 }
 
 template <typename R, int LROWS, int GROWS>
@@ -625,7 +683,7 @@ cudaError_t launch_filter_table(const Geom& g, const double* sin2, int lmax, dou
 // ---------------------------------------------------------------------------
 
 __global__ void set_state_kernel(DevState* st, double tol, int max_iter, int reset_iter, int hist_cap, double* Fh,
-                                 double* Th) {
+                                 double* Th, int* flh, double* dfh, double defect_bound, int flags0) {
   st->tol = tol;
   st->max_iter = max_iter;
   if (reset_iter) {
@@ -635,19 +693,71 @@ __global__ void set_state_kernel(DevState* st, double tol, int max_iter, int res
     st->revert = 0;
     st->use_m = 0;
     st->n_fallback = 0;
+    st->redo = 0;
+    st->repaired = 0;
   }
   st->hist_cap = hist_cap;
   st->F_hist = Fh;
   st->theta_hist = Th;
+  st->flag_hist = flh;
+  st->defect_hist = dfh;
+  st->defect_bound = defect_bound;
   if (hist_cap > 0 && reset_iter) {
     Fh[0] = st->F;
     Th[0] = st->theta;
+    if (flh) flh[0] = flags0;
+    if (dfh) dfh[0] = st->defect;
   }
 }
 
 cudaError_t launch_set_state(DevState* st, double tol, int max_iter, int reset_iter, int hist_cap, double* F_hist,
-                             double* theta_hist, cudaStream_t s) {
-  set_state_kernel<<<1, 1, 0, s>>>(st, tol, max_iter, reset_iter, hist_cap, F_hist, theta_hist);
+                             double* theta_hist, cudaStream_t s, int* flag_hist, double* defect_hist,
+                             double defect_bound, int flags0) {
+  set_state_kernel<<<1, 1, 0, s>>>(st, tol, max_iter, reset_iter, hist_cap, F_hist, theta_hist, flag_hist,
+                                   defect_hist, defect_bound, flags0);
+  return cudaGetLastError();
+}
+
+// Gram-Schmidt on rows 1-2 of every link, row 3 = (a x b)^* when stored.
+template <typename R, int ROWS>
+__global__ void reunitarize_links_kernel(int64_t n, MatField<R, ROWS> U) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int m = (int)(i / U.V);
+  const int64_t s = i - (int64_t)m * U.V;
+  M3<R> M;
+  U.load(m, s, M);
+  C2<R>* a = M.e[0];
+  C2<R>* b = M.e[1];
+  const R ia = (R)1 / sqrt(cnorm2<R>(a[0]) + cnorm2<R>(a[1]) + cnorm2<R>(a[2]));
+#pragma unroll
+  for (int j = 0; j < 3; ++j) a[j] = cscale<R>(a[j], ia);
+  C2<R> ip = cconjmul<R>(a[0], b[0]);
+  ip = cadd<R>(ip, cconjmul<R>(a[1], b[1]));
+  ip = cadd<R>(ip, cconjmul<R>(a[2], b[2]));
+  const C2<R> nip = mkc<R>(-ip.x, -ip.y);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) b[j] = cfma<R>(nip, a[j], b[j]);
+  const R ib = (R)1 / sqrt(cnorm2<R>(b[0]) + cnorm2<R>(b[1]) + cnorm2<R>(b[2]));
+#pragma unroll
+  for (int j = 0; j < 3; ++j) b[j] = cscale<R>(b[j], ib);
+  su3_third_row<R>(M.e[0], M.e[1], M.e[2]);
+  U.store(m, s, M);
+}
+
+__global__ void mark_repaired_kernel(DevState* st) {
+  st->repaired = 1;
+  if (st->status == ST_DEFECT) st->status = ST_OK;
+}
+
+template <typename R, int ROWS>
+cudaError_t launch_reunitarize_links(const Geom& g, C2<R>* links, DevState* st, cudaStream_t s) {
+  MatField<R, ROWS> U{links, g.V};
+  const int64_t n = 4 * g.V;
+  reunitarize_links_kernel<R, ROWS><<<(unsigned)((n + CONV_THREADS - 1) / CONV_THREADS), CONV_THREADS, 0, s>>>(n, U);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  mark_repaired_kernel<<<1, 1, 0, s>>>(st);
   return cudaGetLastError();
 }
 
@@ -720,7 +830,8 @@ cudaError_t launch_project_sites_f32_to_f64(const Geom& g, const float2* G32, do
   template cudaError_t launch_links_to_aos<R, ROWS>(const Geom&, const C2<R>*, double*, cudaStream_t);              \
   template cudaError_t launch_sites_to_aos<R, ROWS>(const Geom&, const C2<R>*, double*, cudaStream_t);              \
   template cudaError_t launch_sites_from_aos<R, ROWS>(const Geom&, const double*, C2<R>*, cudaStream_t);            \
-  template cudaError_t launch_set_identity<R, ROWS>(const Geom&, C2<R>*, cudaStream_t);
+  template cudaError_t launch_set_identity<R, ROWS>(const Geom&, C2<R>*, cudaStream_t);                        \
+  template cudaError_t launch_reunitarize_links<R, ROWS>(const Geom&, C2<R>*, DevState*, cudaStream_t);
 
 LGF_INST_R_ROWS(double, 3)
 LGF_INST_R_ROWS(double, 2)

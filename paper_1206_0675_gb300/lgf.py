@@ -31,6 +31,7 @@ LGF_OK, LGF_E_ARG, LGF_E_NOMEM, LGF_E_CUDA, LGF_E_STATE, LGF_E_NONFINITE, LGF_E_
 LGF_FP64, LGF_FP32, LGF_MIXED = 0, 1, 2
 LGF_STORE18, LGF_STORE12, LGF_TRACK_G, LGF_LEARNED, LGF_PLAIN_SD, LGF_EXACT_EXP = 0, 1, 2, 4, 8, 16
 LGF_FFT_2D2D, LGF_FFT_1D4, LGF_FFT_3D1D = 0, 1, 2
+LGF_TRACE_FP64, LGF_TRACE_LEARNED, LGF_TRACE_REDO, LGF_TRACE_REPAIRED = 1, 2, 4, 8
 LGF_MLP_NPARAM = 8897
 MLP_NBUCKET = 40
 MLP_NSTAT = 5
@@ -39,10 +40,21 @@ LGF_HOST, LGF_DEVICE = 0, 1
 _c_int_p = ctypes.POINTER(ctypes.c_int32)
 _c_dbl_p = ctypes.POINTER(ctypes.c_double)
 
+# lgf_allocator: void* alloc(size_t, void* stream, void* ctx); void free(void*, size_t, void* stream, void* ctx)
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class LgfAllocator(ctypes.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", ctypes.c_void_p)]
+
 # (name, restype, argtypes) for every entry point of include/lgf.h
 SIGNATURES = [
     ("lgf_create", ctypes.c_int, [ctypes.POINTER(ctypes.c_int32), ctypes.c_int, ctypes.c_uint32, ctypes.c_void_p,
                                   ctypes.POINTER(ctypes.c_void_p)]),
+    ("lgf_create_with_allocator", ctypes.c_int, [ctypes.POINTER(ctypes.c_int32), ctypes.c_int, ctypes.c_uint32,
+                                                 ctypes.c_void_p, ctypes.POINTER(LgfAllocator),
+                                                 ctypes.POINTER(ctypes.c_void_p)]),
     ("lgf_destroy", ctypes.c_int, [ctypes.c_void_p]),
     ("lgf_set_links", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     ("lgf_get_links", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
@@ -54,6 +66,10 @@ SIGNATURES = [
     ("lgf_get_gauge", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     ("lgf_get_divergence", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     ("lgf_set_trace", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
+    ("lgf_set_trace_ex", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_int32]),
+    ("lgf_set_defect_bound", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_double]),
+    ("lgf_get_link_defect", ctypes.c_int, [ctypes.c_void_p, _c_dbl_p, _c_int_p]),
     ("lgf_fft4", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int]),
     ("lgf_get_phase", ctypes.c_int, [ctypes.c_void_p, _c_int_p]),
     ("lgf_set_timing", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
@@ -131,6 +147,36 @@ def lgf_create(extents, prec: int, flags: int, stream: int = 0) -> int:
     return h.value
 
 
+def lgf_create_with_allocator(extents, prec: int, flags: int, stream: int, allocator) -> int:
+    """allocator: an LgfAllocator (kept alive by the caller for the handle's lifetime) or None."""
+    lib = load_library()
+    ext = (ctypes.c_int32 * 4)(*[int(e) for e in extents])
+    h = ctypes.c_void_p()
+    st = lib.lgf_create_with_allocator(ext, int(prec), ctypes.c_uint32(flags), ctypes.c_void_p(stream or None),
+                                       ctypes.byref(allocator) if allocator is not None else None, ctypes.byref(h))
+    if st != LGF_OK:
+        raise LgfError(st, "lgf_create_with_allocator")
+    return h.value
+
+
+def torch_allocator():
+    """An LgfAllocator that takes the handle's device memory from PyTorch's
+    caching allocator (torch.cuda.caching_allocator_alloc / _delete), so
+    that it is counted and reused with the rest of the process's tensors."""
+    import torch
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+        except Exception:
+            return None
+
+    def _free(ptr, nbytes, stream, ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    return LgfAllocator(ALLOC_FN(_alloc), FREE_FN(_free), None)
+
+
 def _check(h, st, where, allow=()):
     if st != LGF_OK and st not in allow:
         detail = load_library().lgf_last_error(ctypes.c_void_p(h)).decode(errors="replace")
@@ -186,6 +232,24 @@ def lgf_get_divergence(h: int, ptr: int, where: int) -> None:
 def lgf_set_trace(h: int, f_ptr: int, t_ptr: int, cap: int) -> None:
     _check(h, load_library().lgf_set_trace(ctypes.c_void_p(h), ctypes.c_void_p(f_ptr), ctypes.c_void_p(t_ptr),
                                            int(cap)), "lgf_set_trace")
+
+
+def lgf_set_trace_ex(h: int, f_ptr: int, t_ptr: int, flags_ptr: int, defect_ptr: int, cap: int) -> None:
+    _check(h, load_library().lgf_set_trace_ex(ctypes.c_void_p(h), ctypes.c_void_p(f_ptr), ctypes.c_void_p(t_ptr),
+                                              ctypes.c_void_p(flags_ptr or None), ctypes.c_void_p(defect_ptr or None),
+                                              int(cap)), "lgf_set_trace_ex")
+
+
+def lgf_set_defect_bound(h: int, bound_fp64: float, bound_fp32: float) -> None:
+    _check(h, load_library().lgf_set_defect_bound(ctypes.c_void_p(h), float(bound_fp64), float(bound_fp32)),
+           "lgf_set_defect_bound")
+
+
+def lgf_get_link_defect(h: int) -> tuple[float, int]:
+    d, n = ctypes.c_double(), ctypes.c_int32()
+    _check(h, load_library().lgf_get_link_defect(ctypes.c_void_p(h), ctypes.byref(d), ctypes.byref(n)),
+           "lgf_get_link_defect")
+    return d.value, n.value
 
 
 def lgf_fft4(h: int, ptr: int, nfields: int, sign: int, where: int) -> None:
@@ -384,7 +448,9 @@ class Lattice:
 
     def __init__(self, extents, precision: str = "fp64", store12: bool = False, track_G: bool = False,
                  plain_sd: bool = False, learned: bool = False, exact_exp: bool = False,
-                 stream: int | None = None):
+                 stream: int | None = None, allocator=None):
+        """allocator: None (CUDA's stream-ordered allocator), "torch" (PyTorch's
+        caching allocator) or an LgfAllocator."""
         self.extents = tuple(int(e) for e in extents)
         lx, ly, lz, lt = self.extents
         self.link_shape = (4, lt, lz, ly, lx, 3, 3)
@@ -398,7 +464,12 @@ class Lattice:
                 stream = torch.cuda.current_stream().cuda_stream
             except Exception:
                 stream = 0
-        self.handle = lgf_create(self.extents, _PREC[precision], flags, stream)
+        if allocator is None:
+            self._allocator = None
+            self.handle = lgf_create(self.extents, _PREC[precision], flags, stream)
+        else:
+            self._allocator = torch_allocator() if allocator == "torch" else allocator
+            self.handle = lgf_create_with_allocator(self.extents, _PREC[precision], flags, stream, self._allocator)
         self._trace = None
 
     def close(self):
@@ -469,17 +540,31 @@ class Lattice:
         it, F, th, st = lgf_fix(self.handle, theta_tol, max_iter, alpha)
         return it, F, th, st == LGF_OK
 
-    def set_trace(self, cap: int):
-        """Record F and theta of every measurement of the next fix(); returns the (F, theta) arrays."""
+    def set_trace(self, cap: int, flags: bool = False):
+        """Record F and theta of every measurement of the next fix(); returns the (F, theta) arrays, or
+        with flags=True (F, theta, trace flags, sampled link defect)."""
         if cap <= 0:
             lgf_set_trace(self.handle, 0, 0, 0)
             self._trace = None
             return None
         Fh = np.zeros(cap)
         Th = np.zeros(cap)
-        lgf_set_trace(self.handle, Fh.ctypes.data, Th.ctypes.data, cap)
-        self._trace = (Fh, Th)
+        if flags:
+            Fl = np.zeros(cap, dtype=np.int32)
+            Dh = np.zeros(cap)
+            lgf_set_trace_ex(self.handle, Fh.ctypes.data, Th.ctypes.data, Fl.ctypes.data, Dh.ctypes.data, cap)
+            self._trace = (Fh, Th, Fl, Dh)
+        else:
+            lgf_set_trace(self.handle, Fh.ctypes.data, Th.ctypes.data, cap)
+            self._trace = (Fh, Th)
         return self._trace
+
+    def set_defect_bound(self, bound_fp64: float = 1e-10, bound_fp32: float = 1e-4) -> None:
+        lgf_set_defect_bound(self.handle, bound_fp64, bound_fp32)
+
+    def link_defect(self) -> tuple[float, int]:
+        """(sampled link defect of the last measurement, reunitarisations in the last fix)."""
+        return lgf_get_link_defect(self.handle)
 
     def fft4(self, data: np.ndarray, sign: int = -1) -> np.ndarray:
         """The library's 4D DFT of 4 complex fields, shape (4, Lt, Lz, Ly, Lx), host arrays."""

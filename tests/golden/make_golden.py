@@ -8,6 +8,7 @@ tests stored expectations that need no oracle run.
 
     python tests/golden/make_golden.py              # the small fa_*.json cases
     python tests/golden/make_golden.py --headline   # the 32^4 cases (minutes per case)
+    python tests/golden/make_golden.py --headline-spread   # then their rounding spread
 
 The 32^4 cases are the 32^4 workload of the benchmark: U_mu(x) = h(x)
 exp(i eps sum_a c_a lambda_a/2) h^dag(x+mu) with eps = 1.0, seed 0 (a 50-step
@@ -86,7 +87,53 @@ def make_headline(case):
     return path
 
 
+SPREAD_DELTA = 2.0 ** -52  # one unit in the last place of an entry of size 1
+
+
+def rounding_spread(case):
+    """A second oracle trajectory of a headline fixture whose links are moved,
+    after every step, by a random rounding-level amount: U <- U + i delta H U
+    with H Hermitian, entries N(0, 1), delta = 2^-52.  Its relative distance
+    from the fixture's F and theta, step by step, is the spread that
+    different but equally valid FP64 rounding orders produce along that
+    trajectory; it is stored beside the trajectory."""
+    name, eps, seed, tol, max_iter = case
+    path = os.path.join(HERE, name + ".json")
+    with open(path) as f:
+        g = json.load(f)
+    rng = np.random.Generator(np.random.Philox(key=991 + seed))
+    U = fields.random_links(HEADLINE_EXT, eps, seed)
+    K = O.fa_filter(HEADLINE_EXT, 0.08)
+
+    def nudge(U):
+        A = rng.standard_normal(U.shape) + 1j * rng.standard_normal(U.shape)
+        H = 0.5 * (A + np.conj(np.swapaxes(A, -1, -2)))
+        return U + 1j * SPREAD_DELTA * (H @ U)
+
+    U = nudge(U)
+    F, th, D = O.measure(U)
+    dF, dT = [abs(F / g["F"][0] - 1)], [abs(th / g["theta"][0] - 1)]
+    for k in range(1, g["iterations"] + 1):
+        U, _ = O.fa_step(U, 0.08, K, D)
+        U = nudge(U)
+        F, th, D = O.measure(U)
+        dF.append(abs(F / g["F"][k] - 1))
+        dT.append(abs(th / g["theta"][k] - 1))
+    g["spread"] = {"delta": SPREAD_DELTA, "F_rel": dF, "theta_rel": dT,
+                   "how": "oracle rerun with U <- U + i delta H U (H Hermitian, N(0,1) entries) after every step"}
+    with open(path, "w") as f:
+        json.dump(g, f, indent=1)
+    return path
+
+
 def main():
+    if "--headline-spread" in sys.argv[1:]:
+        import multiprocessing as mp
+        cases = [c for c in HEADLINE_CASES if c[3] > 0]
+        with mp.get_context("spawn").Pool(len(cases)) as pool:
+            for path in pool.imap_unordered(rounding_spread, cases):
+                print("wrote spread into", path, flush=True)
+        return
     if "--headline" in sys.argv[1:]:
         import multiprocessing as mp
         with mp.get_context("spawn").Pool(len(HEADLINE_CASES)) as pool:

@@ -84,6 +84,22 @@ def check_G(G, g, tol):
         assert np.max(np.abs(G[t, z, y, x] - want)) < tol, s["site"]
 
 
+def check_G_up_to_global(G, g, tol_local, tol_global):
+    """G agrees with the oracle's up to one constant SU(3) matrix C (the
+    Landau gauge leaves global transformations free, and the filter's zero
+    mode K(0) = 0 never acts on them): C(x) = G(x) G_oracle(x)^dag is the
+    same at every sampled site to tol_local, and within tol_global of 1."""
+    Cs = []
+    for s in g["G_samples"]:
+        x, y, z, t = s["site"]
+        want = np.array(s["G_re"]) + 1j * np.array(s["G_im"])
+        Cs.append(G[t, z, y, x] @ want.conj().T)
+    for C in Cs[1:]:
+        assert np.max(np.abs(C - Cs[0])) < tol_local
+    assert np.max(np.abs(Cs[0] - np.eye(3))) < tol_global
+    return max(np.max(np.abs(C - Cs[0])) for C in Cs), np.max(np.abs(Cs[0] - np.eye(3)))
+
+
 @pytest.mark.parametrize("plan", ["2d2d", "1d4", "autotune"])
 def test_trajectory_50_fp64_32x4(plan):
     g = load(TRAJ)
@@ -170,7 +186,10 @@ def test_iterations_to_1e15_mixed_32x4(name):
     assert conv and th < g["tol"]
     assert abs(it - ref_it) <= max(1, 0.02 * ref_it)
     assert abs(F - g["F"][-1]) < 1e-10
-    check_G(G, g, 1e-9)
+    # The FP32 phase leaves a rounding-level global rotation behind (the
+    # zero mode), which no later step removes; the rest of G matches.
+    loc, glob_ = check_G_up_to_global(G, g, 1e-9, 1e-5)
+    print(f"G up to a global rotation: local {loc:.2e}, global {glob_:.2e}")
 
 
 def test_fixtures_cover_the_workload():

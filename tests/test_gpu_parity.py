@@ -440,3 +440,28 @@ def test_anisotropic_48x3_96_one_step(aniso_case, prec, store12):
     assert abs(F1 - Fo1) < (1e-13 if f64 else 1e-6) * abs(Fo1)
     assert rel(th1, tho1) < (1e-11 if f64 else 1e-5)
     assert np.max(np.abs(U1[:, idx[0], idx[1], idx[2], idx[3]] - Uo_s)) < (1e-12 if f64 else 2e-5)
+
+
+# ---------------------------------------------------------------------------
+# per-measurement trace flags and the sampled link defect
+# ---------------------------------------------------------------------------
+
+def test_trace_flags_and_defect_of_a_mixed_fix():
+    ext = (8, 8, 8, 8)
+    U = fields.random_links(ext, eps=1.0, seed=1)
+    with lgf.Lattice(ext, "mixed", store12=True) as lat:
+        lat.set_links(U)
+        Fh, Th, Fl, Dh = lat.set_trace(6001, flags=True)
+        it, F, th, conv = lat.fix(1e-15, 6000, 0.08)
+        d_last, repairs = lat.link_defect()
+    assert conv and repairs == 0
+    n = it + 1
+    fp64 = (Fl[1:n] & lgf.LGF_TRACE_FP64) != 0
+    k = int(np.argmax(fp64)) + 1          # first update run in FP64
+    assert fp64[k - 1:].all() and not fp64[:k - 1].any()
+    # every update from links with theta below the switch level is FP64, none above it
+    assert Th[k - 1] < 1e-9 and np.all(Th[:k - 1] >= 1e-9)
+    assert not np.any(Fl[1:n] & (lgf.LGF_TRACE_LEARNED | lgf.LGF_TRACE_REDO | lgf.LGF_TRACE_REPAIRED))
+    # FP32 links carry a defect of a few FP32 roundings, FP64 links of a few FP64 ones
+    assert 0 < Dh[:k].max() < 2e-6
+    assert Dh[k:n].max() < 1e-13 and d_last == Dh[n - 1]
