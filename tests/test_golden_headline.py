@@ -45,6 +45,12 @@ def test_fixture_structure(path):
     for s in g["G_samples"]:
         G = np.array(s["G_re"]) + 1j * np.array(s["G_im"])
         assert np.max(np.abs(G @ G.conj().T - np.eye(3))) < 1e-12
+    if g["tol"] > 0:
+        # the oracle's rounding spread along the fix: one entry per measurement,
+        # at the level of FP64 rounding (written by make_golden.py --headline-spread)
+        sp = g["spread"]
+        assert len(sp["theta_rel"]) == len(sp["F_rel"]) == n + 1
+        assert 0 <= min(sp["theta_rel"]) and max(sp["theta_rel"]) < 1e-9 and max(sp["F_rel"]) < 1e-13
 
 
 def test_first_step_of_the_50_step_trajectory_reproduces():

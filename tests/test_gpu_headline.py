@@ -12,13 +12,15 @@ paper_1206_0675_gb300.fields:
 Tolerances, all against the oracle:
 
 * FP64, per-iteration F: 1e-11 relative.
-* FP64, per-iteration theta: the larger of 1e-11 and 100 u / sqrt(theta)
-  relative, u = 2^-53.  Each of the eight real components of Delta_A is a
-  signed sum of sixteen entries of unit-norm link rows, so either code
-  carries an absolute error of a few u in it whatever the size of theta;
-  with |Delta_A| of order sqrt(theta) the relative error of
-  theta ~ sum |Delta_A|^2 is of order u / sqrt(theta).  The bound equals
-  1e-11 at theta = 1.2e-6 and allows 3.5e-7 at theta = 1e-15.  The largest
+* FP64, per-iteration theta: 1e-11 relative along the 50-step trajectory.
+  Along the fixes to 1e-15 the bound at step k is the larger of 1e-11 and
+  ten times the rounding spread of the oracle itself up to step k: the
+  fixture stores, step by step, how far a second oracle run moves from the
+  first when its links are nudged by one unit in the last place after every
+  step (tests/golden/make_golden.py, rounding_spread).  Two correct FP64
+  codes that round in different orders differ by about that much; on these
+  fields it reaches 1.5e-11 at theta ~ 1e-5 and 3e-11 to 8e-11 near
+  theta = 1e-15, above the 1e-11 a fixed bound would allow.  The largest
   deviation seen along each trajectory is printed next to the check.
 * FP32 12-real storage: F and theta within 1e-5 relative over the 50 steps.
 * Iterations to theta < 1e-15 within 2% (at least one step), final F
@@ -38,7 +40,6 @@ from paper_1206_0675_gb300 import lgf
 pytestmark = pytest.mark.gpu
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-U_ROUND = 2.0 ** -53
 
 
 def load(name):
@@ -68,8 +69,13 @@ def field(g):
     return _FIELDS[key]
 
 
-def theta_tol(theta):
-    return np.maximum(1e-11, 100.0 * U_ROUND / np.sqrt(np.asarray(theta)))
+def theta_tol(g, n):
+    """Per-step theta bound: 1e-11, or ten times the running maximum of the
+    oracle's own rounding spread where the fixture stores one."""
+    if "spread" not in g:
+        return np.full(n, 1e-11)
+    env = np.maximum.accumulate(np.asarray(g["spread"]["theta_rel"][:n]))
+    return np.maximum(1e-11, 10.0 * env)
 
 
 def rel(a, b):
@@ -120,7 +126,7 @@ def test_trajectory_50_fp64_32x4(plan):
     print(f"max rel dev F {rF.max():.2e}, theta {rT.max():.2e} (theta from {g['theta'][0]:.3e} to "
           f"{g['theta'][-1]:.3e})")
     assert np.all(rF < 1e-11), int(np.argmax(rF))
-    assert np.all(rT < theta_tol(g["theta"])), int(np.argmax(rT / theta_tol(g["theta"])))
+    assert np.all(rT < theta_tol(g, n + 1)), int(np.argmax(rT / theta_tol(g, n + 1)))
     check_G(G, g, 1e-10)
 
 
@@ -165,7 +171,9 @@ def test_iterations_to_1e15_fp64_32x4(name):
     print(f"{it} vs {ref_it} iterations; max rel dev F {rF.max():.2e}, theta {rT.max():.2e} "
           f"(at theta {g['theta'][int(np.argmax(rT))]:.2e})")
     assert np.all(rF < 1e-11)
-    assert np.all(rT < theta_tol(g["theta"][:n])), int(np.argmax(rT / theta_tol(g["theta"][:n])))
+    tol = theta_tol(g, n)
+    print(f"  theta bound from the oracle's rounding spread: {tol.min():.1e} .. {tol.max():.1e}")
+    assert np.all(rT < tol), int(np.argmax(rT / tol))
     check_G(G, g, 1e-9)
 
 
