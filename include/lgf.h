@@ -259,22 +259,30 @@ lgf_status lgf_get_timing(lgf_handle h, double* ms, int32_t nkernels, int32_t* n
 
 /* ---- learned per-mode multiplier (an addition; the paper has no learned part) ----
  *
- * With LGF_LEARNED every step multiplies the filter by m(k) in [0.25, 1.25],
+ * With LGF_LEARNED every step multiplies the filter by m(k) in [0.25, 2],
  * predicted for each momentum class (modes with the same per-direction
- * p2_mu = 4 sin^2(pi k_mu / L_mu)) by a network 7 -> 64 -> 64 -> 64 -> 1
+ * p2_mu = 4 sin^2(pi k_mu / L_mu)) by a network 8 -> 64 -> 64 -> 64 -> 1
  * (ReLU hidden layers, m = softplus(z)) with BF16 weights and FP32
  * accumulation on the tensor cores.  Features of a mode:
  *   (p2_x/4, p2_y/4, p2_z/4, p2_t/4, -floor(2 log10 theta)/32, min(iter/10000, 1),
- *    clamp(log10(theta/theta_prev), -2, 1)/2)
- * where theta and iter are those of the links the step starts from and
- * theta_prev that of the links one step earlier (the last feature is 0 on the
- * first step).  A step that lowers F is undone and redone with the plain
- * filter; theta (of the plain definition) decides convergence.
+ *    clamp(log10(theta/theta_prev), -2, 1)/2, r_class)
+ * where theta and iter are those of the links the step starts from,
+ * theta_prev that of the links one step earlier (the seventh feature is 0 on
+ * the first step), and r_class the contraction of the mode's class over the
+ * last step whose two Fourier-space divergences are kept:
+ *   r_obs = sum Re<D^_{k-1}, D^_{k-2}> / sum |D^_{k-2}|^2  (over the modes and
+ *   packed fields of the class),  r_class = clamp(1 - (1 - r_obs) / m, -1, 1),
+ * m being the multiplier that produced D^_{k-1} from D^_{k-2}, so that r_class
+ * is the contraction the plain filter would have given (0 until two
+ * divergences are kept).  The filter pass stores each step's Fourier-space
+ * divergence (before the filter, FP32) for this purpose.  A step that lowers
+ * F is undone and redone with the plain filter; theta (of the plain
+ * definition) decides convergence.
  *
- * Parameter layout (8897 numbers, rows [out][in]):
- *   W1[64][7] @0, b1[64] @448, W2[64][64] @512, b2[64] @4608,
- *   W3[64][64] @4672, b3[64] @8768, w4[64] @8832, b4 @8896. */
-#define LGF_MLP_NPARAM 8897
+ * Parameter layout (8961 numbers, rows [out][in]):
+ *   W1[64][8] @0, b1[64] @512, W2[64][64] @576, b2[64] @4672,
+ *   W3[64][64] @4736, b3[64] @8832, w4[64] @8896, b4 @8960. */
+#define LGF_MLP_NPARAM 8961
 
 /* Load BF16 network parameters (n_w must be LGF_MLP_NPARAM) into the
  * handle; where = LGF_HOST or LGF_DEVICE.  Synchronises. */
@@ -287,32 +295,33 @@ lgf_status lgf_get_fallbacks(lgf_handle h, int32_t* n);
 /* Mode log (training data).  enable != 0 makes every subsequent lgf_step
  * also accumulate, for each theta bucket b and momentum class c, the sums
  *   Re<D^_{k+1}, D^_k>, |D^_k|^2, count, iteration fraction of step k,
- *   last-step contraction feature of step k
+ *   last-step contraction feature of step k, Re<D^_k, D^_{k-1}>, |D^_{k-1}|^2
  * over the modes of the class, D^ being the 4D Fourier transform of the
- * packed divergence (b = clamp(4 - 2 floor(2 log10 theta_k)/2, 0, 39)).
- * Enabling clears the sums.  Synchronises. */
+ * packed divergence (b = clamp(4 - 2 floor(2 log10 theta_k)/2, 0, 39)); the
+ * last two only once D^_{k-1} is known.  Enabling clears the sums.
+ * Synchronises. */
 lgf_status lgf_set_mode_log(lgf_handle h, int32_t enable);
 
-/* Copy the mode-log sums out: n must be 40 * nclass * 5 doubles, laid out
- * [b][c][5] with nclass = prod_mu (L_mu/2 + 1) and
+/* Copy the mode-log sums out: n must be 40 * nclass * 7 doubles, laid out
+ * [b][c][7] with nclass = prod_mu (L_mu/2 + 1) and
  * c = ((f_t H_z + f_z) H_y + f_y) H_x + f_x, f_mu = min(k_mu, L_mu - k_mu),
  * H_mu = L_mu/2 + 1.  out is a host pointer.  Synchronises. */
 lgf_status lgf_get_mode_log(lgf_handle h, double* out, int64_t n);
 
 /* Network inference on the tensor cores for arbitrary feature rows
- * (device pointers): X[n][7] FP32 features, P[8897] BF16 parameters,
+ * (device pointers): X[n][8] FP32 features, P[8961] BF16 parameters,
  * m[n] = softplus(z) FP32 out (unclamped).  Enqueued on cuda_stream. */
 lgf_status lgf_mlp_eval(const uint16_t* P, const float* X, int64_t n, float* m, void* cuda_stream);
 
 /* Loss L = (1/n) sum_i w_i (log m_i - y_i)^2 over all rows and its gradient
- * with respect to the FP32 parameters (device pointers: P[8897], X[n][7],
- * Y[n], W[n], grad[8897]); *loss on the host.  Synchronises. */
+ * with respect to the FP32 parameters (device pointers: P[8961], X[n][8],
+ * Y[n], W[n], grad[8961]); *loss on the host.  Synchronises. */
 lgf_status lgf_mlp_loss_grad(const float* P, const float* X, const float* Y, const float* W, int64_t n, float* grad,
                              double* loss, void* cuda_stream);
 
 /* Adam training of the FP32 parameters P (device, in place) on minibatches of
  * `batch` rows drawn by a counter-based hash of (seed, step, row): `steps`
- * updates with learning rate lr, moments in adam[2 * 8897] (device, zero for
+ * updates with learning rate lr, moments in adam[2 * 8961] (device, zero for
  * a fresh start), t0 = number of updates done before (bias correction).
  * loss_hist (host, may be NULL) receives the minibatch loss of every
  * update.  Synchronises. */
@@ -320,7 +329,7 @@ lgf_status lgf_mlp_train(float* P, float* adam, const float* X, const float* Y, 
                          int32_t batch, int32_t steps, float lr, uint64_t seed, int32_t t0, double* loss_hist,
                          void* cuda_stream);
 
-/* FP32 -> BF16 (round to nearest even) of the 8897 parameters (device). */
+/* FP32 -> BF16 (round to nearest even) of the 8961 parameters (device). */
 lgf_status lgf_mlp_to_bf16(const float* P, uint16_t* out, void* cuda_stream);
 
 /* Theta below which an LGF_MIXED fix leaves the FP32 phase (default 1e-9;
@@ -343,13 +352,13 @@ enum { LGF_FFT_2D2D = 0, LGF_FFT_1D4 = 1, LGF_FFT_3D1D = 2 };
 lgf_status lgf_set_fft_decomposition(lgf_handle h, int32_t decomposition);
 
 /* FP32 phase only: run the link update and the following measurement as one
- * kernel (enable != 0, the default for LGF_FP32 and LGF_MIXED handles
- * without LGF_LEARNED) or as two (enable = 0).  The fused kernel reads the
- * links from one of two buffers and writes the updated links to the other;
- * it recomputes the updated backward links U'_mu(x - mu^) in registers
- * instead of reading them back, so the links cross HBM once less per step.
- * Results are bit-identical either way.  No effect on FP64 phases.
- * LGF_E_UNSUPPORTED for enable != 0 with LGF_LEARNED.  Synchronises. */
+ * kernel (enable != 0, the default for LGF_FP32 and LGF_MIXED handles) or as
+ * two (enable = 0).  The fused kernel reads the links from one of two
+ * buffers and writes the updated links to the other; it recomputes the
+ * updated backward links U'_mu(x - mu^) in registers instead of reading them
+ * back, so the links cross HBM once less per step.  The undo of a rejected
+ * learned step works on whichever buffer holds the current links.  Results
+ * are bit-identical either way.  No effect on FP64 phases.  Synchronises. */
 lgf_status lgf_set_fused_update(lgf_handle h, int32_t enable);
 
 /* Autotuner of a handle: times the transform and g of one step (CUDA events,

@@ -6,22 +6,27 @@ additions -- a per-mode multiplier m(k) applied on top of the
 Fourier-acceleration filter alpha p2max/p2(k) of Eq. (eq:gx), predicted by a
 small MLP and trained on statistics logged from plain FA-SD trajectories.
 
-Network (flat parameter vector, the library's layout, 8897 numbers)
+Network (flat parameter vector, the library's layout, 8961 numbers)
 -------------------------------------------------------------------
-    h1 = relu(W1 x + b1)      W1: [64][7]   offset 0,    b1: [64] offset 448
-    h2 = relu(W2 h1 + b2)     W2: [64][64]  offset 512,  b2: [64] offset 4608
-    h3 = relu(W3 h2 + b3)     W3: [64][64]  offset 4672, b3: [64] offset 8768
-    z  = w4 . h3 + b4         w4: [64]      offset 8832, b4: [1]  offset 8896
+    h1 = relu(W1 x + b1)      W1: [64][8]   offset 0,    b1: [64] offset 512
+    h2 = relu(W2 h1 + b2)     W2: [64][64]  offset 576,  b2: [64] offset 4672
+    h3 = relu(W3 h2 + b3)     W3: [64][64]  offset 4736, b3: [64] offset 8832
+    z  = w4 . h3 + b4         w4: [64]      offset 8896, b4: [1]  offset 8960
     m  = softplus(z) = log(1 + e^z)
 
 Features of a momentum mode k at iteration k_it with stopping quantity theta
 --------------------------------------------------------------------------
-    x = (p2_x/4, p2_y/4, p2_z/4, p2_t/4, -bucket(theta)/16, iter_frac, rate)
+    x = (p2_x/4, p2_y/4, p2_z/4, p2_t/4, -bucket(theta)/16, iter_frac, rate, r_class)
     p2_mu = 4 sin^2(pi k_mu / L_mu)        (per direction, as in the filter)
     bucket(theta) = floor(2 log10 theta) / 2   (half decades; theta <= 0 -> -20)
     iter_frac = min(k_it / 10000, 1)
     rate = clamp(log10(theta / theta_prev), -2, 1) / 2   (0 on the first step),
            theta_prev being the stopping quantity one step earlier
+    r_class = clamp(r, -1, 1): the contraction of the mode's class (modes with
+           the same p2 tuple) over the last step whose two Fourier-space
+           divergences are known, under the plain filter:
+           r = sum Re<D^_new, D^_old> / sum |D^_old|^2 over the class
+           (0 while fewer than two divergences are known)
 
 Inference on the GPU uses BF16 weights with FP32 accumulation: ``forward``
 with ``bf16=True`` emulates it (weights and the inputs of the three mma
@@ -35,26 +40,28 @@ p2 tuple) and theta bucket b, the logged ratio
     r = sum Re<D^_{k+1}, D^_k> / sum |D^_k|^2
 estimates the per-step contraction 1 - K0 lambda_eff of that class.  The
 multiplier that would remove it in one step in the linear model is
-m* = 1/(1 - r); it is clamped to [M_LO, M_HI] (M_HI is the largest uniform
-multiplier that kept plain FA-SD stable on the synthetic fields).  The
-linear model holds only once the step is small: in buckets with
-theta >= THETA_LINEAR the target is the plain filter, m* = 1.  The loss is
-the weighted mean square error of log m against log m*, with weight
-|D^_k|^2 normalised per bucket.
+m* = 1/(1 - r); it is clamped to [M_LO, M_HI].  M_HI = 2 bounds the step a
+slowly contracting class may take: with the class's own contraction as an
+input the multiplier can stay near 1 (or below) on classes that contract
+fast or oscillate, so the cap that a uniform multiplier needed for stability
+(1.25) no longer binds.  The linear model holds only once the step is small:
+in buckets with theta >= THETA_LINEAR the target is the plain filter,
+m* = 1.  The loss is the weighted mean square error of log m against log m*,
+with weight |D^_k|^2 normalised per bucket.
 """
 
 from __future__ import annotations
 
 import numpy as np
 
-NIN, NH = 7, 64
-OFF_W1, OFF_B1 = 0, 448
-OFF_W2, OFF_B2 = 512, 4608
-OFF_W3, OFF_B3 = 4672, 8768
-OFF_W4, OFF_B4 = 8832, 8896
-NPARAM = 8897
+NIN, NH = 8, 64
+OFF_W1, OFF_B1 = 0, 512
+OFF_W2, OFF_B2 = 576, 4672
+OFF_W3, OFF_B3 = 4736, 8832
+OFF_W4, OFF_B4 = 8896, 8960
+NPARAM = 8961
 ITER_SCALE = 10000.0
-M_LO, M_HI = 0.25, 1.25
+M_LO, M_HI = 0.25, 2.0
 THETA_LINEAR = 1e-4
 
 
@@ -104,8 +111,9 @@ def rate_feature(theta: float, theta_prev: float) -> float:
     return 0.5 * float(np.clip(np.log10(theta / theta_prev), -2.0, 1.0))
 
 
-def features(p2_tuple, theta: float, iteration: int, theta_prev: float = 0.0) -> np.ndarray:
-    """Feature rows for an array of per-direction p2 tuples, shape (n, 4) -> (n, 7)."""
+def features(p2_tuple, theta: float, iteration: int, theta_prev: float = 0.0, r_class=0.0) -> np.ndarray:
+    """Feature rows for an array of per-direction p2 tuples, shape (n, 4) -> (n, 8);
+    r_class (scalar or one value per row) is the class contraction, clamped to [-1, 1]."""
     p2 = np.atleast_2d(np.asarray(p2_tuple, dtype=np.float64))
     n = p2.shape[0]
     x = np.empty((n, NIN))
@@ -113,6 +121,7 @@ def features(p2_tuple, theta: float, iteration: int, theta_prev: float = 0.0) ->
     x[:, 4] = -theta_bucket(theta) / 16.0
     x[:, 5] = min(iteration / ITER_SCALE, 1.0)
     x[:, 6] = rate_feature(theta, theta_prev) if iteration > 0 else 0.0
+    x[:, 7] = np.clip(np.broadcast_to(np.asarray(r_class, dtype=np.float64), (n,)), -1.0, 1.0)
     return x
 
 

@@ -28,7 +28,7 @@ constexpr double kSU3Tol = 1e-10;       // input validation threshold
 // of either the FP64 or the FP32 arithmetic.
 template <typename R> struct Lane {
   C2<R>* U = nullptr;      // links [4][rows][3][V]
-  C2<R>* U2 = nullptr;     // second link buffer (FP32 lanes without the learned multiplier)
+  C2<R>* U2 = nullptr;     // second link buffer (FP32 lanes)
   bool fused = false;      // update and measurement run as one kernel, links ping-pong between U and U2
   C2<R>* g = nullptr;      // gauge transform of the last step [grows][3][V]
   C2<R>* D = nullptr;      // packed divergence / FFT workspace [4][V]
@@ -47,8 +47,9 @@ template <typename R> struct Lane {
   float* mtab = nullptr;   // multiplier per momentum class
   float* p2f = nullptr;    // per-direction p2 tables for the network features
   MlpGeom mg{};
-  C2<R>* Dlog = nullptr;   // Fourier-space divergence of the current / previous step (mode log)
+  C2<R>* Dlog = nullptr;   // Fourier-space divergence of the current / previous / earlier step (mode log)
   C2<R>* Dprev = nullptr;
+  C2<R>* Dprev2 = nullptr;
 };
 
 // Per-kernel CUDA-event timing of lgf_step (ring of in-flight steps).
@@ -123,6 +124,8 @@ struct lgf_ctx {
   TimingRing timing;
   double switch_theta = 1e-9;     // FP32 -> FP64 switch level of LGF_MIXED
   bool learned = false;           // LGF_LEARNED
+  float* mtab = nullptr;          // learned multiplier tables of even and odd steps [2][nclass]
+  float2* snap = nullptr;         // Fourier-space divergence snapshots of even and odd steps [2][4][V]
   uint16_t* mlp_w = nullptr;      // BF16 network parameters (device)
   bool logging = false;           // per-mode statistics of every lgf_step
   bool log_primed = false;
@@ -176,7 +179,7 @@ template <typename R> void set_decomp(Lane<R>& L, int decomposition) {
 template <typename R> void free_lane(lgf_ctx* h, Lane<R>& L) {
   drop_graph(L);
   for (void* p : {(void*)L.U, (void*)L.U2, (void*)L.g, (void*)L.D, (void*)L.K, (void*)L.tw, (void*)L.pos,
-                  (void*)L.G, (void*)L.mtab, (void*)L.p2f, (void*)L.Dlog, (void*)L.Dprev})
+                  (void*)L.G, (void*)L.p2f, (void*)L.Dlog, (void*)L.Dprev, (void*)L.Dprev2})
     h->mem.put(p);
   L = Lane<R>();
 }
@@ -187,9 +190,9 @@ template <typename R> lgf_status alloc_lane(lgf_ctx* h, Lane<R>& L, int rows, in
   L.grows = grows;
   LGF_CK(h, h->mem.get(&L.U, (size_t)4 * rows * 3 * V));
   // FP32 lanes stream HBM in the update and the measurement: fuse them
-  // (not with the learned multiplier, whose undo of a rejected step
-  // transforms the links in place)
-  if (sizeof(R) == sizeof(float) && !h->learned) {
+  // (the undo of a rejected learned step then works on whichever of the two
+  // link buffers holds the current links)
+  if (sizeof(R) == sizeof(float)) {
     LGF_CK(h, h->mem.get(&L.U2, (size_t)4 * rows * 3 * V));
     L.fused = true;
   }
@@ -230,11 +233,24 @@ template <typename R> lgf_status alloc_lane(lgf_ctx* h, Lane<R>& L, int rows, in
       p2.push_back((float)(4.0 * sv * sv));
     }
   }
-  L.mg.m_lo = 0.25f;
-  L.mg.m_hi = 1.25f;
+  L.mg.m_lo = MLP_M_LO;
+  L.mg.m_hi = MLP_M_HI;
   LGF_CK(h, h->mem.get(&L.p2f, p2.size()));
   LGF_CK(h, cudaMemcpyAsync(L.p2f, p2.data(), p2.size() * sizeof(float), cudaMemcpyHostToDevice, h->stream));
-  if (h->learned) LGF_CK(h, h->mem.get(&L.mtab, (size_t)L.mg.nclass));
+  if (h->learned) {
+    // one pair of multiplier tables and divergence snapshots per handle,
+    // shared by both lanes of a mixed handle (the contraction feature spans
+    // the precision switch)
+    if (!h->mtab) {
+      LGF_CK(h, h->mem.get(&h->mtab, (size_t)2 * L.mg.nclass));
+      std::vector<float> ones((size_t)2 * L.mg.nclass, 1.f);
+      LGF_CK(h, cudaMemcpyAsync(h->mtab, ones.data(), ones.size() * sizeof(float), cudaMemcpyHostToDevice,
+                                h->stream));
+      LGF_CK(h, cudaStreamSynchronize(h->stream));
+      LGF_CK(h, h->mem.get(&h->snap, (size_t)2 * 4 * V));
+    }
+    L.mtab = h->mtab;
+  }
   L.active = true;
   return LGF_OK;
 }
@@ -313,6 +329,17 @@ inline int kernel_category(int k) {
 
 inline int exact_exp(const lgf_ctx* h) { return (h->flags & LGF_EXACT_EXP) ? 1 : 0; }
 
+// The learned extras of the pass that carries the filter (none without LGF_LEARNED).
+template <typename R> LearnedIO learned_io(const lgf_ctx* h, const Lane<R>& L) {
+  LearnedIO io;
+  if (!h->learned) return io;
+  io.mtab = L.mtab;
+  io.snap = h->snap;
+  io.st = h->st;
+  io.nclass = L.mg.nclass;
+  return io;
+}
+
 // Passes of the 1D x 4 and 3D + 1D decompositions, and g from their output.
 template <typename R> cudaError_t enqueue_alt_fft(lgf_ctx* h, Lane<R>& L, int k, cudaStream_t s) {
   const Geom& g = h->geom;
@@ -320,7 +347,7 @@ template <typename R> cudaError_t enqueue_alt_fft(lgf_ctx* h, Lane<R>& L, int k,
     case K_F1X: return launch_fft_line<R>(g, L.plan, 0, L.D, L.tw, L.pos, L.K, -1, 4, s);
     case K_F1Y: return launch_fft_line<R>(g, L.plan, 1, L.D, L.tw, L.pos, L.K, -1, 4, s);
     case K_F1Z: return launch_fft_line<R>(g, L.plan, 2, L.D, L.tw, L.pos, L.K, -1, 4, s);
-    case K_T1: return launch_fft_line<R>(g, L.plan, 3, L.D, L.tw, L.pos, L.K, 0, 4, s, Batch(), L.mtab, &h->st->use_m);
+    case K_T1: return launch_fft_line<R>(g, L.plan, 3, L.D, L.tw, L.pos, L.K, 0, 4, s, Batch(), learned_io(h, L));
     case K_I1Z: return launch_fft_line<R>(g, L.plan, 2, L.D, L.tw, L.pos, L.K, +1, 4, s);
     case K_I1Y: return launch_fft_line<R>(g, L.plan, 1, L.D, L.tw, L.pos, L.K, +1, 4, s);
     case K_I1X: return launch_fft_line<R>(g, L.plan, 0, L.D, L.tw, L.pos, L.K, +1, 4, s);
@@ -340,7 +367,7 @@ template <> cudaError_t enqueue_kernel<double>(lgf_ctx* h, Lane<double>& L, int 
   const Geom& g = h->geom;
   switch (k) {
     case K_A: return launch_fft_xy<double>(g, L.plan, L.D, L.tw, L.pos, -1, 4, s);
-    case K_B: return launch_fft_zt<double>(g, L.plan, L.D, L.tw, L.pos, L.K, 0, 4, s, L.mtab, &h->st->use_m);
+    case K_B: return launch_fft_zt<double>(g, L.plan, L.D, L.tw, L.pos, L.K, 0, 4, s, learned_io(h, L));
     case K_C:
       return launch_fft_xy_inv_gauge<double, double, 3>(g, L.plan, L.D, L.tw, L.pos, L.g, L.G, s, Batch(),
                                                         exact_exp(h));
@@ -348,10 +375,10 @@ template <> cudaError_t enqueue_kernel<double>(lgf_ctx* h, Lane<double>& L, int 
       return L.rows == 3 ? launch_update<double, 3, 3>(g, L.U, L.g, s) : launch_update<double, 2, 3>(g, L.U, L.g, s);
     case K_MEAS: return enqueue_measure<double>(h, L, 1, cond, use_cond, s);
     case K_REVERT:
-      return L.rows == 3 ? launch_revert<double, 3, 3>(g, L.U, L.g, L.G, h->st, s)
-                         : launch_revert<double, 2, 3>(g, L.U, L.g, L.G, h->st, s);
+      return L.rows == 3 ? launch_revert<double, 3, 3>(g, L.U, L.g, L.G, h->st, s, L.U2)
+                         : launch_revert<double, 2, 3>(g, L.U, L.g, L.G, h->st, s, L.U2);
     case K_RESTORE: return enqueue_measure<double>(h, L, -1, 0, 0, s, 1);
-    case K_MLP: return launch_mlp_multiplier(h->mlp_w, L.mg, L.p2f, h->st, L.mtab, s);
+    case K_MLP: return launch_mlp_multiplier(h->mlp_w, L.mg, g, L.p2f, h->st, L.mtab, h->snap, s);
     default: return enqueue_alt_fft<double>(h, L, k, s);
   }
 }
@@ -361,7 +388,7 @@ template <> cudaError_t enqueue_kernel<float>(lgf_ctx* h, Lane<float>& L, int k,
   const Geom& g = h->geom;
   switch (k) {
     case K_A: return launch_fft_xy<float>(g, L.plan, L.D, L.tw, L.pos, -1, 4, s);
-    case K_B: return launch_fft_zt<float>(g, L.plan, L.D, L.tw, L.pos, L.K, 0, 4, s, L.mtab, &h->st->use_m);
+    case K_B: return launch_fft_zt<float>(g, L.plan, L.D, L.tw, L.pos, L.K, 0, 4, s, learned_io(h, L));
     case K_C:
       return L.grows == 2 ? launch_fft_xy_inv_gauge<float, float, 2>(g, L.plan, L.D, L.tw, L.pos, L.g, L.G, s,
                                                                      Batch(), exact_exp(h))
@@ -374,10 +401,10 @@ template <> cudaError_t enqueue_kernel<float>(lgf_ctx* h, Lane<float>& L, int k,
                  : launch_update_measure<float, 3, 3>(g, L.U, L.U2, L.g, L.D, h->partials, h->st, cond, use_cond, s);
     case K_MEAS: return enqueue_measure<float>(h, L, 1, cond, use_cond, s);
     case K_REVERT:
-      return L.grows == 2 ? launch_revert<float, 2, 2>(g, L.U, L.g, L.G, h->st, s)
-                          : launch_revert<float, 3, 3>(g, L.U, L.g, L.G, h->st, s);
+      return L.grows == 2 ? launch_revert<float, 2, 2>(g, L.U, L.g, L.G, h->st, s, L.U2)
+                          : launch_revert<float, 3, 3>(g, L.U, L.g, L.G, h->st, s, L.U2);
     case K_RESTORE: return enqueue_measure<float>(h, L, -1, 0, 0, s, 1);
-    case K_MLP: return launch_mlp_multiplier(h->mlp_w, L.mg, L.p2f, h->st, L.mtab, s);
+    case K_MLP: return launch_mlp_multiplier(h->mlp_w, L.mg, g, L.p2f, h->st, L.mtab, h->snap, s);
     default: return enqueue_alt_fft<float>(h, L, k, s);
   }
 }
@@ -552,9 +579,12 @@ template <typename R> cudaError_t log_modes(lgf_ctx* h, Lane<R>& L, bool prime_o
     return e;
   if ((e = launch_fft_xy<R>(g, L.plan, L.Dlog, L.tw, L.pos, -1, 4, h->stream)) != cudaSuccess) return e;
   if ((e = launch_fft_zt<R>(g, L.plan, L.Dlog, L.tw, L.pos, L.K, -1, 4, h->stream)) != cudaSuccess) return e;
-  if (!prime_only && (e = launch_mode_log<R>(g, L.mg, L.Dlog, L.Dprev, h->ls, h->stats, h->stream)) != cudaSuccess)
+  if (!prime_only &&
+      (e = launch_mode_log<R>(g, L.mg, L.Dlog, L.Dprev, L.Dprev2, h->ls, h->stats, h->stream)) != cudaSuccess)
     return e;
   if ((e = launch_log_state_update(h->ls, h->st, h->stream)) != cudaSuccess) return e;
+  // rotate: current -> previous -> the one before
+  std::swap(L.Dprev2, L.Dprev);
   std::swap(L.Dlog, L.Dprev);
   return cudaSuccess;
 }
@@ -1095,10 +1125,12 @@ lgf_status lgf_set_mode_log(lgf_handle h, int32_t enable) {
   if (h->phase == 64 && !h->d.Dlog) {
     LGF_CK(h, h->mem.get(&h->d.Dlog, (size_t)4 * V));
     LGF_CK(h, h->mem.get(&h->d.Dprev, (size_t)4 * V));
+    LGF_CK(h, h->mem.get(&h->d.Dprev2, (size_t)4 * V));
   }
   if (h->phase == 32 && !h->f.Dlog) {
     LGF_CK(h, h->mem.get(&h->f.Dlog, (size_t)4 * V));
     LGF_CK(h, h->mem.get(&h->f.Dprev, (size_t)4 * V));
+    LGF_CK(h, h->mem.get(&h->f.Dprev2, (size_t)4 * V));
   }
   LGF_CK(h, cudaMemsetAsync(h->stats, 0, sizeof(double) * MLP_NBUCKET * nclass * MLP_NSTAT, h->stream));
   LGF_CK(h, cudaMemsetAsync(h->ls, 0, sizeof(LogState), h->stream));
@@ -1302,8 +1334,10 @@ lgf_status lgf_autotune(lgf_handle h, char* report, size_t len) {
     if ((s = tune_lane<float>(h, h->f, rep)) != LGF_OK) return s;
   }
   rep += "}";
-  // the trials overwrote the divergence and g: restore the measurement
+  // the trials overwrote the divergence, g and the divergence snapshots of a
+  // learned handle: restore the measurement, forget the snapshots
   h->have_g = false;
+  LGF_CK(h, cudaMemsetAsync(&h->st->snaps, 0, sizeof(int), h->stream));
   if (h->have_links) {
     if ((s = measure_current(h)) != LGF_OK) return s;
     if ((s = sync_state(h)) != LGF_OK) return s;
@@ -1322,7 +1356,7 @@ lgf_status lgf_set_fused_update(lgf_handle h, int32_t enable) {
   if (s != LGF_OK) return s;
   Lane<float>& L = h->f;
   if (!L.active) return LGF_OK;  // FP64 handles never fuse
-  if (enable && !L.U2) return fail(h, LGF_E_UNSUPPORTED, "the learned multiplier needs the unfused update");
+  if (enable && !L.U2) return fail(h, LGF_E_UNSUPPORTED, "the FP32 lane has no second link buffer");
   if ((enable != 0) == L.fused) return LGF_OK;
   if ((s = sync_state(h)) != LGF_OK) return s;
   if (!enable && h->st_host->ubuf) {

@@ -129,7 +129,7 @@ cudaError_t time_plan(ClassLane& C, const FFTPlan& p, cudaStream_t s, float* ms_
   for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
     e = cudaEventRecord(e0, s);
     if (e == cudaSuccess) e = launch_fft_xy<double>(C.geom, p, C.D, C.tw, C.pos, -1, 4, s, B);
-    if (e == cudaSuccess) e = launch_fft_zt<double>(C.geom, p, C.D, C.tw, C.pos, C.K, 0, 4, s, nullptr, nullptr, B);
+    if (e == cudaSuccess) e = launch_fft_zt<double>(C.geom, p, C.D, C.tw, C.pos, C.K, 0, 4, s, LearnedIO(), B);
     if (e == cudaSuccess)
       e = launch_fft_xy_inv_gauge<double, double, 3>(C.geom, p, C.D, C.tw, C.pos, C.g, nullptr, s, B);
     if (e == cudaSuccess) e = cudaEventRecord(e1, s);
@@ -234,7 +234,7 @@ lgf_status setup_class(lgf_batch_ctx* b, ClassLane& C) {
 cudaError_t enqueue_class_body(ClassLane& C, cudaStream_t s) {
   cudaError_t e;
   if ((e = launch_fft_xy<double>(C.geom, C.plan, C.D, C.tw, C.pos, -1, 4, s, C.B)) != cudaSuccess) return e;
-  if ((e = launch_fft_zt<double>(C.geom, C.plan, C.D, C.tw, C.pos, C.K, 0, 4, s, nullptr, nullptr, C.B)) != cudaSuccess)
+  if ((e = launch_fft_zt<double>(C.geom, C.plan, C.D, C.tw, C.pos, C.K, 0, 4, s, LearnedIO(), C.B)) != cudaSuccess)
     return e;
   if ((e = launch_fft_xy_inv_gauge<double, double, 3>(C.geom, C.plan, C.D, C.tw, C.pos, C.g, nullptr, s, C.B)) !=
       cudaSuccess)

@@ -181,6 +181,20 @@ __device__ __forceinline__ void fft_lines_dif(C2<R>* tile, const Lines& ln, cons
 // shared-memory layout helpers
 // ---------------------------------------------------------------------------
 
+// Global -> shared copy of one complex element without a register round trip
+// (PTX cp.async; 8 bytes for FP32, 16 bytes for FP64, both aligned to their
+// size), so that a thread keeps all of its tile's loads in flight at once
+// instead of waiting for each before issuing the next.  cp_async_wait() waits
+// for this thread's copies; a __syncthreads() after it publishes the tile.
+template <typename R> __device__ __forceinline__ void cp_async_elem(C2<R>* dst, const C2<R>* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  if constexpr (sizeof(C2<R>) == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // Shared memory of a pass: twiddles of two directions, position tables of two
 // directions, then the tile.  Returns the tile pointer.
 template <typename R>
@@ -230,8 +244,9 @@ __global__ void __launch_bounds__(512) fft_xy_kernel(Geom g, FFTDir dx, FFTDir d
   __syncthreads();
   for (int i = threadIdx.x; i < fpb * plane; i += blockDim.x) {
     const int f = (int)cd.a.div((uint32_t)i), r = i - f * plane, y = (int)cd.b.div((uint32_t)r), x = r - y * Lx;
-    tile[f * PS + pos[Lx + y] * RS + pos[x]] = data[(int64_t)(f0 + f) * g.V + slab * plane + r];
+    cp_async_elem<R>(&tile[f * PS + pos[Lx + y] * RS + pos[x]], &data[(int64_t)(f0 + f) * g.V + slab * plane + r]);
   }
+  cp_async_wait();
   __syncthreads();
   fft_lines_dit<R, SIGN>(tile, lx, dx, tw);
   fft_lines_dit<R, SIGN>(tile, ly, dy, tw + Lx);
@@ -248,9 +263,8 @@ __global__ void __launch_bounds__(512) fft_xy_kernel(Geom g, FFTDir dx, FFTDir d
 template <typename R>
 __global__ void __launch_bounds__(512) fft_zt_filter_kernel(Geom g, FFTDir dz, FFTDir dt, C2<R>* __restrict__ data,
                                      const C2<R>* __restrict__ twg, const short* __restrict__ posg,
-                                     const R* __restrict__ K, int xc, int mode, const float* __restrict__ mtab,
-                                     int4 H, const int* __restrict__ use_m, Lines lz, Lines lt, CopyDiv cd,
-                                     Batch B) {
+                                     const R* __restrict__ K, int xc, int mode, LearnedIO lio, int4 H, Lines lz,
+                                     Lines lt, CopyDiv cd, Batch B) {
   if (batch_skip(B)) return;
   data += blockIdx.z * B.s_delta;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -271,14 +285,19 @@ __global__ void __launch_bounds__(512) fft_zt_filter_kernel(Geom g, FFTDir dz, F
   const int t = (int)cd.b.div((uint32_t)zt), z = zt - t * Lz;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     LGF_ZT_IDX(i)
-    tile[pos[Lz + t] * TS + pos[z] * xc + xi] = fld[(int64_t)zt * plane + sxy + xi];
+    cp_async_elem<R>(&tile[pos[Lz + t] * TS + pos[z] * xc + xi], &fld[(int64_t)zt * plane + sxy + xi]);
   }
+  cp_async_wait();
   __syncthreads();
   if (mode == 0) {
     fft_lines_dit<R, -1>(tile, lz, dz, tw);
     fft_lines_dit<R, -1>(tile, lt, dt, tw + Lz);
     // learned multiplier of the momentum class (f_mu = min(k_mu, L_mu - k_mu))
-    const bool learned = mtab != nullptr && *use_m != 0;
+    // and the snapshot of the transformed divergence, both of step k
+    const int kit = lio.st != nullptr ? lio.st->iter : 0;
+    const bool learned = lio.mtab != nullptr && lio.st->use_m != 0;
+    const float* mtab = lio.mtab + (int64_t)(kit & 1) * lio.nclass;
+    float2* snap = lio.snap != nullptr ? lio.snap + ((int64_t)(kit & 1) * 4 + blockIdx.y) * g.V : nullptr;
     const int fy = min(y, Ly - y);
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       LGF_ZT_IDX(i)
@@ -289,6 +308,7 @@ __global__ void __launch_bounds__(512) fft_zt_filter_kernel(Geom g, FFTDir dz, F
         k *= (R)__ldg(&mtab[((ft * H.z + fz) * H.y + fy) * H.x + fx]);
       }
       C2<R>& e = tile[t * TS + z * xc + xi];
+      if (snap != nullptr) snap[(int64_t)zt * plane + sxy + xi] = make_float2((float)e.x, (float)e.y);
       e = mkc<R>(e.x * k, e.y * k);
     }
     __syncthreads();
@@ -343,8 +363,7 @@ struct LinePass {
 template <typename R>
 __global__ void __launch_bounds__(512) fft_line_kernel(LinePass lp, FFTDir d, Geom g, C2<R>* __restrict__ data,
                                                        const C2<R>* __restrict__ twg, const short* __restrict__ posg,
-                                                       const R* __restrict__ K, int mode, Lines ln,
-                                                       const float* __restrict__ mtab, const int* __restrict__ use_m,
+                                                       const R* __restrict__ K, int mode, Lines ln, LearnedIO lio,
                                                        int4 H, Batch B) {
   const int64_t V = g.V;
   if (batch_skip(B)) return;
@@ -373,8 +392,9 @@ __global__ void __launch_bounds__(512) fft_line_kernel(LinePass lp, FFTDir d, Ge
   const bool natural_in = mode > 0;
   for (int i = threadIdx.x; i < n_el; i += blockDim.x) {
     LGF_LINE_IDX(i)
-    tile[l * RS + (natural_in ? n : pos[n])] = fld[site];
+    cp_async_elem<R>(&tile[l * RS + (natural_in ? n : pos[n])], &fld[site]);
   }
+  cp_async_wait();
   __syncthreads();
   if (mode < 0) {
     fft_lines_dit<R, -1>(tile, ln, d, tw);
@@ -382,7 +402,10 @@ __global__ void __launch_bounds__(512) fft_line_kernel(LinePass lp, FFTDir d, Ge
     fft_lines_dif<R, +1>(tile, ln, d, tw);
   } else {
     fft_lines_dit<R, -1>(tile, ln, d, tw);
-    const bool learned = mtab != nullptr && *use_m != 0;
+    const int kit = lio.st != nullptr ? lio.st->iter : 0;
+    const bool learned = lio.mtab != nullptr && lio.st->use_m != 0;
+    const float* mtab = lio.mtab + (int64_t)(kit & 1) * lio.nclass;
+    float2* snap = lio.snap != nullptr ? lio.snap + ((int64_t)(kit & 1) * 4 + blockIdx.y) * V : nullptr;
     for (int i = threadIdx.x; i < n_el; i += blockDim.x) {
       LGF_LINE_IDX(i)
       R k = __ldg(&K[site]);
@@ -394,6 +417,7 @@ __global__ void __launch_bounds__(512) fft_line_kernel(LinePass lp, FFTDir d, Ge
         k *= (R)__ldg(&mtab[((ft * H.z + fz) * H.y + fy) * H.x + fx]);
       }
       C2<R>& e = tile[l * RS + n];
+      if (snap != nullptr) snap[site] = make_float2((float)e.x, (float)e.y);
       e = mkc<R>(e.x * k, e.y * k);
     }
     __syncthreads();
@@ -431,8 +455,9 @@ __global__ void __launch_bounds__(512) fft_xyz_kernel(Geom g, FFTDir dx, FFTDir 
   for (int i = threadIdx.x; i < n_el; i += blockDim.x) {
     LGF_XYZ_IDX(i)
     const int o = SIGN < 0 ? pos[Lx + Ly + z] * PS + pos[Lx + y] * RS + pos[x] : z * PS + y * RS + x;
-    tile[o] = fld[i];
+    cp_async_elem<R>(&tile[o], &fld[i]);
   }
+  cp_async_wait();
   __syncthreads();
   if (SIGN < 0) {
     fft_lines_dit<R, -1>(tile, lx, dx, tw);
@@ -476,28 +501,55 @@ __device__ __forceinline__ double rsqrt_fp64(double x) {
 // v = w / |w| with w = r2 - <u, r2> u = r2 - (c / |r1|^2) r1, where
 // c = <r1, r2> = sum_j conj(r1_j) r2_j = (a + d)(Im f1 + i Re f1) + conj(f2) f3
 // (the two terms in f1 combine).  All of it in FP64.
-__device__ __forceinline__ void gauge_from_packed(double2 f0, double2 f1, double2 f2, double2 f3, double2 u[3],
-                                                  double2 v[3]) {
-  const double a = f0.x, d = f0.y;
+// The FP64 Gram-Schmidt factors of 1 + X: i1 = 1/|r1|, w = r2 - k r1 and
+// i2 = 1/|w|, so that u = i1 r1 and v = i2 w.
+struct GSFactors {
+  double i1, i2;
+  double2 w[3];
+};
+
+__device__ __forceinline__ void gram_schmidt_factors(double a, double d, double2 f1, double2 f2, double2 f3,
+                                                     GSFactors& o) {
   const double n1 = fma(f2.x, f2.x, fma(f2.y, f2.y, fma(f1.x, f1.x, fma(f1.y, f1.y, fma(a, a, 1.0)))));
-  const double i1 = rsqrt_fp64(n1);
+  o.i1 = rsqrt_fp64(n1);
   const double s = a + d;
-  const double q = i1 * i1;  // 1 / |r1|^2
+  const double q = o.i1 * o.i1;  // 1 / |r1|^2
   const double kx = q * fma(f2.x, f3.x, fma(f2.y, f3.y, s * f1.y));
   const double ky = q * fma(f2.x, f3.y, fma(-f2.y, f3.x, s * f1.x));
   // w = r2 - k r1
-  const double2 w0 = make_double2(fma(ky, a, -f1.x - kx), fma(-kx, a, f1.y - ky));
-  const double2 w1 = make_double2(fma(ky, f1.y, fma(-kx, f1.x, 1.0)), fma(-ky, f1.x, fma(-kx, f1.y, d)));
-  const double2 w2 = make_double2(fma(ky, f2.y, fma(-kx, f2.x, f3.x)), fma(-ky, f2.x, fma(-kx, f2.y, f3.y)));
-  const double n2 = fma(w2.x, w2.x, fma(w2.y, w2.y, fma(w1.x, w1.x, fma(w1.y, w1.y, fma(w0.x, w0.x, w0.y * w0.y)))));
-  const double i2 = rsqrt_fp64(n2);
-  u[0] = make_double2(i1, a * i1);
-  u[1] = make_double2(f1.x * i1, f1.y * i1);
-  u[2] = make_double2(f2.x * i1, f2.y * i1);
-  v[0] = cscale<double>(w0, i2);
-  v[1] = cscale<double>(w1, i2);
-  v[2] = cscale<double>(w2, i2);
+  o.w[0] = make_double2(fma(ky, a, -f1.x - kx), fma(-kx, a, f1.y - ky));
+  o.w[1] = make_double2(fma(ky, f1.y, fma(-kx, f1.x, 1.0)), fma(-ky, f1.x, fma(-kx, f1.y, d)));
+  o.w[2] = make_double2(fma(ky, f2.y, fma(-kx, f2.x, f3.x)), fma(-ky, f2.x, fma(-kx, f2.y, f3.y)));
+  const double n2 = fma(o.w[2].x, o.w[2].x, fma(o.w[2].y, o.w[2].y, fma(o.w[1].x, o.w[1].x,
+                    fma(o.w[1].y, o.w[1].y, fma(o.w[0].x, o.w[0].x, o.w[0].y * o.w[0].y)))));
+  o.i2 = rsqrt_fp64(n2);
 }
+
+// Rows u, v of g = reunitarize(1 + X) in the field precision R; the
+// Gram-Schmidt factors are FP64 in both.  FP64 fields take u = i1 r1 and
+// v = i2 w in FP64.  FP32 fields, whose rows are stored in FP32, apply the
+// FP64 factors in FP32: u = fl(i1) r1 with r1 the FP32 entries of the
+// filtered field itself, v = fl(i2) fl(w) -- within one FP32 rounding of the
+// FP64 product, and without the FP64 multiplies and most of the FP64 -> FP32
+// conversions of rounding each FP64 entry.
+template <typename R>
+__device__ __forceinline__ void gauge_rows(C2<R> f0, C2<R> f1, C2<R> f2, C2<R> f3, C2<R> u[3], C2<R> v[3]) {
+  GSFactors o;
+  gram_schmidt_factors((double)f0.x, (double)f0.y, ccast<double, R>(f1), ccast<double, R>(f2), ccast<double, R>(f3),
+                       o);
+  const R i1 = (R)o.i1, i2 = (R)o.i2;
+  u[0] = mkc<R>(i1, f0.x * i1);
+  u[1] = cscale<R>(f1, i1);
+  u[2] = cscale<R>(f2, i1);
+  if constexpr (sizeof(R) == sizeof(double)) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) v[j] = cscale<double>(o.w[j], o.i2);
+  } else {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) v[j] = cscale<R>(ccast<R, double>(o.w[j]), i2);
+  }
+}
+
 
 // Rows 1 and 2 of g = exp(X) (the exponential of Eq. (eq:gx) evaluated
 // exactly instead of to first order), for X traceless anti-Hermitian packed
@@ -589,29 +641,13 @@ __device__ __forceinline__ void gauge_exp_from_packed(double2 f0, double2 f1, do
   for (int j = 0; j < 3; ++j) v[j] = cscale<double>(v[j], i2);
 }
 
+// Stores rows u, v (precision RG) and, where needed, row 3 = (u x v)^*.
 template <typename RG, int GROWS>
-__device__ __forceinline__ void store_gauge(int64_t V, int64_t s, const double2 u[3], const double2 v[3],
-                                            C2<RG>* __restrict__ gf, C2<RG>* __restrict__ Gf) {
-  // rows 1-2 in the storage precision; row 3 = (a x b)^* in FP64 when g is
-  // stored in FP64, otherwise from the rounded rows in the storage precision
-  // (a 12-real FP32 update rebuilds it the same way)
-  C2<RG> a[3], b[3], c[3];
-#pragma unroll
-  for (int j = 0; j < 3; ++j) {
-    a[j] = ccast<RG, double>(u[j]);
-    b[j] = ccast<RG, double>(v[j]);
-  }
+__device__ __forceinline__ void store_gauge_rows(int64_t V, int64_t s, const C2<RG> a[3], const C2<RG> b[3],
+                                                 C2<RG>* __restrict__ gf, C2<RG>* __restrict__ Gf) {
+  C2<RG> c[3];
   const bool need_c = (GROWS == 3) || (Gf != nullptr);
-  if (need_c) {
-    if (sizeof(RG) == sizeof(double)) {
-      double2 w[3];
-      su3_third_row<double>(u, v, w);
-#pragma unroll
-      for (int j = 0; j < 3; ++j) c[j] = ccast<RG, double>(w[j]);
-    } else {
-      su3_third_row<RG>(a, b, c);
-    }
-  }
+  if (need_c) su3_third_row<RG>(a, b, c);
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
     gf[(0 * 3 + j) * V + s] = a[j];
@@ -638,6 +674,27 @@ __device__ __forceinline__ void store_gauge(int64_t V, int64_t s, const double2 
   }
 }
 
+// g(x) of one site from its packed filtered field and its store (and G <- g G).
+template <typename R, typename RG, int GROWS, bool EXPG>
+__device__ __forceinline__ void gauge_site(C2<R> f0, C2<R> f1, C2<R> f2, C2<R> f3, int64_t V, int64_t s,
+                                           C2<RG>* __restrict__ gf, C2<RG>* __restrict__ Gf) {
+  static_assert(sizeof(R) == sizeof(RG), "g is stored in the precision of the divergence");
+  C2<RG> a[3], b[3];
+  if constexpr (EXPG) {
+    double2 u[3], v[3];
+    gauge_exp_from_packed(ccast<double, R>(f0), ccast<double, R>(f1), ccast<double, R>(f2), ccast<double, R>(f3),
+                          u, v);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      a[j] = ccast<RG, double>(u[j]);
+      b[j] = ccast<RG, double>(v[j]);
+    }
+  } else {
+    gauge_rows<RG>(f0, f1, f2, f3, a, b);
+  }
+  store_gauge_rows<RG, GROWS>(V, s, a, b, gf, Gf);
+}
+
 template <typename R, typename RG, int GROWS, bool EXPG>
 __global__ void __launch_bounds__(512) fft_xy_inv_gauge_kernel(Geom g, FFTDir dx, FFTDir dy, const C2<R>* __restrict__ data,
                                         const C2<R>* __restrict__ twg, const short* __restrict__ posg,
@@ -657,22 +714,17 @@ __global__ void __launch_bounds__(512) fft_xy_inv_gauge_kernel(Geom g, FFTDir dx
   const int plane = Lx * Ly;
   for (int i = threadIdx.x; i < 4 * plane; i += blockDim.x) {
     const int f = (int)cd.a.div((uint32_t)i), r = i - f * plane, y = (int)cd.b.div((uint32_t)r), x = r - y * Lx;
-    tile[f * PS + y * RS + x] = data[(int64_t)f * g.V + slab * plane + r];
+    cp_async_elem<R>(&tile[f * PS + y * RS + x], &data[(int64_t)f * g.V + slab * plane + r]);
   }
+  cp_async_wait();
   __syncthreads();
   fft_lines_dif<R, +1>(tile, lx, dx, tw);
   fft_lines_dif<R, +1>(tile, ly, dy, tw + Lx);
   for (int i = threadIdx.x; i < plane; i += blockDim.x) {
     const int y = (int)cd.b.div((uint32_t)i), x = i - y * Lx;
     const int o = pos[Lx + y] * RS + pos[x];
-    double2 u[3], v[3];
-    if constexpr (EXPG)
-      gauge_exp_from_packed(ccast<double, R>(tile[o]), ccast<double, R>(tile[PS + o]),
-                            ccast<double, R>(tile[2 * PS + o]), ccast<double, R>(tile[3 * PS + o]), u, v);
-    else
-      gauge_from_packed(ccast<double, R>(tile[o]), ccast<double, R>(tile[PS + o]), ccast<double, R>(tile[2 * PS + o]),
-                        ccast<double, R>(tile[3 * PS + o]), u, v);
-    store_gauge<RG, GROWS>(g.V, slab * plane + i, u, v, gf, Gf);
+    gauge_site<R, RG, GROWS, EXPG>(tile[o], tile[PS + o], tile[2 * PS + o], tile[3 * PS + o], g.V, slab * plane + i, gf,
+                                   Gf);
   }
 }
 
@@ -687,14 +739,7 @@ __global__ void gauge_from_delta_kernel(Geom g, const C2<R>* __restrict__ data, 
   if (Gf != nullptr) Gf += blockIdx.z * B.s_G;
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= g.V) return;
-  double2 u[3], v[3];
-  if constexpr (EXPG)
-    gauge_exp_from_packed(ccast<double, R>(data[s]), ccast<double, R>(data[g.V + s]),
-                          ccast<double, R>(data[2 * g.V + s]), ccast<double, R>(data[3 * g.V + s]), u, v);
-  else
-    gauge_from_packed(ccast<double, R>(data[s]), ccast<double, R>(data[g.V + s]), ccast<double, R>(data[2 * g.V + s]),
-                      ccast<double, R>(data[3 * g.V + s]), u, v);
-  store_gauge<RG, GROWS>(g.V, s, u, v, gf, Gf);
+  gauge_site<R, RG, GROWS, EXPG>(data[s], data[g.V + s], data[2 * g.V + s], data[3 * g.V + s], g.V, s, gf, Gf);
 }
 
 // ---------------------------------------------------------------------------
@@ -929,8 +974,7 @@ cudaError_t launch_fft_xy(const Geom& g, const FFTPlan& p, C2<R>* data, const C2
 
 template <typename R>
 cudaError_t launch_fft_zt(const Geom& g, const FFTPlan& p, C2<R>* data, const C2<R>* tw, const short* pos,
-                          const R* K, int mode, int nfields, cudaStream_t s, const float* mtab, const int* use_m,
-                          const Batch& B) {
+                          const R* K, int mode, int nfields, cudaStream_t s, const LearnedIO& lio, const Batch& B) {
   const size_t smem = p.smem_zt;
   dim3 grid((unsigned)(g.L[0] / p.xc * g.L[1]), (unsigned)nfields, (unsigned)B.n);
   cudaError_t e = allow_smem(fft_zt_filter_kernel<R>, smem);
@@ -939,15 +983,14 @@ cudaError_t launch_fft_zt(const Geom& g, const FFTPlan& p, C2<R>* data, const C2
   const int xc = p.xc, Lz = g.L[2], Lt = g.L[3], TS = Lz * xc + 1;
   const Lines lz = make_lines(Lt * xc, xc, 1, TS, xc), lt = make_lines(Lz * xc, Lz * xc, 1, 0, TS);
   const CopyDiv cd{FastDiv::make((uint32_t)xc), FastDiv::make((uint32_t)Lz)};
-  fft_zt_filter_kernel<R><<<grid, p.threads_zt, smem, s>>>(g, p.d[2], p.d[3], data, tw, pos, K, p.xc, mode, mtab, H,
-                                                           use_m, lz, lt, cd, B);
+  fft_zt_filter_kernel<R><<<grid, p.threads_zt, smem, s>>>(g, p.d[2], p.d[3], data, tw, pos, K, p.xc, mode, lio, H,
+                                                           lz, lt, cd, B);
   return cudaGetLastError();
 }
 
 template <typename R>
 cudaError_t launch_fft_line(const Geom& g, const FFTPlan& p, int mu, C2<R>* data, const C2<R>* tw, const short* pos,
-                            const R* K, int mode, int nfields, cudaStream_t s, const Batch& B, const float* mtab,
-                            const int* use_m) {
+                            const R* K, int mode, int nfields, cudaStream_t s, const Batch& B, const LearnedIO& lio) {
   const int N = g.L[mu];
   LinePass lp;
   lp.N = N;
@@ -965,7 +1008,7 @@ cudaError_t launch_fft_line(const Geom& g, const FFTPlan& p, int mu, C2<R>* data
   const Lines ln = make_lines(lp.nl, lp.nl, N + 1, 0, 1);
   const int4 H = make_int4(g.L[0] / 2 + 1, g.L[1] / 2 + 1, g.L[2] / 2 + 1, g.L[3] / 2 + 1);
   fft_line_kernel<R><<<dim3((unsigned)blocks, (unsigned)nfields, (unsigned)B.n), p.threads_line[mu], smem, s>>>(
-      lp, p.d[mu], g, data, tw + off, pos + off, K, mode, ln, mtab, use_m, H, B);
+      lp, p.d[mu], g, data, tw + off, pos + off, K, mode, ln, lio, H, B);
   return cudaGetLastError();
 }
 
@@ -1036,11 +1079,9 @@ template cudaError_t launch_fft_xy<double>(const Geom&, const FFTPlan&, C2<doubl
 template cudaError_t launch_fft_xy<float>(const Geom&, const FFTPlan&, C2<float>*, const C2<float>*, const short*,
                                           int, int, cudaStream_t, const Batch&);
 template cudaError_t launch_fft_zt<double>(const Geom&, const FFTPlan&, C2<double>*, const C2<double>*, const short*,
-                                           const double*, int, int, cudaStream_t, const float*, const int*,
-                                           const Batch&);
+                                           const double*, int, int, cudaStream_t, const LearnedIO&, const Batch&);
 template cudaError_t launch_fft_zt<float>(const Geom&, const FFTPlan&, C2<float>*, const C2<float>*, const short*,
-                                          const float*, int, int, cudaStream_t, const float*, const int*,
-                                          const Batch&);
+                                          const float*, int, int, cudaStream_t, const LearnedIO&, const Batch&);
 #define LGF_INST_C(R, RG, GR)                                                                                    \
   template cudaError_t launch_fft_xy_inv_gauge<R, RG, GR>(const Geom&, const FFTPlan&, C2<R>*, const C2<R>*,      \
                                                           const short*, C2<RG>*, C2<RG>*, cudaStream_t, const Batch&, \
@@ -1058,8 +1099,7 @@ LGF_INST_G(float, float, 2)
 LGF_INST_G(float, float, 3)
 #define LGF_INST_ALT(R)                                                                                         \
   template cudaError_t launch_fft_line<R>(const Geom&, const FFTPlan&, int, C2<R>*, const C2<R>*, const short*, \
-                                          const R*, int, int, cudaStream_t, const Batch&, const float*,         \
-                                          const int*);                                                          \
+                                          const R*, int, int, cudaStream_t, const Batch&, const LearnedIO&);   \
   template cudaError_t launch_fft_xyz<R>(const Geom&, const FFTPlan&, C2<R>*, const C2<R>*, const short*, int,  \
                                          int, cudaStream_t, const Batch&);
 LGF_INST_ALT(double)

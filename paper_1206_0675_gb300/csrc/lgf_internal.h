@@ -39,6 +39,7 @@ struct DevState {
   int repaired;        // the links were reunitarised since the last counted measurement
   int* flag_hist;      // flags of measurement number i (TRACE_* bits) if i < hist_cap
   double* defect_hist; // defect of measurement number i if i < hist_cap
+  int snaps;           // learned handles: steps whose Fourier-space divergence snapshot is kept
 };
 
 enum { ST_OK = 0, ST_NONFINITE = 1, ST_DEFECT = 3 };
@@ -97,9 +98,10 @@ cudaError_t launch_update_measure(const Geom& g, C2<R>* U0, C2<R>* U1, const C2<
 
 // Undo of the last update when st->revert is set: U_mu(x) <- g^dag(x) U_mu(x)
 // g(x + mu^) and, when G is given (3 rows, precision R), G <- g^dag G.
+// links_alt (fused lanes): the second link buffer, used instead of links when st->ubuf is set.
 template <typename R, int LROWS, int GROWS>
 cudaError_t launch_revert(const Geom& g, C2<R>* links, const C2<R>* gfield, C2<R>* Gacc, const DevState* st,
-                          cudaStream_t s);
+                          cudaStream_t s, C2<R>* links_alt = nullptr);
 
 // U_mu(x) <- g(x) U_mu(x) g^dagger(x + mu^) in place (Sec. 2 eq. 2; kernel k6).
 // Links in precision R with LROWS stored rows; g in precision R with GROWS rows.
@@ -197,12 +199,24 @@ cudaError_t launch_fft_xy(const Geom& g, const FFTPlan& p, C2<R>* data, const C2
                           int nfields, cudaStream_t s, const Batch& B = Batch());
 // mode 0: forward (z,t) DFT, multiply by K, inverse (z,t) DFT (pass B);
 // mode -1 / +1: forward / inverse (z,t) DFT only (K unused).
-// mtab (may be NULL): learned multiplier per momentum class, applied when
-// *use_m != 0 (mode 0 only).
+// lio (mode 0 only): with lio.mtab the learned multiplier per momentum class
+// is applied when st->use_m != 0; with lio.snap the transformed divergence is
+// stored before the filter.
+// Learned handles' extras of the pass that carries the filter: the multiplier
+// table of step k is mtab + (k & 1) * nclass and the Fourier-space divergence
+// (before the filter) is stored, in FP32, in snap + (k & 1) * 4 V, with
+// k = st->iter read on the device.
+struct LearnedIO {
+  const float* mtab = nullptr;   // [2][nclass]
+  float2* snap = nullptr;        // [2][4][V]
+  const DevState* st = nullptr;  // st->use_m, st->iter
+  int64_t nclass = 0;
+};
+
 template <typename R>
 cudaError_t launch_fft_zt(const Geom& g, const FFTPlan& p, C2<R>* data, const C2<R>* tw, const short* pos,
-                          const R* K, int mode, int nfields, cudaStream_t s, const float* mtab = nullptr,
-                          const int* use_m = nullptr, const Batch& B = Batch());
+                          const R* K, int mode, int nfields, cudaStream_t s, const LearnedIO& lio = LearnedIO(),
+                          const Batch& B = Batch());
 // Inverse (x,y) transform fused with g(x) = reunitarize(1 + Delta'(x)) in FP64
 // (exact_exp != 0: g(x) = reunitarize(exp(Delta'(x)))); g stored with GROWS
 // rows in precision RG; optional G <- g G (precision RG with 3 rows).
@@ -212,12 +226,13 @@ cudaError_t launch_fft_xy_inv_gauge(const Geom& g, const FFTPlan& p, C2<R>* data
                                     int exact_exp = 0);
 
 // 1D pass along mu (0..3) over nfields fields: mode -1 forward, +1 inverse,
-// 0 forward, multiply by K (and by the learned table mtab when *use_m != 0),
+// 0 forward, multiply by K (and by the learned table when lio.mtab is given
+// and st->use_m != 0; snapshot of the transform when lio.snap is given),
 // inverse.
 template <typename R>
 cudaError_t launch_fft_line(const Geom& g, const FFTPlan& p, int mu, C2<R>* data, const C2<R>* tw, const short* pos,
                             const R* K, int mode, int nfields, cudaStream_t s, const Batch& B = Batch(),
-                            const float* mtab = nullptr, const int* use_m = nullptr);
+                            const LearnedIO& lio = LearnedIO());
 // 3D DFT over every (x, y, z) slab (requires p.fit_xyz); sign -1 / +1.
 template <typename R>
 cudaError_t launch_fft_xyz(const Geom& g, const FFTPlan& p, C2<R>* data, const C2<R>* tw, const short* pos, int sign,

@@ -1,7 +1,7 @@
 // Learned momentum-space multiplier m(k) (not in arXiv:1206.0675; an
 // addition on top of the filter alpha p2max/p2(k) of its Eq. (eq:gx)).
 //
-//   * inference: MLP 6 -> 64 -> 64 -> 64 -> 1 with BF16 weights and FP32
+//   * inference: MLP 8 -> 64 -> 64 -> 64 -> 1 with BF16 weights and FP32
 //     accumulation on the tensor cores (mma.sync m16n8k16), one warp per 16
 //     feature rows, hidden activations kept in registers between layers;
 //     evaluated once per iteration for the distinct momentum classes
@@ -172,54 +172,114 @@ __global__ void __launch_bounds__(128) mlp_eval_kernel(const __nv_bfloat16* __re
   }
 }
 
-// Multiplier of every momentum class of the lattice for the current
-// iteration: class c = ((ft Hz + fz) Hy + fy) Hx + fx with f = min(k, L - k)
-// and H = L/2 + 1; features from p2 = 4 sin^2(pi f / L), the stopping quantity
-// and the iteration count in the controller state.  Block 0 also decides
-// whether this step uses the table (not when it redoes a rejected step).
+// Multiplier of every momentum class of the lattice for the step that starts
+// from the current links (iteration k): class c = ((ft Hz + fz) Hy + fy) Hx + fx
+// with f = min(k, L - k) and H = L/2 + 1.  Features: p2 = 4 sin^2(pi f / L)
+// per direction, the theta bucket, the iteration fraction, the contraction
+// of theta over the last step, and the class's own contraction over the last
+// step whose two divergences are stored:
+//   r = 1 - (1 - r_obs) / m,  r_obs = sum Re<D^_{k-1}, D^_{k-2}> / sum |D^_{k-2}|^2
+// over the modes and packed fields of the class, m the multiplier that step
+// k - 2 applied to the class (the table of step k - 2, which this kernel then
+// overwrites), so that r is the contraction the plain filter would have given.
+// The four lanes that share a feature row gather one packed field each, in a
+// fixed order, and add their sums by shuffles (deterministic).  A step that
+// redoes a rejected one runs the plain filter: its table is all ones.
+// Block 0 also decides whether the step uses the table.
 __global__ void __launch_bounds__(128) mlp_multiplier_kernel(const __nv_bfloat16* __restrict__ P, MlpGeom mg,
-                                                             const float* __restrict__ p2, DevState* st,
-                                                             float* __restrict__ mtab) {
+                                                             Geom geo, const float* __restrict__ p2, DevState* st,
+                                                             float* __restrict__ mtab_base,
+                                                             const float2* __restrict__ snap) {
   __shared__ MlpSmem S;
   mlp_load_smem(S, P);
   const double theta = st->theta;
   const double theta_prev = st->theta_prev;
   const int iter = st->iter;
+  const int redo = st->revert;  // the measurement after the step assigns revert afresh
+  const bool have_rate = snap != nullptr && st->snaps >= 2;
   __syncthreads();
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    st->use_m = st->revert ? 0 : 1;
-    st->redo = st->revert;
-    st->revert = 0;
+    st->use_m = redo ? 0 : 1;
+    st->redo = redo;
   }
+  float* mtab = mtab_base + (int64_t)(iter & 1) * mg.nclass;
+  const int64_t V = geo.V;
+  const float2* sa = snap + (int64_t)((iter + 1) & 1) * 4 * V;  // divergence k - 1
+  const float2* sb = snap + (int64_t)(iter & 1) * 4 * V;        // divergence k - 2
   const float fb = theta > 0.0 ? (float)(floor(2.0 * log10(theta)) * 0.5) : -20.f;
   const float f4 = -fb / 16.f;
   const float f5 = fminf((float)iter / MLP_ITER_SCALE, 1.f);
   const float f6 = iter > 0 ? mlp_rate_feature(theta, theta_prev) : 0.f;
-  const int lane = threadIdx.x & 31, g = lane >> 2;
+  const int lane = threadIdx.x & 31, g = lane >> 2, tig = lane & 3;
   const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t n = mg.nclass;
   for (int64_t base = wid * 16; base < n; base += nw * 16) {
+    if (redo) {
+      if (tig == 0) {
+        if (base + g < n) mtab[base + g] = 1.f;
+        if (base + g + 8 < n) mtab[base + g + 8] = 1.f;
+      }
+      continue;
+    }
     float x[2][MLP_NIN];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       int64_t c = base + g + 8 * h;
       if (c >= n) c = n - 1;
-      const int fx = (int)(c % mg.H[0]); c /= mg.H[0];
-      const int fy = (int)(c % mg.H[1]); c /= mg.H[1];
-      const int fz = (int)(c % mg.H[2]); c /= mg.H[2];
-      const int ft = (int)c;
-      x[h][0] = 0.25f * p2[fx];
-      x[h][1] = 0.25f * p2[mg.off[1] + fy];
-      x[h][2] = 0.25f * p2[mg.off[2] + fz];
-      x[h][3] = 0.25f * p2[mg.off[3] + ft];
+      const int64_t cls = c;
+      int f[4];
+      f[0] = (int)(c % mg.H[0]); c /= mg.H[0];
+      f[1] = (int)(c % mg.H[1]); c /= mg.H[1];
+      f[2] = (int)(c % mg.H[2]); c /= mg.H[2];
+      f[3] = (int)c;
+      x[h][0] = 0.25f * p2[f[0]];
+      x[h][1] = 0.25f * p2[mg.off[1] + f[1]];
+      x[h][2] = 0.25f * p2[mg.off[2] + f[2]];
+      x[h][3] = 0.25f * p2[mg.off[3] + f[3]];
       x[h][4] = f4;
       x[h][5] = f5;
       x[h][6] = f6;
+      float r = 0.f;
+      if (have_rate) {
+        // the modes k_mu in {f_mu, L_mu - f_mu} of the class; this lane takes packed field tig
+        float ip = 0.f, nb = 0.f;
+        for (int bt = 0; bt < 2; ++bt) {
+          if (bt && (f[3] == 0 || 2 * f[3] == geo.L[3])) continue;
+          const int kt = bt ? geo.L[3] - f[3] : f[3];
+          for (int bz = 0; bz < 2; ++bz) {
+            if (bz && (f[2] == 0 || 2 * f[2] == geo.L[2])) continue;
+            const int kz = bz ? geo.L[2] - f[2] : f[2];
+            for (int by = 0; by < 2; ++by) {
+              if (by && (f[1] == 0 || 2 * f[1] == geo.L[1])) continue;
+              const int ky = by ? geo.L[1] - f[1] : f[1];
+              for (int bx = 0; bx < 2; ++bx) {
+                if (bx && (f[0] == 0 || 2 * f[0] == geo.L[0])) continue;
+                const int kx = bx ? geo.L[0] - f[0] : f[0];
+                const int64_t sidx = (int64_t)tig * V + kx + geo.stride[1] * ky + geo.stride[2] * kz +
+                                     geo.stride[3] * kt;
+                const float2 va = __ldg(&sa[sidx]), vb = __ldg(&sb[sidx]);
+                ip = fmaf(va.x, vb.x, fmaf(va.y, vb.y, ip));
+                nb = fmaf(vb.x, vb.x, fmaf(vb.y, vb.y, nb));
+              }
+            }
+          }
+        }
+        ip += __shfl_xor_sync(0xffffffffu, ip, 1);
+        nb += __shfl_xor_sync(0xffffffffu, nb, 1);
+        ip += __shfl_xor_sync(0xffffffffu, ip, 2);
+        nb += __shfl_xor_sync(0xffffffffu, nb, 2);
+        if (nb > 0.f) {
+          const float m_prev = mtab[cls];
+          r = 1.f - (1.f - ip / nb) / m_prev;
+          r = fminf(fmaxf(r, -1.f), 1.f);
+        }
+      }
+      x[h][7] = r;
     }
     float z0, z1;
     mlp_tile(S, x[0], x[1], z0, z1);
-    if ((lane & 3) == 0) {
+    if (tig == 0) {
       const int64_t r0 = base + g, r1 = base + g + 8;
       if (r0 < n) mtab[r0] = fminf(fmaxf(softplusf(z0), mg.m_lo), mg.m_hi);
       if (r1 < n) mtab[r1] = fminf(fmaxf(softplusf(z1), mg.m_lo), mg.m_hi);
@@ -234,12 +294,12 @@ cudaError_t launch_mlp_eval(const uint16_t* P, const float* X, int64_t n, float*
   return cudaGetLastError();
 }
 
-cudaError_t launch_mlp_multiplier(const uint16_t* P, const MlpGeom& mg, const float* p2, DevState* st, float* mtab,
-                                  cudaStream_t s) {
+cudaError_t launch_mlp_multiplier(const uint16_t* P, const MlpGeom& mg, const Geom& g, const float* p2, DevState* st,
+                                  float* mtab, const float2* snap, cudaStream_t s) {
   const int64_t warps = (mg.nclass + 15) / 16;
   const unsigned blocks = (unsigned)std::min<int64_t>((warps + 3) / 4, 152 * 4);
-  mlp_multiplier_kernel<<<blocks > 0 ? blocks : 1, 128, 0, s>>>(reinterpret_cast<const __nv_bfloat16*>(P), mg, p2,
-                                                               st, mtab);
+  mlp_multiplier_kernel<<<blocks > 0 ? blocks : 1, 128, 0, s>>>(reinterpret_cast<const __nv_bfloat16*>(P), mg, g, p2,
+                                                               st, mtab, snap);
   return cudaGetLastError();
 }
 
@@ -490,7 +550,8 @@ cudaError_t launch_f32_to_bf16(const float* in, uint16_t* out, int n, cudaStream
 // rate feature belong to the links of prev.
 template <typename R>
 __global__ void mode_log_kernel(Geom g, MlpGeom mg, const C2<R>* __restrict__ cur, const C2<R>* __restrict__ prev,
-                                const LogState* __restrict__ ls, double* __restrict__ stats) {
+                                const C2<R>* __restrict__ prev2, const LogState* __restrict__ ls,
+                                double* __restrict__ stats) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= g.V || !ls->have_prev) return;
   const int bucket = mlp_bucket_index(ls->theta_prev);
@@ -503,12 +564,18 @@ __global__ void mode_log_kernel(Geom g, MlpGeom mg, const C2<R>* __restrict__ cu
     const int f = min(c[mu], g.L[mu] - c[mu]);
     cls = cls * mg.H[mu] + f;
   }
-  double num = 0.0, den = 0.0;
+  double num = 0.0, den = 0.0, num_lag = 0.0, den_lag = 0.0;
+  const bool lag = ls->have_prev2 != 0;
 #pragma unroll
   for (int f = 0; f < 4; ++f) {
     const C2<R> a = cur[f * g.V + s], b = prev[f * g.V + s];
     num += (double)a.x * b.x + (double)a.y * b.y;
     den += (double)b.x * b.x + (double)b.y * b.y;
+    if (lag) {
+      const C2<R> c = prev2[f * g.V + s];
+      num_lag += (double)b.x * c.x + (double)b.y * c.y;
+      den_lag += (double)c.x * c.x + (double)c.y * c.y;
+    }
   }
   double* row = stats + ((int64_t)bucket * mg.nclass + cls) * MLP_NSTAT;
   atomicAdd(row, num);
@@ -516,16 +583,21 @@ __global__ void mode_log_kernel(Geom g, MlpGeom mg, const C2<R>* __restrict__ cu
   atomicAdd(row + 2, 1.0);
   atomicAdd(row + 3, (double)iter_frac);
   atomicAdd(row + 4, (double)rate);
+  if (lag) {
+    atomicAdd(row + 5, num_lag);
+    atomicAdd(row + 6, den_lag);
+  }
 }
 
 template <typename R>
 cudaError_t launch_mode_log(const Geom& g, const MlpGeom& mg, const C2<R>* cur, const C2<R>* prev,
-                            const LogState* ls, double* stats, cudaStream_t s) {
-  mode_log_kernel<R><<<(unsigned)((g.V + 255) / 256), 256, 0, s>>>(g, mg, cur, prev, ls, stats);
+                            const C2<R>* prev2, const LogState* ls, double* stats, cudaStream_t s) {
+  mode_log_kernel<R><<<(unsigned)((g.V + 255) / 256), 256, 0, s>>>(g, mg, cur, prev, prev2, ls, stats);
   return cudaGetLastError();
 }
 
 __global__ void log_state_update_kernel(LogState* ls, const DevState* st) {
+  ls->have_prev2 = ls->have_prev;
   ls->theta_prev2 = ls->have_prev ? ls->theta_prev : 0.0;
   ls->theta_prev = st->theta;
   ls->iter_prev = st->iter;
@@ -538,8 +610,8 @@ cudaError_t launch_log_state_update(LogState* ls, const DevState* st, cudaStream
 }
 
 template cudaError_t launch_mode_log<double>(const Geom&, const MlpGeom&, const C2<double>*, const C2<double>*,
-                                             const LogState*, double*, cudaStream_t);
+                                             const C2<double>*, const LogState*, double*, cudaStream_t);
 template cudaError_t launch_mode_log<float>(const Geom&, const MlpGeom&, const C2<float>*, const C2<float>*,
-                                            const LogState*, double*, cudaStream_t);
+                                            const C2<float>*, const LogState*, double*, cudaStream_t);
 
 }  // namespace lgf

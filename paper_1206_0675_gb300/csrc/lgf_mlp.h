@@ -8,12 +8,13 @@
 
 namespace lgf {
 
-// 7 -> 64 -> 64 -> 64 -> 1, flat parameter layout (row-major [out][in]):
-constexpr int MLP_NIN = 7, MLP_NH = 64;
-constexpr int MLP_OFF_W1 = 0, MLP_OFF_B1 = 448, MLP_OFF_W2 = 512, MLP_OFF_B2 = 4608;
-constexpr int MLP_OFF_W3 = 4672, MLP_OFF_B3 = 8768, MLP_OFF_W4 = 8832, MLP_OFF_B4 = 8896;
-constexpr int MLP_NPARAM = 8897;
-constexpr int MLP_NSTAT = 5;               // mode-log sums per (bucket, class)
+// 8 -> 64 -> 64 -> 64 -> 1, flat parameter layout (row-major [out][in]):
+constexpr int MLP_NIN = 8, MLP_NH = 64;
+constexpr int MLP_OFF_W1 = 0, MLP_OFF_B1 = 512, MLP_OFF_W2 = 576, MLP_OFF_B2 = 4672;
+constexpr int MLP_OFF_W3 = 4736, MLP_OFF_B3 = 8832, MLP_OFF_W4 = 8896, MLP_OFF_B4 = 8960;
+constexpr int MLP_NPARAM = 8961;
+constexpr int MLP_NSTAT = 7;               // mode-log sums per (bucket, class)
+constexpr float MLP_M_LO = 0.25f, MLP_M_HI = 2.0f;  // clamp of the multiplier
 constexpr float MLP_ITER_SCALE = 10000.f;  // iter_frac = min(iter / 10000, 1)
 constexpr int MLP_NBUCKET = 40;            // theta buckets of the mode log
 
@@ -36,8 +37,16 @@ __host__ __device__ inline int mlp_bucket_index(double theta) {
 }
 
 cudaError_t launch_mlp_eval(const uint16_t* P, const float* X, int64_t n, float* out, cudaStream_t s);
-cudaError_t launch_mlp_multiplier(const uint16_t* P, const MlpGeom& mg, const float* p2, DevState* st, float* mtab,
-                                  cudaStream_t s);
+// Multiplier of every momentum class for the step that starts from the
+// current links (iteration k = st->iter), written to mtab + (k & 1) * nclass
+// (the table of step k - 2 before: its entries turn the observed contraction
+// into the plain-filter one).  snap: the two Fourier-space divergence
+// snapshots [2][4][V] (FP32) that the filter passes write, slot k & 1 at step
+// k; with st->snaps >= 2 the class contraction of the last step is formed
+// from slots (k - 1) & 1 (divergence k - 1) and k & 1 (divergence k - 2).
+// A step that redoes a rejected one writes m = 1 (the plain filter it uses).
+cudaError_t launch_mlp_multiplier(const uint16_t* P, const MlpGeom& mg, const Geom& g, const float* p2, DevState* st,
+                                  float* mtab, const float2* snap, cudaStream_t s);
 size_t mlp_train_smem();
 cudaError_t launch_mlp_grad(const float* P, const float* X, const float* Y, const float* Wt, int64_t n, int64_t batch,
                             uint64_t seed, int step, float inv_sw, float* part_g, double* part_l, int nblocks,
@@ -51,6 +60,7 @@ struct LogState {
   double theta_prev2;  // theta one step earlier (0 if none)
   int iter_prev;
   int have_prev;
+  int have_prev2;      // the divergence before "previous" is stored too
 };
 
 // Seventh feature: the last step's contraction, clamp(log10(theta/theta_prev), -2, 1)/2
@@ -61,9 +71,11 @@ __host__ __device__ inline float mlp_rate_feature(double theta, double theta_pre
   r = r < -2.0 ? -2.0 : (r > 1.0 ? 1.0 : r);
   return (float)(0.5 * r);
 }
+// prev2 (may hold anything while ls->have_prev2 == 0): the divergence one
+// step before prev, for the class contraction of the previous step.
 template <typename R>
 cudaError_t launch_mode_log(const Geom& g, const MlpGeom& mg, const C2<R>* cur, const C2<R>* prev,
-                            const LogState* ls, double* stats, cudaStream_t s);
+                            const C2<R>* prev2, const LogState* ls, double* stats, cudaStream_t s);
 cudaError_t launch_log_state_update(LogState* ls, const DevState* st, cudaStream_t s);
 
 }  // namespace lgf

@@ -128,6 +128,7 @@ __device__ __forceinline__ void measure_tail(const Geom& g, double fsum, double 
       it -= 1;
       st->iter = it;
     }
+    st->snaps += count_iter;  // a rejected step's snapshot is replaced by its redo
     st->F = F;
     st->theta = th;
     st->defect = d;
@@ -427,8 +428,10 @@ cudaError_t launch_update(const Geom& g, C2<R>* links, const C2<R>* gfield, cuda
 
 template <typename R, int LROWS, int GROWS>
 __global__ void __launch_bounds__(UPDATE_THREADS)
-revert_kernel(Geom g, MatField<R, LROWS> U, MatField<R, GROWS> Gf, MatField<R, 3> Gacc, const DevState* st) {
+revert_kernel(Geom g, MatField<R, LROWS> U, MatField<R, GROWS> Gf, MatField<R, 3> Gacc, const DevState* st,
+              C2<R>* links_alt) {
   if (!st->revert) return;
+  if (links_alt != nullptr && st->ubuf) U.p = links_alt;  // the current buffer of a fused lane
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= g.V) return;
   int c[4];
@@ -479,12 +482,12 @@ revert_kernel(Geom g, MatField<R, LROWS> U, MatField<R, GROWS> Gf, MatField<R, 3
 
 template <typename R, int LROWS, int GROWS>
 cudaError_t launch_revert(const Geom& g, C2<R>* links, const C2<R>* gfield, C2<R>* Gacc, const DevState* st,
-                          cudaStream_t s) {
+                          cudaStream_t s, C2<R>* links_alt) {
   MatField<R, LROWS> U{links, g.V};
   MatField<R, GROWS> Gf{const_cast<C2<R>*>(gfield), g.V};
   MatField<R, 3> Ga{Gacc, g.V};
   const int64_t nb = (g.V + UPDATE_THREADS - 1) / UPDATE_THREADS;
-  revert_kernel<R, LROWS, GROWS><<<(unsigned)nb, UPDATE_THREADS, 0, s>>>(g, U, Gf, Ga, st);
+  revert_kernel<R, LROWS, GROWS><<<(unsigned)nb, UPDATE_THREADS, 0, s>>>(g, U, Gf, Ga, st, links_alt);
   return cudaGetLastError();
 }
 
@@ -695,6 +698,7 @@ __global__ void set_state_kernel(DevState* st, double tol, int max_iter, int res
     st->n_fallback = 0;
     st->redo = 0;
     st->repaired = 0;
+    st->snaps = 0;
   }
   st->hist_cap = hist_cap;
   st->F_hist = Fh;
@@ -839,13 +843,13 @@ LGF_INST_R_ROWS(float, 3)
 LGF_INST_R_ROWS(float, 2)
 
 template cudaError_t launch_revert<double, 3, 3>(const Geom&, C2<double>*, const C2<double>*, C2<double>*,
-                                                 const DevState*, cudaStream_t);
+                                                 const DevState*, cudaStream_t, C2<double>*);
 template cudaError_t launch_revert<double, 2, 3>(const Geom&, C2<double>*, const C2<double>*, C2<double>*,
-                                                 const DevState*, cudaStream_t);
+                                                 const DevState*, cudaStream_t, C2<double>*);
 template cudaError_t launch_revert<float, 2, 2>(const Geom&, C2<float>*, const C2<float>*, C2<float>*,
-                                                const DevState*, cudaStream_t);
+                                                 const DevState*, cudaStream_t, C2<float>*);
 template cudaError_t launch_revert<float, 3, 3>(const Geom&, C2<float>*, const C2<float>*, C2<float>*,
-                                                const DevState*, cudaStream_t);
+                                                 const DevState*, cudaStream_t, C2<float>*);
 template cudaError_t launch_update<double, 3, 3>(const Geom&, C2<double>*, const C2<double>*, cudaStream_t, const Batch&);
 template cudaError_t launch_update<double, 2, 3>(const Geom&, C2<double>*, const C2<double>*, cudaStream_t, const Batch&);
 template cudaError_t launch_update<float, 2, 2>(const Geom&, C2<float>*, const C2<float>*, cudaStream_t, const Batch&);

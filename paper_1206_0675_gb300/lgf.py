@@ -32,9 +32,9 @@ LGF_FP64, LGF_FP32, LGF_MIXED = 0, 1, 2
 LGF_STORE18, LGF_STORE12, LGF_TRACK_G, LGF_LEARNED, LGF_PLAIN_SD, LGF_EXACT_EXP = 0, 1, 2, 4, 8, 16
 LGF_FFT_2D2D, LGF_FFT_1D4, LGF_FFT_3D1D = 0, 1, 2
 LGF_TRACE_FP64, LGF_TRACE_LEARNED, LGF_TRACE_REDO, LGF_TRACE_REPAIRED = 1, 2, 4, 8
-LGF_MLP_NPARAM = 8897
+LGF_MLP_NPARAM = 8961
 MLP_NBUCKET = 40
-MLP_NSTAT = 5
+MLP_NSTAT = 7
 LGF_HOST, LGF_DEVICE = 0, 1
 
 _c_int_p = ctypes.POINTER(ctypes.c_int32)
@@ -607,7 +607,7 @@ class Lattice:
         return lgf_get_timing(self.handle)
 
     def load_preconditioner(self, weights_bf16) -> None:
-        """weights_bf16: uint16 numpy array (host) or CUDA tensor (int16/uint16/bfloat16) of 8897 values."""
+        """weights_bf16: uint16 numpy array (host) or CUDA tensor (int16/uint16/bfloat16) of 8961 values."""
         if _is_torch_cuda(weights_bf16):
             lgf_load_preconditioner(self.handle, weights_bf16.data_ptr(), LGF_MLP_NPARAM, LGF_DEVICE)
         else:

@@ -10,8 +10,7 @@ and momentum class c the log gives
 (D^ the 4D Fourier transform of the packed divergence), the per-step
 contraction of that class under the plain filter.  The training target is
 the multiplier that would remove it in one step in a linear model,
-m* = 1/(1 - r), clamped to [0.25, 1.25] (1.25 is the largest uniform
-multiplier that kept plain FA-SD stable on these fields).  The linear model
+m* = 1/(1 - r), clamped to [0.25, 2].  The linear model
 holds only once the gauge transformations are small: for theta >= 1e-4
 (the first, non-linear part of every trajectory, where a uniformly larger
 step was measured to slow fast-converging fields) the target is the plain
@@ -20,11 +19,16 @@ The loss is the mean square error of log m, weighted by |D^_k|^2
 normalised within each (configuration, bucket).
 
 Features (identical to the ones the inference kernel builds):
-    (p2_x/4, p2_y/4, p2_z/4, p2_t/4, -bucket/16, iter_frac, rate)
+    (p2_x/4, p2_y/4, p2_z/4, p2_t/4, -bucket/16, iter_frac, rate, r_class)
 with p2_mu = 4 sin^2(pi f_mu / L_mu), bucket = floor(2 log10 theta)/2 of the
-step's starting links, iter_frac = min(iteration / 10000, 1) and
+step's starting links, iter_frac = min(iteration / 10000, 1),
 rate = clamp(log10(theta/theta_prev), -2, 1)/2 the contraction of theta over
-the previous step (0 on the first step), averaged over the steps of a bucket.
+the previous step (0 on the first step), averaged over the steps of a bucket,
+and r_class = sum Re<D^_k, D^_{k-1}> / sum |D^_{k-1}|^2 the class's own
+contraction over the previous step (summed over the steps of the bucket,
+clamped to [-1, 1]; 0 where the previous step is not logged).  The inference
+kernel forms the same quantity one step later than the step it predicts for,
+from the divergences it keeps.
 
 The network is trained with Adam by ``lgf_mlp_train`` (FP32 forward and
 backward kernels of liblgf) and stored as BF16 (``lgf_mlp_to_bf16``).
@@ -45,7 +49,7 @@ from . import fields, lgf
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_WEIGHTS = os.path.join(HERE, "preconditioner_bf16.npy")
-M_LO, M_HI = 0.25, 1.25
+M_LO, M_HI = 0.25, 2.0
 THETA_LINEAR = 1e-4
 NPARAM = lgf.LGF_MLP_NPARAM
 
@@ -66,30 +70,32 @@ def targets(r: np.ndarray, bucket: np.ndarray) -> np.ndarray:
 
 
 def samples_from_log(extents, stats: np.ndarray, rng: np.random.Generator, per_bucket: int = 256):
-    """(X, r, w) rows from one configuration's mode log [bucket][class][4]: features,
+    """(X, r, w) rows from one configuration's mode log [bucket][class][7]: features,
     logged contraction ratio and weight.  Buckets below theta = 1e-15 are left out."""
     p2 = class_p2(extents)
     X, Rr, W = [], [], []
     for b in range(stats.shape[0]):
         if (4 - b) / 2.0 < -15.0:
             continue
-        num, den, cnt, itf, rate = stats[b].T
+        num, den, cnt, itf, rate, num_lag, den_lag = stats[b].T
         ok = np.nonzero((cnt > 0) & (den > 0))[0]
         if ok.size == 0:
             continue
         if ok.size > per_bucket:
             ok = rng.choice(ok, per_bucket, replace=False)
         bucket = (4 - b) / 2.0
-        x = np.empty((ok.size, 7))
+        x = np.empty((ok.size, 8))
         x[:, :4] = p2[ok] / 4.0
         x[:, 4] = -bucket / 16.0
         x[:, 5] = np.minimum(itf[ok] / cnt[ok], 1.0)
         x[:, 6] = rate[ok] / cnt[ok]
+        with np.errstate(divide="ignore", invalid="ignore"):
+            x[:, 7] = np.where(den_lag[ok] > 0, np.clip(num_lag[ok] / den_lag[ok], -1.0, 1.0), 0.0)
         X.append(x)
         Rr.append(num[ok] / den[ok])
         W.append(den[ok] / den[ok].sum())
     if not X:
-        return np.zeros((0, 7)), np.zeros(0), np.zeros(0)
+        return np.zeros((0, 8)), np.zeros(0), np.zeros(0)
     return np.concatenate(X), np.concatenate(Rr), np.concatenate(W)
 
 
@@ -114,10 +120,10 @@ def init_params(seed: int) -> np.ndarray:
     """He initialisation; the output layer starts at zero with b4 = log(e - 1) (m = 1)."""
     rng = np.random.Generator(np.random.Philox(key=seed + 7))
     p = np.zeros(NPARAM, dtype=np.float32)
-    p[0:448] = rng.standard_normal(448) * np.sqrt(2.0 / 7)
-    p[512:4608] = rng.standard_normal(4096) * np.sqrt(2.0 / 64)
-    p[4672:8768] = rng.standard_normal(4096) * np.sqrt(2.0 / 64)
-    p[8896] = np.log(np.e - 1.0)
+    p[0:512] = rng.standard_normal(512) * np.sqrt(2.0 / 8)
+    p[576:4672] = rng.standard_normal(4096) * np.sqrt(2.0 / 64)
+    p[4736:8832] = rng.standard_normal(4096) * np.sqrt(2.0 / 64)
+    p[8960] = np.log(np.e - 1.0)
     return p
 
 

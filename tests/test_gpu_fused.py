@@ -90,9 +90,28 @@ def test_fused_fix_against_oracle_and_mixed():
     assert abs(O.plaquette(U1) - O.plaquette(U)) < 1e-12
 
 
-def test_learned_handles_refuse_fusion():
-    with lgf.Lattice((4, 4, 4, 4), "fp32", learned=True) as lat:
-        with pytest.raises(lgf.LgfError) as e:
-            lat.set_fused_update(True)
-        assert e.value.status == lgf.LGF_E_UNSUPPORTED
-        lat.set_fused_update(False)
+def test_learned_handles_fuse_bit_identically():
+    """A learned FP32 handle runs the fused update + measure: with a constant
+    multiplier of 2 and alpha scaled by 1.6 steps are rejected, undone on the
+    current link buffer and redone, and the run equals the unfused one bit
+    for bit (histories, fallbacks, links, transform)."""
+    from oracle import lgf_mlp_oracle as M
+    p = np.zeros(M.NPARAM)
+    p[M.OFF_B4] = 3.0
+    bits = (M.bf16_round(p).astype(np.float32).view(np.uint32) >> 16).astype(np.uint16)
+    ext = (6, 4, 8, 4)
+    U = fields.random_links(ext, eps=0.9, seed=21)
+    out = []
+    for fused in (True, False):
+        with lgf.Lattice(ext, "fp32", store12=True, track_G=True, learned=True) as lat:
+            lat.set_fused_update(fused)
+            lat.load_preconditioner(bits)
+            lat.set_links(U)
+            Fh, Th, Fl, Dh = lat.set_trace(31, flags=True)
+            it, F, th, conv = lat.fix(0.0, 30, 0.128)
+            out.append((it, lat.fallbacks(), Fh.copy(), Th.copy(), Fl.copy(), lat.get_links(), lat.get_transform()))
+    a, b = out
+    assert a[0] == b[0] == 30 and a[1] == b[1] and a[1] > 0
+    for x, y in zip(a[2:], b[2:]):
+        assert np.array_equal(x, y)
+    assert np.count_nonzero(a[4] & lgf.LGF_TRACE_REDO) == a[1]

@@ -98,7 +98,7 @@ def test_inference_matches_bf16_oracle_row_by_row(torch):
     roundings of its doubtful activations."""
     rng = np.random.default_rng(0)
     p = random_params(0)
-    X = rng.random((1000 + 13, 7))  # ragged tail: not a multiple of the 16-row tile
+    X = rng.random((1000 + 13, 8))  # ragged tail: not a multiple of the 16-row tile
     m_gpu = gpu_eval(torch, bf16_bits(p), X)
     W1, b1, W2, b2, W3, b3, w4, b4 = M.unpack(M.bf16_round(p))
     Xb = M.bf16_round(X)
@@ -107,7 +107,7 @@ def test_inference_matches_bf16_oracle_row_by_row(torch):
         a1 = W1 @ Xb[i] + b1
         S1 = np.abs(W1) @ np.abs(Xb[i]) + np.abs(b1)
         best = np.inf
-        opts1 = _rounding_options(a1, S1, 8, 6)
+        opts1 = _rounding_options(a1, S1, 9, 6)
         assert opts1 is not None, i
         for h1 in opts1:
             a2 = W2 @ h1 + b2
@@ -128,7 +128,7 @@ def test_gradient_matches_oracle(torch):
     rng = np.random.default_rng(1)
     p = random_params(1).astype(np.float32)
     n = 777
-    X = rng.random((n, 7)).astype(np.float32)
+    X = rng.random((n, 8)).astype(np.float32)
     Y = (rng.standard_normal(n) * 0.2).astype(np.float32)
     W = rng.random(n) + 0.2
     W = (W / W.mean()).astype(np.float32)
@@ -147,7 +147,7 @@ def test_gradient_matches_oracle(torch):
 def test_training_reduces_loss(torch):
     rng = np.random.default_rng(2)
     n = 20000
-    X = rng.random((n, 7)).astype(np.float32)
+    X = rng.random((n, 8)).astype(np.float32)
     Y = (0.15 * np.sin(3 * X[:, 0]) - 0.1 * X[:, 4] + 0.05 * X[:, 5]).astype(np.float32)
     W = np.ones(n, dtype=np.float32)
     dev = torch.device("cuda")
@@ -193,13 +193,13 @@ def oracle_learned_fix(U, K, m, n_steps):
 
 @pytest.mark.parametrize("alpha_scale,z0", [(1.0, 0.7), (1.6, 3.0)])
 def test_learned_constant_multiplier_and_fallback_match_oracle(torch, alpha_scale, z0):
-    """z0 = 0.7: m = softplus(0.7) = 1.10, no fallback.  z0 = 3: m clamps to 1.25 and,
+    """z0 = 0.7: m = softplus(0.7) = 1.10, no fallback.  z0 = 3: m clamps to 2 and,
     with alpha scaled by 1.6, steps overshoot and are redone with the plain filter."""
     ext = (6, 4, 8, 4)
     alpha = 0.08 * alpha_scale
     U = fields.random_links(ext, eps=0.9, seed=21)
     bits = constant_multiplier_bits(z0)
-    m = float(np.clip(gpu_eval(torch, bits, np.zeros((1, 7)))[0], 0.25, 1.25))
+    m = float(np.clip(gpu_eval(torch, bits, np.zeros((1, 8)))[0], 0.25, 2.0))
     n = 30
     with lgf.Lattice(ext, "fp64", learned=True) as lat:
         lat.load_preconditioner(bits)
@@ -258,6 +258,7 @@ def test_mode_log_matches_oracle(torch):
     Ucur = U
     F, th, D = O.measure(Ucur)
     prev = packed_hat(D)
+    prev2 = None
     th_before = 0.0
     for k in range(steps):
         b = int(np.clip(4 - 2 * np.floor(2 * np.log10(th)) / 2, 0, 39))
@@ -271,13 +272,19 @@ def test_mode_log_matches_oracle(torch):
         ref[b, :, 2] += np.bincount(cls.ravel(), minlength=nclass)
         ref[b, :, 3] += np.bincount(cls.ravel(), minlength=nclass) * min(k / 10000.0, 1.0)
         ref[b, :, 4] += np.bincount(cls.ravel(), minlength=nclass) * (M.rate_feature(th, th_before) if k else 0.0)
-        prev, th_before, th = cur, th, th_new
+        if prev2 is not None:
+            ref[b, :, 5] += np.bincount(cls.ravel(), np.sum(np.real(np.conj(prev2) * prev), axis=0).ravel(), nclass)
+            ref[b, :, 6] += np.bincount(cls.ravel(), np.sum(np.abs(prev2) ** 2, axis=0).ravel(), nclass)
+        prev2, prev, th_before, th = prev, cur, th, th_new
     scale = np.max(np.abs(ref[..., 1]))
     assert np.array_equal(stats[..., 2], ref[..., 2])
     assert np.max(np.abs(stats[..., 0] - ref[..., 0])) < 1e-10 * scale
     assert np.max(np.abs(stats[..., 1] - ref[..., 1])) < 1e-10 * scale
     assert np.max(np.abs(stats[..., 3] - ref[..., 3])) < 1e-6
     assert np.max(np.abs(stats[..., 4] - ref[..., 4])) < 1e-3
+    assert np.max(np.abs(stats[..., 5] - ref[..., 5])) < 1e-10 * scale
+    assert np.max(np.abs(stats[..., 6] - ref[..., 6])) < 1e-10 * scale
+    assert np.any(ref[..., 6] > 0)
 
 
 def test_trained_preconditioner_gains_on_slow_fields(torch):

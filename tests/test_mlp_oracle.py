@@ -18,13 +18,13 @@ def random_params(seed):
 
 def test_parameter_layout_roundtrip():
     p = random_params(0)
-    assert p.size == M.NPARAM == 8897
+    assert p.size == M.NPARAM == 8961
     assert np.array_equal(M.pack(*M.unpack(p)), p)
 
 
 def test_initial_network_is_the_plain_filter():
     p = M.init_params(3)
-    X = np.random.default_rng(0).random((50, 7))
+    X = np.random.default_rng(0).random((50, 8))
     m, _ = M.forward(p, X)
     assert np.allclose(m, 1.0, rtol=0, atol=1e-15)
 
@@ -32,7 +32,7 @@ def test_initial_network_is_the_plain_filter():
 def test_gradient_against_central_differences():
     rng = np.random.default_rng(1)
     p = random_params(1)
-    X = rng.random((40, 7))
+    X = rng.random((40, 8))
     Y = rng.standard_normal(40) * 0.2
     Wt = rng.random(40) + 0.1
     loss, g = M.loss_and_grad(p, X, Y, Wt)
@@ -60,9 +60,11 @@ def test_targets_and_features():
     r = np.array([0.0, 0.5, -0.28, 0.993, 1.2, -5.0])
     m = np.exp(M.targets_from_stats(r, np.ones_like(r)))
     assert np.allclose(m, [1.0, M.M_HI, 1 / 1.28, M.M_HI, M.M_HI, M.M_LO])
-    x = M.features([[0.0, 4.0, 2.0, 1.0]], 3e-10, 2500, 3e-9)
-    assert np.allclose(x, [[0.0, 1.0, 0.5, 0.25, 10.0 / 16.0, 0.25, -0.5]])
+    x = M.features([[0.0, 4.0, 2.0, 1.0]], 3e-10, 2500, 3e-9, 0.75)
+    assert np.allclose(x, [[0.0, 1.0, 0.5, 0.25, 10.0 / 16.0, 0.25, -0.5, 0.75]])
     assert M.features([[1, 1, 1, 1]], 1e-3, 0, 1e-1)[0, 6] == 0.0  # no previous step
+    x2 = M.features([[1, 1, 1, 1], [2, 2, 2, 2]], 1e-3, 5, 1e-2, [3.0, -7.0])
+    assert np.array_equal(x2[:, 7], [1.0, -1.0])                     # class contraction clamped
     assert M.rate_feature(1e-9, 1e-3) == -1.0 and M.rate_feature(1e-3, 1e-9) == 0.5
     assert M.theta_bucket(1e-9) == -9.0 and M.theta_bucket(0.0) == -20.0
 
