@@ -181,17 +181,20 @@ __device__ __forceinline__ void fft_lines_dif(C2<R>* tile, const Lines& ln, cons
 // shared-memory layout helpers
 // ---------------------------------------------------------------------------
 
-// Global -> shared copy of one complex element without a register round trip
-// (PTX cp.async; 8 bytes for FP32, 16 bytes for FP64, both aligned to their
-// size), so that a thread keeps all of its tile's loads in flight at once
-// instead of waiting for each before issuing the next.  cp_async_wait() waits
-// for this thread's copies; a __syncthreads() after it publishes the tile.
+// Global -> shared copy of one complex element.  FP32 elements go without a
+// register round trip (PTX cp.async, 8 bytes, aligned to its size), so that
+// a thread keeps all of its tile's loads in flight at once instead of waiting
+// for each before issuing the next.  cp_async_wait() waits for this thread's
+// copies; a __syncthreads() after it publishes the tile.
 template <typename R> __device__ __forceinline__ void cp_async_elem(C2<R>* dst, const C2<R>* src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  if constexpr (sizeof(C2<R>) == 16)
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
-  else
+  if constexpr (sizeof(C2<R>) == 16) {
+    // FP64 passes are bound by the FP64 pipe, not by their loads: a plain
+    // 16-byte load measured faster there than the asynchronous copy
+    *dst = *src;
+  } else {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+  }
 }
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 

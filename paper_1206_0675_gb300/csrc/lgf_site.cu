@@ -21,25 +21,27 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Block reduction of two sums and a maximum in a fixed order; result valid
-// in thread 0.
-__device__ __forceinline__ void block_reduce3(double& a, double& b, double& m) {
-  __shared__ double sa[32], sb[32], sm[32];
+// Block reduction of two sums (FP64, fixed order) and a maximum (FP32: the
+// link defect is compared with bounds far above FP32 resolution, and FP32
+// max and shuffles keep the FP64 pipe free); result valid in thread 0.
+__device__ __forceinline__ void block_reduce3(double& a, double& b, float& m) {
+  __shared__ double sa[32], sb[32];
+  __shared__ float sm[32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
   a = warp_sum(a);
   b = warp_sum(b);
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
   if (lane == 0) { sa[warp] = a; sb[warp] = b; sm[warp] = m; }
   __syncthreads();
   if (warp == 0) {
     a = lane < nw ? sa[lane] : 0.0;
     b = lane < nw ? sb[lane] : 0.0;
-    m = lane < nw ? sm[lane] : 0.0;
+    m = lane < nw ? sm[lane] : 0.f;
     a = warp_sum(a);
     b = warp_sum(b);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
   }
   __syncthreads();
 }
@@ -47,14 +49,15 @@ __device__ __forceinline__ void block_reduce3(double& a, double& b, double& m) {
 // Unitarity defect of a link from its rows 1-2 (row 3 is always rebuilt as
 // (a x b)^* or stored from that rebuild): the largest of | |a|^2 - 1 |,
 // | |b|^2 - 1 | and the components of <a, b>, in the link precision.
-template <typename R> __device__ __forceinline__ double rows_defect(const C2<R> a[3], const C2<R> b[3]) {
+template <typename R> __device__ __forceinline__ float rows_defect(const C2<R> a[3], const C2<R> b[3]) {
   const R na = cnorm2<R>(a[0]) + cnorm2<R>(a[1]) + cnorm2<R>(a[2]);
   const R nb = cnorm2<R>(b[0]) + cnorm2<R>(b[1]) + cnorm2<R>(b[2]);
   C2<R> ip = cconjmul<R>(a[0], b[0]);
   ip = cadd<R>(ip, cconjmul<R>(a[1], b[1]));
   ip = cadd<R>(ip, cconjmul<R>(a[2], b[2]));
-  const R d = fmax(fmax(fabs(na - (R)1), fabs(nb - (R)1)), fmax(fabs(ip.x), fabs(ip.y)));
-  return (double)d;
+  // the four deviations, each taken to FP32 before the maximum
+  return fmaxf(fmaxf(fabsf((float)(na - (R)1)), fabsf((float)(nb - (R)1))),
+               fmaxf(fabsf((float)ip.x), fabsf((float)ip.y)));
 }
 
 // The links whose defect a measurement samples: every fourth warp of the
@@ -74,17 +77,18 @@ __device__ __forceinline__ int defect_sample_mu() {
 // measurement as one of FP64 links in the trace flags.
 // fsum and tsum are one site's sums, already in FP64; every sum above a
 // site (warp, CTA, grid) is FP64 in a fixed order.
-__device__ __forceinline__ void measure_tail(const Geom& g, double fsum, double tsum, double dmax,
+__device__ __forceinline__ void measure_tail(const Geom& g, double fsum, double tsum, float dmax,
                                              double* __restrict__ partials, DevState* __restrict__ st, int count_iter,
                                              unsigned long long cond, int use_cond, bool batch, int flip_ubuf,
                                              int fp64) {
-  double fb = fsum, tb = tsum, db = dmax;
+  double fb = fsum, tb = tsum;
+  float db = dmax;
   block_reduce3(fb, tb, db);
   __shared__ int is_last;
   if (threadIdx.x == 0) {
     partials[MEASURE_PARTIALS * blockIdx.x] = fb;
     partials[MEASURE_PARTIALS * blockIdx.x + 1] = tb;
-    partials[MEASURE_PARTIALS * blockIdx.x + 2] = db;
+    partials[MEASURE_PARTIALS * blockIdx.x + 2] = (double)db;
     __threadfence();
     const unsigned int t = atomicAdd(&st->ticket, 1u);
     is_last = (t == gridDim.x - 1);
@@ -94,11 +98,12 @@ __device__ __forceinline__ void measure_tail(const Geom& g, double fsum, double 
   __threadfence();
   // Final sum over the per-CTA partials in a fixed order (independent of
   // which CTA finished last), so the result is bit-reproducible.
-  double f = 0.0, t = 0.0, d = 0.0;
+  double f = 0.0, t = 0.0;
+  float d = 0.f;
   for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
     f += __ldcg(&partials[MEASURE_PARTIALS * i]);
     t += __ldcg(&partials[MEASURE_PARTIALS * i + 1]);
-    d = fmax(d, __ldcg(&partials[MEASURE_PARTIALS * i + 2]));
+    d = fmaxf(d, (float)__ldcg(&partials[MEASURE_PARTIALS * i + 2]));
   }
   block_reduce3(f, t, d);
   if (threadIdx.x == 0) {
@@ -225,7 +230,7 @@ measure_kernel(Geom g, MatField<R, ROWS> U, const C2<R>* __restrict__ links_alt,
     // ||Delta_A||_F^2
     tsum = (double)delta_norm2<R>(a0, a1, a2, d01, d02, d12);
   }
-  double dmax = 0.0;
+  float dmax = 0.f;
   const int dmu = defect_sample_mu();
   if (dmu >= 0 && s < g.V) {
     C2<R> rows[2][3];
@@ -300,7 +305,7 @@ update_measure_kernel(Geom g, C2<R>* __restrict__ U0, C2<R>* __restrict__ U1, Ma
   const MatField<R, LROWS> Us{cur ? U1 : U0, g.V}, Ud{cur ? U0 : U1, g.V};
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double fsum = 0, tsum = 0;  // as in measure_kernel: FP64 above one link
-  double dmax = 0.0;
+  float dmax = 0.f;
   const int dmu = defect_sample_mu();
   if (s < g.V) {
     int c[4];
@@ -316,7 +321,6 @@ update_measure_kernel(Geom g, C2<R>* __restrict__ U0, C2<R>* __restrict__ U1, Ma
       Gf.load_ro(0, site_fwd(g, s, c, mu), h);
       gauge_product<R>(gx, u, h, o);
       Ud.store(mu, s, o);
-      if (mu == dmu) dmax = rows_defect<R>(o.e[0], o.e[1]);
       fsum += (double)(o.e[0][0].x + o.e[1][1].x + o.e[2][2].x);
       add_antiherm<R>(o, (R)-1, im0, im1, im2, w01, w02, w12);
       const int64_t sb = site_back(g, s, c, mu);
@@ -334,6 +338,16 @@ update_measure_kernel(Geom g, C2<R>* __restrict__ U0, C2<R>* __restrict__ U1, Ma
     delta[2 * g.V + s] = d02;
     delta[3 * g.V + s] = d12;
     tsum = (double)delta_norm2<R>(a0, a1, a2, d01, d02, d12);
+    if (dmu >= 0) {
+      // the sampled link as this thread stored it above (plain loads see the
+      // thread's own stores; keeping the rows in registers instead spilled)
+      C2<R> rows[2][3];
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) rows[r][c] = Ud.p[Ud.off(dmu, r, c, s)];
+      dmax = rows_defect<R>(rows[0], rows[1]);
+    }
   }
   measure_tail(g, fsum, tsum, dmax, partials, st, 1, cond, use_cond, false, 1, sizeof(R) == 8);
 }
