@@ -211,7 +211,7 @@ lgf_status lgf_set_trace_ex(lgf_handle h, double* F_hist, double* theta_hist, in
  * Algorithm 1 reunitarises the links, so rounding drift accumulates, and far
  * from the fixed point -- e.g. with alpha above its convergent range -- the
  * rebuild of row 3 from rows 1-2 compounds it until F overflows).  Every
- * measurement also forms, over one link in sixteen (every fourth warp of
+ * measurement also forms, over one link in 64 (every sixteenth warp of
  * sites, one direction each, all four directions covered), the largest of
  * | |a|^2 - 1 |, | |b|^2 - 1 | and |<a, b>| over the stored rows a, b, in the
  * link precision.  When it exceeds the bound of the running phase, lgf_fix

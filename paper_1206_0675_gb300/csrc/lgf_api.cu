@@ -267,12 +267,12 @@ template <typename R> lgf_status ensure_filter(lgf_ctx* h, Lane<R>& L, double al
 // Measurement of the current links of a lane.
 template <typename R> cudaError_t enqueue_measure(lgf_ctx* h, Lane<R>& L, int count_iter,
                                                    unsigned long long cond, int use_cond, cudaStream_t s,
-                                                   int only_if_revert = 0) {
+                                                   int only_if_revert = 0, unsigned long long cond_undo = 0) {
   if (L.rows == 3)
     return launch_measure<R, 3>(h->geom, L.U, L.D, h->partials, h->st, count_iter, cond, use_cond, s,
-                                only_if_revert, Batch(), L.U2);
+                                only_if_revert, Batch(), L.U2, cond_undo);
   return launch_measure<R, 2>(h->geom, L.U, L.D, h->partials, h->st, count_iter, cond, use_cond, s, only_if_revert,
-                              Batch(), L.U2);
+                              Batch(), L.U2, cond_undo);
 }
 
 // Gauge-transform step of a lane given the divergence in L.D (from the last
@@ -292,14 +292,19 @@ enum { K_A = 0, K_B, K_C, K_UPD, K_MEAS, K_REVERT, K_RESTORE, K_MLP,
 constexpr int kLongestBody = 3 + 8 + 2;
 static_assert(TimingRing::kMaxK >= kLongestBody, "the timing ring must hold the longest body");
 
+// Parts of a body: the undo pair of a learned handle (undo of a rejected
+// step and its re-measurement) and the rest.
+enum { PART_ALL = 0, PART_UNDO = 1, PART_STEP = 2 };
+
 // ks must hold TimingRing::kMaxK entries.
-template <typename R> int body_kernels(const lgf_ctx* h, const Lane<R>& L, int* ks) {
+template <typename R> int body_kernels(const lgf_ctx* h, const Lane<R>& L, int* ks, int part = PART_ALL) {
   int n = 0;
-  if (h->learned) {
+  if (h->learned && part != PART_STEP) {
     ks[n++] = K_REVERT;
     ks[n++] = K_RESTORE;
-    ks[n++] = K_MLP;
   }
+  if (part == PART_UNDO) return n;
+  if (h->learned) ks[n++] = K_MLP;
   if (L.decomp == FFT_1D4) {
     for (int k : {K_F1X, K_F1Y, K_F1Z, K_T1, K_I1Z, K_I1Y, K_I1X, K_GD}) ks[n++] = k;
   } else if (L.decomp == FFT_3D1D) {
@@ -359,11 +364,14 @@ template <typename R> cudaError_t enqueue_alt_fft(lgf_ctx* h, Lane<R>& L, int k,
   }
 }
 
+// cond: the WHILE handle of a captured loop (use_cond != 0); cond_undo: the
+// handle of the conditional node that runs the undo pair (0 = none), set by
+// every counted measurement to whether its step was rejected.
 template <typename R> cudaError_t enqueue_kernel(lgf_ctx* h, Lane<R>& L, int k, unsigned long long cond,
-                                                  int use_cond, cudaStream_t s);
+                                                  int use_cond, cudaStream_t s, unsigned long long cond_undo = 0);
 
 template <> cudaError_t enqueue_kernel<double>(lgf_ctx* h, Lane<double>& L, int k, unsigned long long cond,
-                                               int use_cond, cudaStream_t s) {
+                                               int use_cond, cudaStream_t s, unsigned long long cond_undo) {
   const Geom& g = h->geom;
   switch (k) {
     case K_A: return launch_fft_xy<double>(g, L.plan, L.D, L.tw, L.pos, -1, 4, s);
@@ -373,7 +381,7 @@ template <> cudaError_t enqueue_kernel<double>(lgf_ctx* h, Lane<double>& L, int 
                                                         exact_exp(h));
     case K_UPD:
       return L.rows == 3 ? launch_update<double, 3, 3>(g, L.U, L.g, s) : launch_update<double, 2, 3>(g, L.U, L.g, s);
-    case K_MEAS: return enqueue_measure<double>(h, L, 1, cond, use_cond, s);
+    case K_MEAS: return enqueue_measure<double>(h, L, 1, cond, use_cond, s, 0, cond_undo);
     case K_REVERT:
       return L.rows == 3 ? launch_revert<double, 3, 3>(g, L.U, L.g, L.G, h->st, s, L.U2)
                          : launch_revert<double, 2, 3>(g, L.U, L.g, L.G, h->st, s, L.U2);
@@ -384,7 +392,7 @@ template <> cudaError_t enqueue_kernel<double>(lgf_ctx* h, Lane<double>& L, int 
 }
 
 template <> cudaError_t enqueue_kernel<float>(lgf_ctx* h, Lane<float>& L, int k, unsigned long long cond,
-                                              int use_cond, cudaStream_t s) {
+                                              int use_cond, cudaStream_t s, unsigned long long cond_undo) {
   const Geom& g = h->geom;
   switch (k) {
     case K_A: return launch_fft_xy<float>(g, L.plan, L.D, L.tw, L.pos, -1, 4, s);
@@ -397,9 +405,11 @@ template <> cudaError_t enqueue_kernel<float>(lgf_ctx* h, Lane<float>& L, int k,
     case K_UPD: return L.grows == 2 ? launch_update<float, 2, 2>(g, L.U, L.g, s) : launch_update<float, 3, 3>(g, L.U, L.g, s);
     case K_UM:
       return L.grows == 2
-                 ? launch_update_measure<float, 2, 2>(g, L.U, L.U2, L.g, L.D, h->partials, h->st, cond, use_cond, s)
-                 : launch_update_measure<float, 3, 3>(g, L.U, L.U2, L.g, L.D, h->partials, h->st, cond, use_cond, s);
-    case K_MEAS: return enqueue_measure<float>(h, L, 1, cond, use_cond, s);
+                 ? launch_update_measure<float, 2, 2>(g, L.U, L.U2, L.g, L.D, h->partials, h->st, cond, use_cond, s,
+                                                      cond_undo)
+                 : launch_update_measure<float, 3, 3>(g, L.U, L.U2, L.g, L.D, h->partials, h->st, cond, use_cond, s,
+                                                      cond_undo);
+    case K_MEAS: return enqueue_measure<float>(h, L, 1, cond, use_cond, s, 0, cond_undo);
     case K_REVERT:
       return L.grows == 2 ? launch_revert<float, 2, 2>(g, L.U, L.g, L.G, h->st, s, L.U2)
                           : launch_revert<float, 3, 3>(g, L.U, L.g, L.G, h->st, s, L.U2);
@@ -429,7 +439,8 @@ cudaError_t timing_collect(TimingRing& T, int slot) {
 // update, measure.  With timing enabled (and outside graph capture) every
 // kernel is bracketed by CUDA events on the launching stream.
 template <typename R> cudaError_t enqueue_body(lgf_ctx* h, Lane<R>& L, unsigned long long cond, int use_cond,
-                                                cudaStream_t s) {
+                                                cudaStream_t s, int part = PART_ALL,
+                                                unsigned long long cond_undo = 0) {
   TimingRing& T = h->timing;
   const bool timed = T.enabled && !use_cond;
   int slot = 0;
@@ -441,9 +452,9 @@ template <typename R> cudaError_t enqueue_body(lgf_ctx* h, Lane<R>& L, unsigned 
     if ((e = cudaEventRecord(T.ev[slot][0], s)) != cudaSuccess) return e;
   }
   int ks[TimingRing::kMaxK];
-  const int nk = body_kernels<R>(h, L, ks);
+  const int nk = body_kernels<R>(h, L, ks, part);
   for (int i = 0; i < nk; ++i) {
-    if ((e = enqueue_kernel<R>(h, L, ks[i], cond, use_cond, s)) != cudaSuccess) return e;
+    if ((e = enqueue_kernel<R>(h, L, ks[i], cond, use_cond, s, cond_undo)) != cudaSuccess) return e;
     if (timed) {
       T.cat[slot][i] = kernel_category(ks[i]);
       if ((e = cudaEventRecord(T.ev[slot][i + 1], s)) != cudaSuccess) return e;
@@ -470,8 +481,32 @@ template <typename R> lgf_status ensure_graph(lgf_ctx* h, Lane<R>& L) {
   cudaGraphNode_t node;
   LGF_CK(h, cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np));
   cudaGraph_t body = np.conditional.phGraph_out[0];
-  LGF_CK(h, cudaStreamBeginCaptureToGraph(h->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-  cudaError_t e = enqueue_body<R>(h, L, (unsigned long long)cond, 1, h->cap_stream);
+  // Learned handles: the undo pair sits in an IF node at the top of the body,
+  // taken only after a rejected step (the measurement sets its handle), so
+  // that accepted steps launch neither kernel.
+  cudaGraphNode_t undo_node = nullptr;
+  unsigned long long undo_h = 0;
+  if (h->learned) {
+    cudaGraphConditionalHandle hu;
+    LGF_CK(h, cudaGraphConditionalHandleCreate(&hu, graph, 0, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams up = {cudaGraphNodeTypeConditional};
+    up.conditional.handle = hu;
+    up.conditional.type = cudaGraphCondTypeIf;
+    up.conditional.size = 1;
+    LGF_CK(h, cudaGraphAddNode(&undo_node, body, nullptr, nullptr, 0, &up));
+    LGF_CK(h, cudaStreamBeginCaptureToGraph(h->cap_stream, up.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                            cudaStreamCaptureModeRelaxed));
+    cudaError_t eu = enqueue_body<R>(h, L, (unsigned long long)cond, 1, h->cap_stream, PART_UNDO);
+    cudaGraph_t cu = nullptr;
+    cudaError_t eu2 = cudaStreamEndCapture(h->cap_stream, &cu);
+    if (eu != cudaSuccess) return fail_cuda(h, eu, "capture of the undo pair");
+    if (eu2 != cudaSuccess) return fail_cuda(h, eu2, "cudaStreamEndCapture");
+    undo_h = (unsigned long long)hu;
+  }
+  LGF_CK(h, cudaStreamBeginCaptureToGraph(h->cap_stream, body, undo_node ? &undo_node : nullptr, nullptr,
+                                          undo_node ? 1 : 0, cudaStreamCaptureModeRelaxed));
+  cudaError_t e = enqueue_body<R>(h, L, (unsigned long long)cond, 1, h->cap_stream,
+                                  h->learned ? PART_STEP : PART_ALL, undo_h);
   cudaGraph_t captured = nullptr;
   cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &captured);
   if (e != cudaSuccess) return fail_cuda(h, e, "capture of the iteration body");
@@ -562,9 +597,15 @@ template <typename R> lgf_status run_loop(lgf_ctx* h, Lane<R>& L, double tol, in
       continue;
     }
     if (!(std::isfinite(S.F) && std::isfinite(S.theta))) return LGF_OK;
-    if (S.theta < tol || S.iter >= max_iter) return LGF_OK;
+    if ((S.theta < tol || S.iter >= max_iter) && !S.revert) return LGF_OK;
     s = ensure_graph<R>(h, L);
     if (s != LGF_OK) return s;
+    // the graph's undo node is off at launch: a rejected step left over from
+    // an earlier launch (stopped by the defect guard) is undone here first
+    if (h->learned && S.revert) {
+      cudaError_t eu = enqueue_body<R>(h, L, 0, 0, h->stream, PART_UNDO);
+      if (eu != cudaSuccess) return fail_cuda(h, eu, "undo of a rejected step");
+    }
     LGF_CK(h, cudaGraphLaunch(L.exec, h->stream));
     if ((s = sync_state(h)) != LGF_OK) return s;
   }
@@ -597,11 +638,16 @@ template <typename R> lgf_status step_lane(lgf_ctx* h, Lane<R>& L, double alpha)
     if ((e = log_modes<R>(h, L, true)) != cudaSuccess) return fail_cuda(h, e, "mode log");
     h->log_primed = true;
   }
-  if ((e = enqueue_body<R>(h, L, 0, 0, h->stream)) != cudaSuccess) return fail_cuda(h, e, "lgf_step");
+  // a learned handle synchronised after its last call, so the host knows
+  // whether a rejected step still waits for its undo (normally not: it is
+  // redone below); otherwise the body skips the undo pair
+  const bool pending = h->learned && h->st_host->revert;
+  if ((e = enqueue_body<R>(h, L, 0, 0, h->stream, (h->learned && !pending) ? PART_STEP : PART_ALL)) != cudaSuccess)
+    return fail_cuda(h, e, "lgf_step");
   if (h->learned) {
     // a rejected learned step is undone and redone with the plain filter now
     if ((s = sync_state(h)) != LGF_OK) return s;
-    if (h->st_host->revert && (e = enqueue_body<R>(h, L, 0, 0, h->stream)) != cudaSuccess)
+    if (h->st_host->revert && (e = enqueue_body<R>(h, L, 0, 0, h->stream, PART_ALL)) != cudaSuccess)
       return fail_cuda(h, e, "lgf_step redo");
   }
   if (h->logging && (e = log_modes<R>(h, L, false)) != cudaSuccess) return fail_cuda(h, e, "mode log");

@@ -181,20 +181,17 @@ __device__ __forceinline__ void fft_lines_dif(C2<R>* tile, const Lines& ln, cons
 // shared-memory layout helpers
 // ---------------------------------------------------------------------------
 
-// Global -> shared copy of one complex element.  FP32 elements go without a
-// register round trip (PTX cp.async, 8 bytes, aligned to its size), so that
-// a thread keeps all of its tile's loads in flight at once instead of waiting
-// for each before issuing the next.  cp_async_wait() waits for this thread's
-// copies; a __syncthreads() after it publishes the tile.
+// Global -> shared copy of one complex element without a register round trip
+// (PTX cp.async; 8 bytes for FP32, 16 bytes for FP64, both aligned to their
+// size), so that a thread keeps all of its tile's loads in flight at once
+// instead of waiting for each before issuing the next.  cp_async_wait() waits
+// for this thread's copies; a __syncthreads() after it publishes the tile.
 template <typename R> __device__ __forceinline__ void cp_async_elem(C2<R>* dst, const C2<R>* src) {
-  if constexpr (sizeof(C2<R>) == 16) {
-    // FP64 passes are bound by the FP64 pipe, not by their loads: a plain
-    // 16-byte load measured faster there than the asynchronous copy
-    *dst = *src;
-  } else {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  if constexpr (sizeof(C2<R>) == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+  else
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
-  }
 }
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
@@ -263,7 +260,9 @@ __global__ void __launch_bounds__(512) fft_xy_kernel(Geom g, FFTDir dx, FFTDir d
 // (z, t) plane pass with the momentum filter: one CTA per (x-block, y, field)
 // ---------------------------------------------------------------------------
 
-template <typename R>
+// LRN: the learned handles' variant (multiplier table, divergence snapshot);
+// the plain variant carries none of that code.
+template <typename R, bool LRN>
 __global__ void __launch_bounds__(512) fft_zt_filter_kernel(Geom g, FFTDir dz, FFTDir dt, C2<R>* __restrict__ data,
                                      const C2<R>* __restrict__ twg, const short* __restrict__ posg,
                                      const R* __restrict__ K, int xc, int mode, LearnedIO lio, int4 H, Lines lz,
@@ -297,10 +296,10 @@ __global__ void __launch_bounds__(512) fft_zt_filter_kernel(Geom g, FFTDir dz, F
     fft_lines_dit<R, -1>(tile, lt, dt, tw + Lz);
     // learned multiplier of the momentum class (f_mu = min(k_mu, L_mu - k_mu))
     // and the snapshot of the transformed divergence, both of step k
-    const int kit = lio.st != nullptr ? lio.st->iter : 0;
-    const bool learned = lio.mtab != nullptr && lio.st->use_m != 0;
+    const int kit = LRN ? lio.st->iter : 0;
+    const bool learned = LRN && lio.mtab != nullptr && lio.st->use_m != 0;
     const float* mtab = lio.mtab + (int64_t)(kit & 1) * lio.nclass;
-    float2* snap = lio.snap != nullptr ? lio.snap + ((int64_t)(kit & 1) * 4 + blockIdx.y) * g.V : nullptr;
+    float2* snap = (LRN && lio.snap != nullptr) ? lio.snap + ((int64_t)(kit & 1) * 4 + blockIdx.y) * g.V : nullptr;
     const int fy = min(y, Ly - y);
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       LGF_ZT_IDX(i)
@@ -311,7 +310,7 @@ __global__ void __launch_bounds__(512) fft_zt_filter_kernel(Geom g, FFTDir dz, F
         k *= (R)__ldg(&mtab[((ft * H.z + fz) * H.y + fy) * H.x + fx]);
       }
       C2<R>& e = tile[t * TS + z * xc + xi];
-      if (snap != nullptr) snap[(int64_t)zt * plane + sxy + xi] = make_float2((float)e.x, (float)e.y);
+      if (LRN && snap != nullptr) snap[(int64_t)zt * plane + sxy + xi] = make_float2((float)e.x, (float)e.y);
       e = mkc<R>(e.x * k, e.y * k);
     }
     __syncthreads();
@@ -363,7 +362,7 @@ struct LinePass {
 // mtab (mode 0, may be NULL): learned multiplier per momentum class, applied
 // when *use_m != 0; the class of momentum k is (min(k_mu, L_mu - k_mu))_mu in
 // a table of H.x * H.y * H.z * H.w classes.
-template <typename R>
+template <typename R, bool LRN>
 __global__ void __launch_bounds__(512) fft_line_kernel(LinePass lp, FFTDir d, Geom g, C2<R>* __restrict__ data,
                                                        const C2<R>* __restrict__ twg, const short* __restrict__ posg,
                                                        const R* __restrict__ K, int mode, Lines ln, LearnedIO lio,
@@ -405,10 +404,10 @@ __global__ void __launch_bounds__(512) fft_line_kernel(LinePass lp, FFTDir d, Ge
     fft_lines_dif<R, +1>(tile, ln, d, tw);
   } else {
     fft_lines_dit<R, -1>(tile, ln, d, tw);
-    const int kit = lio.st != nullptr ? lio.st->iter : 0;
-    const bool learned = lio.mtab != nullptr && lio.st->use_m != 0;
+    const int kit = LRN ? lio.st->iter : 0;
+    const bool learned = LRN && lio.mtab != nullptr && lio.st->use_m != 0;
     const float* mtab = lio.mtab + (int64_t)(kit & 1) * lio.nclass;
-    float2* snap = lio.snap != nullptr ? lio.snap + ((int64_t)(kit & 1) * 4 + blockIdx.y) * V : nullptr;
+    float2* snap = (LRN && lio.snap != nullptr) ? lio.snap + ((int64_t)(kit & 1) * 4 + blockIdx.y) * V : nullptr;
     for (int i = threadIdx.x; i < n_el; i += blockDim.x) {
       LGF_LINE_IDX(i)
       R k = __ldg(&K[site]);
@@ -420,7 +419,7 @@ __global__ void __launch_bounds__(512) fft_line_kernel(LinePass lp, FFTDir d, Ge
         k *= (R)__ldg(&mtab[((ft * H.z + fz) * H.y + fy) * H.x + fx]);
       }
       C2<R>& e = tile[l * RS + n];
-      if (snap != nullptr) snap[site] = make_float2((float)e.x, (float)e.y);
+      if (LRN && snap != nullptr) snap[site] = make_float2((float)e.x, (float)e.y);
       e = mkc<R>(e.x * k, e.y * k);
     }
     __syncthreads();
@@ -980,14 +979,19 @@ cudaError_t launch_fft_zt(const Geom& g, const FFTPlan& p, C2<R>* data, const C2
                           const R* K, int mode, int nfields, cudaStream_t s, const LearnedIO& lio, const Batch& B) {
   const size_t smem = p.smem_zt;
   dim3 grid((unsigned)(g.L[0] / p.xc * g.L[1]), (unsigned)nfields, (unsigned)B.n);
-  cudaError_t e = allow_smem(fft_zt_filter_kernel<R>, smem);
+  const bool lrn = mode == 0 && (lio.mtab != nullptr || lio.snap != nullptr);
+  cudaError_t e = lrn ? allow_smem(fft_zt_filter_kernel<R, true>, smem) : allow_smem(fft_zt_filter_kernel<R, false>, smem);
   if (e != cudaSuccess) return e;
   const int4 H = make_int4(g.L[0] / 2 + 1, g.L[1] / 2 + 1, g.L[2] / 2 + 1, g.L[3] / 2 + 1);
   const int xc = p.xc, Lz = g.L[2], Lt = g.L[3], TS = Lz * xc + 1;
   const Lines lz = make_lines(Lt * xc, xc, 1, TS, xc), lt = make_lines(Lz * xc, Lz * xc, 1, 0, TS);
   const CopyDiv cd{FastDiv::make((uint32_t)xc), FastDiv::make((uint32_t)Lz)};
-  fft_zt_filter_kernel<R><<<grid, p.threads_zt, smem, s>>>(g, p.d[2], p.d[3], data, tw, pos, K, p.xc, mode, lio, H,
-                                                           lz, lt, cd, B);
+  if (lrn)
+    fft_zt_filter_kernel<R, true><<<grid, p.threads_zt, smem, s>>>(g, p.d[2], p.d[3], data, tw, pos, K, p.xc, mode, lio,
+                                                                   H, lz, lt, cd, B);
+  else
+    fft_zt_filter_kernel<R, false><<<grid, p.threads_zt, smem, s>>>(g, p.d[2], p.d[3], data, tw, pos, K, p.xc, mode,
+                                                                    lio, H, lz, lt, cd, B);
   return cudaGetLastError();
 }
 
@@ -1005,13 +1009,19 @@ cudaError_t launch_fft_line(const Geom& g, const FFTPlan& p, int mu, C2<R>* data
   lp.dlob = FastDiv::make((uint32_t)(lp.contiguous ? 1 : lp.S / lp.nl));
   const int64_t blocks = g.V / ((int64_t)N * lp.nl);
   const size_t smem = p.smem_line[mu];
-  cudaError_t e = allow_smem(fft_line_kernel<R>, smem);
+  const bool lrn = mode == 0 && (lio.mtab != nullptr || lio.snap != nullptr);
+  cudaError_t e = lrn ? allow_smem(fft_line_kernel<R, true>, smem) : allow_smem(fft_line_kernel<R, false>, smem);
   if (e != cudaSuccess) return e;
   const int off = mu == 0 ? 0 : mu == 1 ? g.L[0] : mu == 2 ? g.L[0] + g.L[1] : g.L[0] + g.L[1] + g.L[2];
   const Lines ln = make_lines(lp.nl, lp.nl, N + 1, 0, 1);
   const int4 H = make_int4(g.L[0] / 2 + 1, g.L[1] / 2 + 1, g.L[2] / 2 + 1, g.L[3] / 2 + 1);
-  fft_line_kernel<R><<<dim3((unsigned)blocks, (unsigned)nfields, (unsigned)B.n), p.threads_line[mu], smem, s>>>(
-      lp, p.d[mu], g, data, tw + off, pos + off, K, mode, ln, lio, H, B);
+  const dim3 grid((unsigned)blocks, (unsigned)nfields, (unsigned)B.n);
+  if (lrn)
+    fft_line_kernel<R, true><<<grid, p.threads_line[mu], smem, s>>>(lp, p.d[mu], g, data, tw + off, pos + off, K, mode,
+                                                                    ln, lio, H, B);
+  else
+    fft_line_kernel<R, false><<<grid, p.threads_line[mu], smem, s>>>(lp, p.d[mu], g, data, tw + off, pos + off, K,
+                                                                     mode, ln, lio, H, B);
   return cudaGetLastError();
 }
 

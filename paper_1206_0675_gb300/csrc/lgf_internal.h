@@ -79,10 +79,13 @@ inline int64_t measure_blocks(int64_t V) { return (V + MEASURE_THREADS - 1) / ME
 // In batch mode (B->st set) each configuration's state is B->st[z] and its
 // last CTA sets that state's `done` instead of a graph condition.
 // links_alt (fused lanes): the second link buffer, read instead of links when st->ubuf is set.
+// cond_undo (use_cond only): handle of the graph's IF node around the undo
+// pair, set by a counted measurement to whether its step was rejected.
 template <typename R, int ROWS>
 cudaError_t launch_measure(const Geom& g, const C2<R>* links, C2<R>* delta, double* partials, DevState* st,
                            int count_iter, unsigned long long cond_handle, int use_cond, cudaStream_t s,
-                           int only_if_revert = 0, const Batch& B = Batch(), const C2<R>* links_alt = nullptr);
+                           int only_if_revert = 0, const Batch& B = Batch(), const C2<R>* links_alt = nullptr,
+                           unsigned long long cond_undo = 0);
 
 // Link update fused with the measurement that follows it: the links are read
 // from buffer st->ubuf of {U0, U1} and the updated links written to the other
@@ -94,7 +97,7 @@ cudaError_t launch_measure(const Geom& g, const C2<R>* links, C2<R>* delta, doub
 template <typename R, int LROWS, int GROWS>
 cudaError_t launch_update_measure(const Geom& g, C2<R>* U0, C2<R>* U1, const C2<R>* gfield, C2<R>* delta,
                                   double* partials, DevState* st, unsigned long long cond, int use_cond,
-                                  cudaStream_t s);
+                                  cudaStream_t s, unsigned long long cond_undo = 0);
 
 // Undo of the last update when st->revert is set: U_mu(x) <- g^dag(x) U_mu(x)
 // g(x + mu^) and, when G is given (3 rows, precision R), G <- g^dag G.

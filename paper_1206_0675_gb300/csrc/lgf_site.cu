@@ -60,13 +60,14 @@ template <typename R> __device__ __forceinline__ float rows_defect(const C2<R> a
                fmaxf(fabsf((float)ip.x), fabsf((float)ip.y)));
 }
 
-// The links whose defect a measurement samples: every fourth warp of the
-// grid (warp index w with w % 4 == 0) takes direction (w / 4) % 4 of its 32
-// sites, i.e. one link in sixteen, spread over all directions.  The choice
-// is uniform within a warp, so the other warps skip the work entirely.
+// The links whose defect a measurement samples: every sixteenth warp of the
+// grid (warp index w with w % 16 == 0) takes direction (w / 16) % 4 of its 32
+// sites, i.e. one link in 64, spread over all directions (the drift the
+// guard watches is slow and lattice-wide).  The choice is uniform within a
+// warp, so the other warps skip the work entirely.
 __device__ __forceinline__ int defect_sample_mu() {
   const unsigned w = (unsigned)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  return (w & 3u) == 0 ? (int)((w >> 2) & 3u) : -1;
+  return (w & 15u) == 0 ? (int)((w >> 4) & 3u) : -1;
 }
 
 // Reduction of the per-thread F and theta sums and the sampled link defect
@@ -80,7 +81,7 @@ __device__ __forceinline__ int defect_sample_mu() {
 __device__ __forceinline__ void measure_tail(const Geom& g, double fsum, double tsum, float dmax,
                                              double* __restrict__ partials, DevState* __restrict__ st, int count_iter,
                                              unsigned long long cond, int use_cond, bool batch, int flip_ubuf,
-                                             int fp64) {
+                                             int fp64, unsigned long long cond_undo) {
   double fb = fsum, tb = tsum;
   float db = dmax;
   block_reduce3(fb, tb, db);
@@ -157,6 +158,8 @@ __device__ __forceinline__ void measure_tail(const Geom& g, double fsum, double 
     if (use_cond) {
       cudaGraphConditionalHandle h = (cudaGraphConditionalHandle)cond;
       cudaGraphSetConditional(h, (finite && sound && ((th >= st->tol && it < st->max_iter) || revert)) ? 1u : 0u);
+      if (cond_undo != 0 && count_iter > 0)
+        cudaGraphSetConditional((cudaGraphConditionalHandle)cond_undo, revert ? 1u : 0u);
     }
   }
 }
@@ -181,7 +184,7 @@ template <typename R, int ROWS>
 __global__ void __launch_bounds__(MEASURE_THREADS)
 measure_kernel(Geom g, MatField<R, ROWS> U, const C2<R>* __restrict__ links_alt, C2<R>* __restrict__ delta,
                double* __restrict__ partials, DevState* __restrict__ st, int count_iter, unsigned long long cond,
-               int use_cond, int only_if_revert, Batch B) {
+               int use_cond, int only_if_revert, Batch B, unsigned long long cond_undo) {
   if (batch_skip(B)) return;
   const bool batch = B.st != nullptr;
   if (batch) {
@@ -237,17 +240,18 @@ measure_kernel(Geom g, MatField<R, ROWS> U, const C2<R>* __restrict__ links_alt,
     U.load_rows01_ro(dmu, s, rows);
     dmax = rows_defect<R>(rows[0], rows[1]);
   }
-  measure_tail(g, fsum, tsum, dmax, partials, st, count_iter, cond, use_cond, batch, 0, sizeof(R) == 8);
+  measure_tail(g, fsum, tsum, dmax, partials, st, count_iter, cond, use_cond, batch, 0, sizeof(R) == 8, cond_undo);
 }
 
 template <typename R, int ROWS>
 cudaError_t launch_measure(const Geom& g, const C2<R>* links, C2<R>* delta, double* partials, DevState* st,
                            int count_iter, unsigned long long cond_handle, int use_cond, cudaStream_t s,
-                           int only_if_revert, const Batch& B, const C2<R>* links_alt) {
+                           int only_if_revert, const Batch& B, const C2<R>* links_alt,
+                           unsigned long long cond_undo) {
   MatField<R, ROWS> U{const_cast<C2<R>*>(links), g.V};
   const int64_t nb = measure_blocks(g.V);
   measure_kernel<R, ROWS><<<dim3((unsigned)nb, 1, (unsigned)B.n), MEASURE_THREADS, 0, s>>>(
-      g, U, links_alt, delta, partials, st, count_iter, cond_handle, use_cond, only_if_revert, B);
+      g, U, links_alt, delta, partials, st, count_iter, cond_handle, use_cond, only_if_revert, B, cond_undo);
   return cudaGetLastError();
 }
 
@@ -300,7 +304,7 @@ template <typename R, int LROWS, int GROWS>
 __global__ void __launch_bounds__(MEASURE_THREADS, 3)
 update_measure_kernel(Geom g, C2<R>* __restrict__ U0, C2<R>* __restrict__ U1, MatField<R, GROWS> Gf,
                       C2<R>* __restrict__ delta, double* __restrict__ partials, DevState* __restrict__ st,
-                      unsigned long long cond, int use_cond) {
+                      unsigned long long cond, int use_cond, unsigned long long cond_undo) {
   const int cur = st->ubuf;
   const MatField<R, LROWS> Us{cur ? U1 : U0, g.V}, Ud{cur ? U0 : U1, g.V};
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -349,17 +353,17 @@ update_measure_kernel(Geom g, C2<R>* __restrict__ U0, C2<R>* __restrict__ U1, Ma
       dmax = rows_defect<R>(rows[0], rows[1]);
     }
   }
-  measure_tail(g, fsum, tsum, dmax, partials, st, 1, cond, use_cond, false, 1, sizeof(R) == 8);
+  measure_tail(g, fsum, tsum, dmax, partials, st, 1, cond, use_cond, false, 1, sizeof(R) == 8, cond_undo);
 }
 
 template <typename R, int LROWS, int GROWS>
 cudaError_t launch_update_measure(const Geom& g, C2<R>* U0, C2<R>* U1, const C2<R>* gfield, C2<R>* delta,
                                   double* partials, DevState* st, unsigned long long cond, int use_cond,
-                                  cudaStream_t s) {
+                                  cudaStream_t s, unsigned long long cond_undo) {
   MatField<R, GROWS> Gf{const_cast<C2<R>*>(gfield), g.V};
   const int64_t nb = measure_blocks(g.V);
   update_measure_kernel<R, LROWS, GROWS><<<(unsigned)nb, MEASURE_THREADS, 0, s>>>(g, U0, U1, Gf, delta, partials,
-                                                                                  st, cond, use_cond);
+                                                                                  st, cond, use_cond, cond_undo);
   return cudaGetLastError();
 }
 
@@ -843,7 +847,7 @@ cudaError_t launch_project_sites_f32_to_f64(const Geom& g, const float2* G32, do
 #define LGF_INST_R_ROWS(R, ROWS)                                                                                     \
   template cudaError_t launch_measure<R, ROWS>(const Geom&, const C2<R>*, C2<R>*, double*, DevState*, int,           \
                                                unsigned long long, int, cudaStream_t, int, const Batch&,            \
-                                               const C2<R>*);                                                       \
+                                               const C2<R>*, unsigned long long);                                   \
   template cudaError_t launch_links_from_aos<R, ROWS>(const Geom&, const double*, C2<R>*, cudaStream_t);            \
   template cudaError_t launch_links_to_aos<R, ROWS>(const Geom&, const C2<R>*, double*, cudaStream_t);              \
   template cudaError_t launch_sites_to_aos<R, ROWS>(const Geom&, const C2<R>*, double*, cudaStream_t);              \
@@ -870,7 +874,8 @@ template cudaError_t launch_update<float, 2, 2>(const Geom&, C2<float>*, const C
 template cudaError_t launch_update<float, 3, 3>(const Geom&, C2<float>*, const C2<float>*, cudaStream_t, const Batch&);
 #define LGF_INST_UM(R, LR, GR)                                                                                     \
   template cudaError_t launch_update_measure<R, LR, GR>(const Geom&, C2<R>*, C2<R>*, const C2<R>*, C2<R>*, double*, \
-                                                        DevState*, unsigned long long, int, cudaStream_t);
+                                                        DevState*, unsigned long long, int, cudaStream_t,          \
+                                                        unsigned long long);
 LGF_INST_UM(float, 2, 2)
 LGF_INST_UM(float, 3, 3)
 template cudaError_t launch_delta_to_aos<double>(const Geom&, const C2<double>*, double*, cudaStream_t);
