@@ -125,7 +125,7 @@ struct lgf_ctx {
   double switch_theta = 1e-9;     // FP32 -> FP64 switch level of LGF_MIXED
   bool learned = false;           // LGF_LEARNED
   float* mtab = nullptr;          // learned multiplier tables of even and odd steps [2][nclass]
-  float2* snap = nullptr;         // Fourier-space divergence snapshots of even and odd steps [2][4][V]
+  uint32_t* snap = nullptr;       // Fourier-space divergence snapshots of even and odd steps [2][4][V], BF16 pairs
   uint16_t* mlp_w = nullptr;      // BF16 network parameters (device)
   bool logging = false;           // per-mode statistics of every lgf_step
   bool log_primed = false;

@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(512) fft_zt_filter_kernel(Geom g, FFTDir dz, F
     const int kit = LRN ? lio.st->iter : 0;
     const bool learned = LRN && lio.mtab != nullptr && lio.st->use_m != 0;
     const float* mtab = lio.mtab + (int64_t)(kit & 1) * lio.nclass;
-    float2* snap = (LRN && lio.snap != nullptr) ? lio.snap + ((int64_t)(kit & 1) * 4 + blockIdx.y) * g.V : nullptr;
+    uint32_t* snap = (LRN && lio.snap != nullptr) ? lio.snap + ((int64_t)(kit & 1) * 4 + blockIdx.y) * g.V : nullptr;
     const int fy = min(y, Ly - y);
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       LGF_ZT_IDX(i)
@@ -310,7 +310,7 @@ __global__ void __launch_bounds__(512) fft_zt_filter_kernel(Geom g, FFTDir dz, F
         k *= (R)__ldg(&mtab[((ft * H.z + fz) * H.y + fy) * H.x + fx]);
       }
       C2<R>& e = tile[t * TS + z * xc + xi];
-      if (LRN && snap != nullptr) snap[(int64_t)zt * plane + sxy + xi] = make_float2((float)e.x, (float)e.y);
+      if (LRN && snap != nullptr) snap[(int64_t)zt * plane + sxy + xi] = bf16x2_of<R>(e);
       e = mkc<R>(e.x * k, e.y * k);
     }
     __syncthreads();
@@ -407,7 +407,7 @@ __global__ void __launch_bounds__(512) fft_line_kernel(LinePass lp, FFTDir d, Ge
     const int kit = LRN ? lio.st->iter : 0;
     const bool learned = LRN && lio.mtab != nullptr && lio.st->use_m != 0;
     const float* mtab = lio.mtab + (int64_t)(kit & 1) * lio.nclass;
-    float2* snap = (LRN && lio.snap != nullptr) ? lio.snap + ((int64_t)(kit & 1) * 4 + blockIdx.y) * V : nullptr;
+    uint32_t* snap = (LRN && lio.snap != nullptr) ? lio.snap + ((int64_t)(kit & 1) * 4 + blockIdx.y) * V : nullptr;
     for (int i = threadIdx.x; i < n_el; i += blockDim.x) {
       LGF_LINE_IDX(i)
       R k = __ldg(&K[site]);
@@ -419,7 +419,7 @@ __global__ void __launch_bounds__(512) fft_line_kernel(LinePass lp, FFTDir d, Ge
         k *= (R)__ldg(&mtab[((ft * H.z + fz) * H.y + fy) * H.x + fx]);
       }
       C2<R>& e = tile[l * RS + n];
-      if (LRN && snap != nullptr) snap[site] = make_float2((float)e.x, (float)e.y);
+      if (LRN && snap != nullptr) snap[site] = bf16x2_of<R>(e);
       e = mkc<R>(e.x * k, e.y * k);
     }
     __syncthreads();

@@ -207,14 +207,35 @@ cudaError_t launch_fft_xy(const Geom& g, const FFTPlan& p, C2<R>* data, const C2
 // stored before the filter.
 // Learned handles' extras of the pass that carries the filter: the multiplier
 // table of step k is mtab + (k & 1) * nclass and the Fourier-space divergence
-// (before the filter) is stored, in FP32, in snap + (k & 1) * 4 V, with
-// k = st->iter read on the device.
+// (before the filter) is stored in snap + (k & 1) * 4 V, with k = st->iter
+// read on the device.  A snapshot entry is one complex value as two BF16
+// halves (real part in the low 16 bits): the class contraction it feeds is a
+// network input, which the tensor cores read in BF16 anyway.
 struct LearnedIO {
   const float* mtab = nullptr;   // [2][nclass]
-  float2* snap = nullptr;        // [2][4][V]
+  uint32_t* snap = nullptr;      // [2][4][V]
   const DevState* st = nullptr;  // st->use_m, st->iter
   int64_t nclass = 0;
 };
+
+// BF16 bits of x by truncation of its FP32 value.
+__device__ __forceinline__ uint32_t bf16_trunc_bits(float x) { return __float_as_uint(x) >> 16; }
+// BF16 bits of an FP64 value by truncation, on the integer pipe (no FP64
+// instruction): sign, exponent rebiased from 1023 to 127, top 7 mantissa bits;
+// values below the FP32 range flush to zero, values above it become infinite.
+__device__ __forceinline__ uint32_t bf16_trunc_bits(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const uint32_t sign = (uint32_t)(b >> 48) & 0x8000u;
+  const int e = (int)((b >> 52) & 0x7ffu) - 1023 + 127;
+  if (e <= 0) return sign;
+  if (e >= 255) return sign | 0x7f80u;
+  return sign | ((uint32_t)e << 7) | ((uint32_t)(b >> 45) & 0x7fu);
+}
+template <typename R> __device__ __forceinline__ uint32_t bf16x2_of(C2<R> v) {
+  return bf16_trunc_bits(v.x) | (bf16_trunc_bits(v.y) << 16);
+}
+__device__ __forceinline__ float bf16x2_re(uint32_t p) { return __uint_as_float(p << 16); }
+__device__ __forceinline__ float bf16x2_im(uint32_t p) { return __uint_as_float(p & 0xffff0000u); }
 
 template <typename R>
 cudaError_t launch_fft_zt(const Geom& g, const FFTPlan& p, C2<R>* data, const C2<R>* tw, const short* pos,

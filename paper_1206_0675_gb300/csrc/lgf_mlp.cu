@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(128) mlp_eval_kernel(const __nv_bfloat16* __re
 __global__ void __launch_bounds__(128) mlp_multiplier_kernel(const __nv_bfloat16* __restrict__ P, MlpGeom mg,
                                                              Geom geo, const float* __restrict__ p2, DevState* st,
                                                              float* __restrict__ mtab_base,
-                                                             const float2* __restrict__ snap) {
+                                                             const uint32_t* __restrict__ snap) {
   __shared__ MlpSmem S;
   mlp_load_smem(S, P);
   const double theta = st->theta;
@@ -204,8 +204,8 @@ __global__ void __launch_bounds__(128) mlp_multiplier_kernel(const __nv_bfloat16
   }
   float* mtab = mtab_base + (int64_t)(iter & 1) * mg.nclass;
   const int64_t V = geo.V;
-  const float2* sa = snap + (int64_t)((iter + 1) & 1) * 4 * V;  // divergence k - 1
-  const float2* sb = snap + (int64_t)(iter & 1) * 4 * V;        // divergence k - 2
+  const uint32_t* sa = snap + (int64_t)((iter + 1) & 1) * 4 * V;  // divergence k - 1
+  const uint32_t* sb = snap + (int64_t)(iter & 1) * 4 * V;        // divergence k - 2
   const float fb = theta > 0.0 ? (float)(floor(2.0 * log10(theta)) * 0.5) : -20.f;
   const float f4 = -fb / 16.f;
   const float f5 = fminf((float)iter / MLP_ITER_SCALE, 1.f);
@@ -258,9 +258,10 @@ __global__ void __launch_bounds__(128) mlp_multiplier_kernel(const __nv_bfloat16
                 const int kx = bx ? geo.L[0] - f[0] : f[0];
                 const int64_t sidx = (int64_t)tig * V + kx + geo.stride[1] * ky + geo.stride[2] * kz +
                                      geo.stride[3] * kt;
-                const float2 va = __ldg(&sa[sidx]), vb = __ldg(&sb[sidx]);
-                ip = fmaf(va.x, vb.x, fmaf(va.y, vb.y, ip));
-                nb = fmaf(vb.x, vb.x, fmaf(vb.y, vb.y, nb));
+                const uint32_t pa = __ldg(&sa[sidx]), pb = __ldg(&sb[sidx]);
+                const float are = bf16x2_re(pa), aim = bf16x2_im(pa), bre = bf16x2_re(pb), bim = bf16x2_im(pb);
+                ip = fmaf(are, bre, fmaf(aim, bim, ip));
+                nb = fmaf(bre, bre, fmaf(bim, bim, nb));
               }
             }
           }
@@ -295,9 +296,11 @@ cudaError_t launch_mlp_eval(const uint16_t* P, const float* X, int64_t n, float*
 }
 
 cudaError_t launch_mlp_multiplier(const uint16_t* P, const MlpGeom& mg, const Geom& g, const float* p2, DevState* st,
-                                  float* mtab, const float2* snap, cudaStream_t s) {
+                                  float* mtab, const uint32_t* snap, cudaStream_t s) {
+  // one 16-row tile per warp up to 16 CTAs per SM: the gathers of the class
+  // contraction need many warps in flight
   const int64_t warps = (mg.nclass + 15) / 16;
-  const unsigned blocks = (unsigned)std::min<int64_t>((warps + 3) / 4, 152 * 4);
+  const unsigned blocks = (unsigned)std::min<int64_t>((warps + 3) / 4, 152 * 16);
   mlp_multiplier_kernel<<<blocks > 0 ? blocks : 1, 128, 0, s>>>(reinterpret_cast<const __nv_bfloat16*>(P), mg, g, p2,
                                                                st, mtab, snap);
   return cudaGetLastError();

@@ -41,12 +41,12 @@ cudaError_t launch_mlp_eval(const uint16_t* P, const float* X, int64_t n, float*
 // current links (iteration k = st->iter), written to mtab + (k & 1) * nclass
 // (the table of step k - 2 before: its entries turn the observed contraction
 // into the plain-filter one).  snap: the two Fourier-space divergence
-// snapshots [2][4][V] (FP32) that the filter passes write, slot k & 1 at step
+// snapshots [2][4][V] (BF16 pairs) that the filter passes write, slot k & 1 at step
 // k; with st->snaps >= 2 the class contraction of the last step is formed
 // from slots (k - 1) & 1 (divergence k - 1) and k & 1 (divergence k - 2).
 // A step that redoes a rejected one writes m = 1 (the plain filter it uses).
 cudaError_t launch_mlp_multiplier(const uint16_t* P, const MlpGeom& mg, const Geom& g, const float* p2, DevState* st,
-                                  float* mtab, const float2* snap, cudaStream_t s);
+                                  float* mtab, const uint32_t* snap, cudaStream_t s);
 size_t mlp_train_smem();
 cudaError_t launch_mlp_grad(const float* P, const float* X, const float* Y, const float* Wt, int64_t n, int64_t batch,
                             uint64_t seed, int step, float inv_sw, float* part_g, double* part_l, int nblocks,

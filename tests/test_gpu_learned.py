@@ -289,13 +289,16 @@ def test_mode_log_matches_oracle(torch):
 
 def test_trained_preconditioner_gains_on_slow_fields(torch):
     """The committed network (trained on 16^4 and 24^4 trajectories) against plain
-    FA-SD on held-out rough fields: fewer iterations to theta < 1e-12, same
-    gauge orbit (plaquette unchanged), every accepted step raising F."""
+    FA-SD on twelve held-out rough 16^4 fields (eps = 1, seeds 100-111), to
+    theta < 1e-12: fewer iterations in all, and on nearly every field (one of
+    these fields, seed 105, sits on a plateau of theta near 1e-11 for
+    thousands of steps, which the larger steps lengthen); same gauge orbit
+    (plaquette unchanged); every accepted step raises F."""
     from paper_1206_0675_gb300.preconditioner import DEFAULT_WEIGHTS
     weights = np.load(DEFAULT_WEIGHTS)
     ext = (16, 16, 16, 16)
-    total_plain = total_learned = 0
-    for seed in (104, 105):
+    total_plain = total_learned = wins = 0
+    for seed in range(100, 112):
         U = fields.random_links(ext, eps=1.0, seed=seed)
         with lgf.Lattice(ext, "fp64") as lat:
             lat.set_links(U)
@@ -311,14 +314,18 @@ def test_trained_preconditioner_gains_on_slow_fields(torch):
         assert abs(O.plaquette(U_l) - O.plaquette(U)) < 1e-12
         total_plain += it_p
         total_learned += it_l
-    print(f"iterations to 1e-12 on two held-out 16^4 eps=1 fields: plain {total_plain}, learned {total_learned}")
-    assert total_learned < 0.95 * total_plain
+        wins += it_l < it_p
+    print(f"iterations to 1e-12 on twelve held-out 16^4 eps=1 fields: plain {total_plain}, learned {total_learned}, "
+          f"learned fewer on {wins}")
+    assert total_learned < 0.9 * total_plain
+    assert wins >= 10
 
 
-def test_trained_preconditioner_cost_on_fast_fields(torch):
-    """On smooth fields that plain FA-SD fixes in a few dozen steps the network's
-    larger late steps cost iterations (the momentum classes mix fast and slow
-    modes); the cost stays bounded and the result stays on the gauge orbit."""
+def test_trained_preconditioner_on_fast_fields(torch):
+    """On smooth fields that plain FA-SD fixes in a few dozen steps the network
+    keeps the multiplier near 1 on the classes that contract fast (their own
+    contraction is an input) and costs no iterations; the result stays on the
+    gauge orbit."""
     from paper_1206_0675_gb300.preconditioner import DEFAULT_WEIGHTS
     weights = np.load(DEFAULT_WEIGHTS)
     ext = (16, 16, 16, 16)
@@ -333,5 +340,5 @@ def test_trained_preconditioner_cost_on_fast_fields(torch):
         U_l = lat.get_links()
     print(f"iterations to 1e-12 on a held-out 16^4 eps=0.7 field: plain {it_p}, learned {it_l}")
     assert conv_p and conv_l
-    assert it_l < 2 * it_p
+    assert it_l <= it_p
     assert abs(O.plaquette(U_l) - O.plaquette(U)) < 1e-12
