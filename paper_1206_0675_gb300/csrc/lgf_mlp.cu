@@ -242,29 +242,35 @@ __global__ void __launch_bounds__(128) mlp_multiplier_kernel(const __nv_bfloat16
       x[h][6] = f6;
       float r = 0.f;
       if (have_rate) {
-        // the modes k_mu in {f_mu, L_mu - f_mu} of the class; this lane takes packed field tig
+        // the modes k_mu in {f_mu, L_mu - f_mu} of the class (one value where
+        // f_mu = 0 or 2 f_mu = L_mu); this lane takes packed field tig.  All
+        // sixteen candidate loads are issued before any is used (predicated,
+        // fully unrolled): a loop that waited on each load left the kernel
+        // bound by load latency.
+        int64_t off[4][2];
+        bool two[4];
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+          two[mu] = f[mu] != 0 && 2 * f[mu] != geo.L[mu];
+          off[mu][0] = geo.stride[mu] * f[mu];
+          off[mu][1] = geo.stride[mu] * (geo.L[mu] - f[mu]);
+        }
+        const int64_t fbase = (int64_t)tig * V;
+        uint32_t pa[16], pb[16];
+#pragma unroll
+        for (int m = 0; m < 16; ++m) {
+          const int bx = m & 1, by = (m >> 1) & 1, bz = (m >> 2) & 1, bt = (m >> 3) & 1;
+          const bool ok = (!bx || two[0]) && (!by || two[1]) && (!bz || two[2]) && (!bt || two[3]);
+          const int64_t sidx = fbase + off[0][bx] + off[1][by] + off[2][bz] + off[3][bt];
+          pa[m] = ok ? __ldg(&sa[sidx]) : 0u;
+          pb[m] = ok ? __ldg(&sb[sidx]) : 0u;
+        }
         float ip = 0.f, nb = 0.f;
-        for (int bt = 0; bt < 2; ++bt) {
-          if (bt && (f[3] == 0 || 2 * f[3] == geo.L[3])) continue;
-          const int kt = bt ? geo.L[3] - f[3] : f[3];
-          for (int bz = 0; bz < 2; ++bz) {
-            if (bz && (f[2] == 0 || 2 * f[2] == geo.L[2])) continue;
-            const int kz = bz ? geo.L[2] - f[2] : f[2];
-            for (int by = 0; by < 2; ++by) {
-              if (by && (f[1] == 0 || 2 * f[1] == geo.L[1])) continue;
-              const int ky = by ? geo.L[1] - f[1] : f[1];
-              for (int bx = 0; bx < 2; ++bx) {
-                if (bx && (f[0] == 0 || 2 * f[0] == geo.L[0])) continue;
-                const int kx = bx ? geo.L[0] - f[0] : f[0];
-                const int64_t sidx = (int64_t)tig * V + kx + geo.stride[1] * ky + geo.stride[2] * kz +
-                                     geo.stride[3] * kt;
-                const uint32_t pa = __ldg(&sa[sidx]), pb = __ldg(&sb[sidx]);
-                const float are = bf16x2_re(pa), aim = bf16x2_im(pa), bre = bf16x2_re(pb), bim = bf16x2_im(pb);
-                ip = fmaf(are, bre, fmaf(aim, bim, ip));
-                nb = fmaf(bre, bre, fmaf(bim, bim, nb));
-              }
-            }
-          }
+#pragma unroll
+        for (int m = 0; m < 16; ++m) {
+          const float are = bf16x2_re(pa[m]), aim = bf16x2_im(pa[m]), bre = bf16x2_re(pb[m]), bim = bf16x2_im(pb[m]);
+          ip = fmaf(are, bre, fmaf(aim, bim, ip));
+          nb = fmaf(bre, bre, fmaf(bim, bim, nb));
         }
         ip += __shfl_xor_sync(0xffffffffu, ip, 1);
         nb += __shfl_xor_sync(0xffffffffu, nb, 1);
