@@ -527,31 +527,59 @@ __device__ __forceinline__ void gram_schmidt_factors(double a, double d, double2
   o.i2 = rsqrt_fp64(n2);
 }
 
+// FP32 <-> FP64 conversions on the integer pipe, written from the IEEE 754
+// binary32 / binary64 layouts.  On this GPU the conversion instructions run
+// on the FP64 pipe, which bounds pass C of FP32 lanes; these take sign,
+// rebiased exponent and mantissa apart with integer operations instead.
+// Zero and subnormal inputs give zero; FP64 -> FP32 rounds to nearest with
+// ties away from zero (IEEE rounds ties to even: the two differ only on exact
+// ties) and overflows to infinity.  Non-finite values are not expected here.
+__device__ __forceinline__ double f32_to_f64_int(float x) {
+  const uint32_t b = __float_as_uint(x);
+  const uint64_t sign = (uint64_t)(b >> 31) << 63;
+  const uint32_t e = (b >> 23) & 0xffu;
+  const uint64_t body = ((uint64_t)(e + (1023u - 127u)) << 52) | ((uint64_t)(b & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)(sign | (e == 0u ? 0ull : body)));
+}
+__device__ __forceinline__ float f64_to_f32_int(double x) {
+  const uint64_t b = (uint64_t)__double_as_longlong(x);
+  const uint32_t sign = (uint32_t)(b >> 63) << 31;
+  const int64_t r = (int64_t)(b & 0x7fffffffffffffffull) - ((int64_t)(1023 - 127) << 52) + (1ll << 28);
+  uint32_t f = r <= (1ll << 28) ? 0u : (uint32_t)(r >> 29);
+  if (r > (1ll << 28) && f >= 0x7f800000u) f = 0x7f800000u;
+  return __uint_as_float(sign | f);
+}
+__device__ __forceinline__ double2 c_f32_to_f64_int(float2 v) { return make_double2(f32_to_f64_int(v.x), f32_to_f64_int(v.y)); }
+__device__ __forceinline__ float2 c_f64_to_f32_int(double2 v) { return make_float2(f64_to_f32_int(v.x), f64_to_f32_int(v.y)); }
+
 // Rows u, v of g = reunitarize(1 + X) in the field precision R; the
 // Gram-Schmidt factors are FP64 in both.  FP64 fields take u = i1 r1 and
 // v = i2 w in FP64.  FP32 fields, whose rows are stored in FP32, apply the
 // FP64 factors in FP32: u = fl(i1) r1 with r1 the FP32 entries of the
 // filtered field itself, v = fl(i2) fl(w) -- within one FP32 rounding of the
-// FP64 product, and without the FP64 multiplies and most of the FP64 -> FP32
-// conversions of rounding each FP64 entry.
+// FP64 product, without the FP64 multiplies -- and take their values to and
+// from FP64 on the integer pipe.
 template <typename R>
 __device__ __forceinline__ void gauge_rows(C2<R> f0, C2<R> f1, C2<R> f2, C2<R> f3, C2<R> u[3], C2<R> v[3]) {
   GSFactors o;
-  gram_schmidt_factors((double)f0.x, (double)f0.y, ccast<double, R>(f1), ccast<double, R>(f2), ccast<double, R>(f3),
-                       o);
-  const R i1 = (R)o.i1, i2 = (R)o.i2;
-  u[0] = mkc<R>(i1, f0.x * i1);
-  u[1] = cscale<R>(f1, i1);
-  u[2] = cscale<R>(f2, i1);
   if constexpr (sizeof(R) == sizeof(double)) {
+    gram_schmidt_factors(f0.x, f0.y, f1, f2, f3, o);
+    u[0] = mkc<R>(o.i1, f0.x * o.i1);
+    u[1] = cscale<R>(f1, o.i1);
+    u[2] = cscale<R>(f2, o.i1);
 #pragma unroll
     for (int j = 0; j < 3; ++j) v[j] = cscale<double>(o.w[j], o.i2);
   } else {
+    gram_schmidt_factors(f32_to_f64_int(f0.x), f32_to_f64_int(f0.y), c_f32_to_f64_int(f1), c_f32_to_f64_int(f2),
+                         c_f32_to_f64_int(f3), o);
+    const float i1 = f64_to_f32_int(o.i1), i2 = f64_to_f32_int(o.i2);
+    u[0] = mkc<R>(i1, f0.x * i1);
+    u[1] = cscale<R>(f1, i1);
+    u[2] = cscale<R>(f2, i1);
 #pragma unroll
-    for (int j = 0; j < 3; ++j) v[j] = cscale<R>(ccast<R, double>(o.w[j]), i2);
+    for (int j = 0; j < 3; ++j) v[j] = cscale<R>(c_f64_to_f32_int(o.w[j]), i2);
   }
 }
-
 
 // Rows 1 and 2 of g = exp(X) (the exponential of Eq. (eq:gx) evaluated
 // exactly instead of to first order), for X traceless anti-Hermitian packed

@@ -5,6 +5,8 @@ exact-exponential and plain-SD variants, and scans over alpha.
     python -m paper_1206_0675_gb300.evaluate --lattice 32 --eps 0.7 --seeds 100-107 [--tol 1e-15]
     python -m paper_1206_0675_gb300.evaluate --lattice 16 --eps 1.0 --seeds 100-101 \
         --modes fp64,fp64_exp,fp64_sd --alphas 0.04,0.06,0.08,0.1,0.12 --tol 1e-12
+    python -m paper_1206_0675_gb300.evaluate --run-steps 3 --lattice 32 --eps 1.0 --seeds 0 \
+        --modes fp32 --store12 --decomps 2d2d     # a few steps of one lattice (profiling case)
 
 Prints one JSON line per configuration and a summary line.
 """
@@ -120,6 +122,26 @@ def kernel_table(ext, U, steps=20, warmup=5, peak_gbs=None, decomps=("2d2d",), u
     return out
 
 
+def run_steps(ext, eps, seed, mode, store12, decomp, steps, weights):
+    """A few lgf_step calls on one lattice with a fixed plan: the small case a
+    profiler captures one kernel of."""
+    import torch
+    prec = {"fp64": "fp64", "fp32": "fp32", "mixed": "mixed", "fp32_learned": "fp32", "fp64_learned": "fp64"}[mode]
+    learned = mode.endswith("_learned")
+    U = fields.random_links(ext, eps, seed)
+    with lgf.Lattice(ext, prec, store12=store12, learned=learned) as lat:
+        if learned:
+            lat.load_preconditioner(weights)
+        lat.set_fft_decomposition(decomp)
+        lat.set_links(U)
+        for _ in range(steps):
+            lat.step(0.08)
+        torch.cuda.synchronize()
+        F, th = lat.measure()
+    print(json.dumps({"extents": ext, "mode": mode, "store12": store12, "decomposition": decomp, "steps": steps,
+                      "F": F, "theta": th}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--lattice", type=int, default=32)
@@ -137,9 +159,17 @@ def main():
                     help="decompositions of the 4D transform for --kernels (2d2d,1d4,3d1d)")
     ap.add_argument("--switch", type=float, default=None, help="switch level of the mixed modes")
     ap.add_argument("--alphas", default="0.08", help="comma-separated step sizes alpha (a scan if several)")
+    ap.add_argument("--run-steps", type=int, default=0,
+                    help="only run this many steps of one lattice (first seed, first mode of fp64, fp32, mixed, "
+                         "fp32_learned, fp64_learned; first of --decomps) and print F and theta")
+    ap.add_argument("--store12", action="store_true", help="with --run-steps: 12-real link storage")
     args = ap.parse_args()
     a, b = (int(v) for v in args.seeds.split("-")) if "-" in args.seeds else (int(args.seeds),) * 2
     ext = tuple(int(v) for v in args.extents.split(",")) if args.extents else (args.lattice,) * 4
+    if args.run_steps:
+        run_steps(ext, args.eps, a, args.modes.split(",")[0], args.store12, args.decomps.split(",")[0], args.run_steps,
+                  np.load(args.weights))
+        return
     if args.kernels:
         peak = None
         try:
