@@ -191,12 +191,20 @@ __global__ void __launch_bounds__(128) mlp_multiplier_kernel(const __nv_bfloat16
                                                              float* __restrict__ mtab_base,
                                                              const uint32_t* __restrict__ snap) {
   __shared__ MlpSmem S;
+  __shared__ float sf[3];  // the features shared by every class, formed once per CTA
   mlp_load_smem(S, P);
-  const double theta = st->theta;
-  const double theta_prev = st->theta_prev;
   const int iter = st->iter;
   const int redo = st->revert;  // the measurement after the step assigns revert afresh
   const bool have_rate = snap != nullptr && st->snaps >= 2;
+  if (threadIdx.x == 0) {
+    // FP64 logarithms: one thread per CTA, not every thread (they would
+    // occupy the FP64 pipe for most of the kernel)
+    const double theta = st->theta, theta_prev = st->theta_prev;
+    const float fb = theta > 0.0 ? (float)(floor(2.0 * log10(theta)) * 0.5) : -20.f;
+    sf[0] = -fb / 16.f;
+    sf[1] = fminf((float)iter / MLP_ITER_SCALE, 1.f);
+    sf[2] = iter > 0 ? mlp_rate_feature(theta, theta_prev) : 0.f;
+  }
   __syncthreads();
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     st->use_m = redo ? 0 : 1;
@@ -206,10 +214,7 @@ __global__ void __launch_bounds__(128) mlp_multiplier_kernel(const __nv_bfloat16
   const int64_t V = geo.V;
   const uint32_t* sa = snap + (int64_t)((iter + 1) & 1) * 4 * V;  // divergence k - 1
   const uint32_t* sb = snap + (int64_t)(iter & 1) * 4 * V;        // divergence k - 2
-  const float fb = theta > 0.0 ? (float)(floor(2.0 * log10(theta)) * 0.5) : -20.f;
-  const float f4 = -fb / 16.f;
-  const float f5 = fminf((float)iter / MLP_ITER_SCALE, 1.f);
-  const float f6 = iter > 0 ? mlp_rate_feature(theta, theta_prev) : 0.f;
+  const float f4 = sf[0], f5 = sf[1], f6 = sf[2];
   const int lane = threadIdx.x & 31, g = lane >> 2, tig = lane & 3;
   const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;

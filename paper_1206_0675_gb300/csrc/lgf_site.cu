@@ -5,6 +5,7 @@
 //   * layout conversion, SU(3) validation, the momentum filter table (k1).
 // One thread per lattice site; link arrays are structure-of-arrays so that a
 // warp touches 32 consecutive sites of one matrix element per load.
+#include <algorithm>
 #include <cmath>
 
 #include "lgf_internal.h"
@@ -627,49 +628,64 @@ cudaError_t launch_set_identity(const Geom& g, C2<R>* field, cudaStream_t s) {
 // SU(3) validation of user links
 // ---------------------------------------------------------------------------
 
-__global__ void su3_defect_kernel(const double2* __restrict__ aos, int64_t nmat, unsigned long long* out) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ double su3_defect_of(const double2* __restrict__ mat) {
+  double2 m[3][3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) m[r][c] = __ldg(&mat[r * 3 + c]);
   double d = 0.0;
-  if (i < nmat) {
-    double2 m[3][3];
+  // U U^dag is Hermitian: its upper triangle holds every distinct entry
 #pragma unroll
-    for (int r = 0; r < 3; ++r)
+  for (int r = 0; r < 3; ++r)
 #pragma unroll
-      for (int c = 0; c < 3; ++c) m[r][c] = __ldg(&aos[i * 9 + r * 3 + c]);
-    // U U^dag is Hermitian: its upper triangle holds every distinct entry
+    for (int c = r; c < 3; ++c) {
+      double2 acc = mkc<double>(0.0, 0.0);
 #pragma unroll
-    for (int r = 0; r < 3; ++r)
+      for (int k = 0; k < 3; ++k) acc = cfmac<double>(m[r][k], m[c][k], acc);
+      if (r == c) acc.x -= 1.0;
+      d = fmax(d, fmax(fabs(acc.x), fabs(acc.y)));
+    }
+  double2 cr[3];
+  su3_third_row<double>(m[0], m[1], cr);  // conj(r0 x r1)
+  // det = r2 . (r0 x r1) = sum_j r2_j conj(cr_j)
+  double2 det = mkc<double>(0.0, 0.0);
 #pragma unroll
-      for (int c = r; c < 3; ++c) {
-        double2 acc = mkc<double>(0.0, 0.0);
+  for (int j = 0; j < 3; ++j) det = cfmac<double>(m[2][j], cr[j], det);
+  d = fmax(d, sqrt((det.x - 1.0) * (det.x - 1.0) + det.y * det.y));
+  bool finite = true;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) acc = cfmac<double>(m[r][k], m[c][k], acc);
-        if (r == c) acc.x -= 1.0;
-        d = fmax(d, fmax(fabs(acc.x), fabs(acc.y)));
-      }
-    double2 cr[3];
-    su3_third_row<double>(m[0], m[1], cr);  // conj(r0 x r1)
-    // det = r2 . (r0 x r1) = sum_j r2_j conj(cr_j)
-    double2 det = mkc<double>(0.0, 0.0);
+  for (int r = 0; r < 3; ++r)
 #pragma unroll
-    for (int j = 0; j < 3; ++j) det = cfmac<double>(m[2][j], cr[j], det);
-    d = fmax(d, sqrt((det.x - 1.0) * (det.x - 1.0) + det.y * det.y));
-    bool finite = true;
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) finite = finite && isfinite(m[r][c].x) && isfinite(m[r][c].y);
-    if (!finite || !isfinite(d)) d = INFINITY;
-  }
+    for (int c = 0; c < 3; ++c) finite = finite && isfinite(m[r][c].x) && isfinite(m[r][c].y);
+  return (!finite || !isfinite(d)) ? INFINITY : d;
+}
+
+// Grid-stride over the matrices; the maximum of a CTA goes to *out by one
+// atomic (a few thousand in all, instead of one per warp on one address).
+__global__ void su3_defect_kernel(const double2* __restrict__ aos, int64_t nmat, unsigned long long* out) {
+  double d = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nmat; i += (int64_t)gridDim.x * blockDim.x)
+    d = fmax(d, su3_defect_of(aos + i * 9));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) d = fmax(d, __shfl_down_sync(0xffffffffu, d, o));
-  if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(d));
+  __shared__ double wm[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  if (lane == 0) wm[warp] = d;
+  __syncthreads();
+  if (warp == 0) {
+    d = lane < nw ? wm[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) d = fmax(d, __shfl_down_sync(0xffffffffu, d, o));
+    if (lane == 0) atomicMax(out, (unsigned long long)__double_as_longlong(d));
+  }
 }
 
 cudaError_t launch_su3_defect(const double* aos, int64_t nmat, unsigned long long* out_bits, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(out_bits, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
-  su3_defect_kernel<<<(unsigned)((nmat + CONV_THREADS - 1) / CONV_THREADS), CONV_THREADS, 0, s>>>(
+  const int64_t blocks = std::min<int64_t>((nmat + CONV_THREADS - 1) / CONV_THREADS, 152 * 8);
+  su3_defect_kernel<<<(unsigned)(blocks > 0 ? blocks : 1), CONV_THREADS, 0, s>>>(
       reinterpret_cast<const double2*>(aos), nmat, out_bits);
   return cudaGetLastError();
 }
