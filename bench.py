@@ -43,6 +43,8 @@ EXT = (32, 32, 32, 32)
 EPS = 1.0
 ALPHA = 0.08
 TOL = 1e-15
+OR_OMEGA = 1.7      # overrelaxation parameter of the overrelaxation measurements
+OR_CHECK = 10       # their sweeps between measurements of theta
 METRIC = "FA-SD iters/s at 32^4 (plain FP64, 18-real links)"
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
@@ -479,6 +481,56 @@ def run_lgf(args, rank, world, local_rank):
                  "site_updates_per_s": float((vols * it_b).sum() / dt_b), "classes": classes,
                  "workload": "16x8^4, 16x12^4, 16x16^4, 8x16^3x32, 8x24^4; eps ~ U[0.3,1.0]; one graph launch"}
 
+    # ---- overrelaxation (the lower-memory method of Sec. 3.2) ---------------
+    orx = None
+    if not args.no_or:
+        orx = {"omega": OR_OMEGA, "field": f"32^4 eps={EPS} seed={rank}",
+               "note": "checkerboard sweeps (even colour, then odd) of Cabibbo-Marinari hits with "
+                       "Mandula-Ogilvie overrelaxation; each region is one lgf_or_sweep call of K sweeps "
+                       "(2K colour kernels and one measurement)"}
+        for mode, kw, real_bytes, rows in (("fp64_18", dict(precision="fp64"), 8, 3),
+                                          ("fp32_12", dict(precision="fp32", store12=True), 4, 2)):
+            Lo = lgf.Lattice(EXT, **kw)
+            Lo.set_links(U)
+            Lo.or_sweep(OR_OMEGA, args.warmup)
+            torch.cuda.synchronize()
+            t_or = []
+            for _ in range(args.reps):
+                st = torch.cuda.current_stream()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(st)
+                Lo.or_sweep(OR_OMEGA, args.steps)
+                e1.record(st)
+                torch.cuda.synchronize()
+                t_or.append(e0.elapsed_time(e1))
+            Lo.close()
+            ms_sw = float(np.median(t_or)) / args.steps
+            byt_or = accounting.or_bytes_per_site_sweep(real_bytes, rows)
+            ops_or = accounting.or_ops_per_site_sweep(rows)
+            rec = {"sweeps_per_s": 1e3 / ms_sw, "ms_per_sweep": ms_sw, "site_updates_per_s": V * 1e3 / ms_sw,
+                   "bytes_per_site_sweep": byt_or, "ops_per_site_sweep": ops_or,
+                   "hbm_gbs": byt_or * V / (ms_sw * 1e-3) / 1e9,
+                   "hbm_frac": byt_or * V / (ms_sw * 1e-3) / 1e9 / hbm_peak}
+            if real_bytes == 8:
+                rec["fp64_tflops"] = 2 * ops_or * V / (ms_sw * 1e-3) / 1e12
+                rec["fp64_frac"] = rec["fp64_tflops"] / FP64_PEAK_TFLOPS
+            orx[mode] = rec
+        if not args.no_tol:
+            for mode, kw in (("fix_fp64_18", dict(precision="fp64")),
+                             ("fix_mixed_12", dict(precision="mixed", store12=True))):
+                Lo = lgf.Lattice(EXT, **kw)
+                Lo.set_links(U)
+                Lo.or_fix(TOL, 1, OR_OMEGA, OR_CHECK)       # builds the loop graph
+                Lo.set_links(U)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                n, F, th, conv = Lo.or_fix(TOL, args.or_max_sweeps, OR_OMEGA, OR_CHECK)
+                torch.cuda.synchronize()
+                orx[mode] = {"seconds": time.perf_counter() - t0, "sweeps": n, "F": F, "theta": th,
+                             "converged": conv, "tol": TOL, "check_every": OR_CHECK}
+                Lo.close()
+
     # ---- CPU oracle on the host cores (rank 0, N = 1 only) ------------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -513,7 +565,7 @@ def run_lgf(args, rank, world, local_rank):
                        "l2": "no flush needed: each step streams 604 MB of links (> 129 MB L2)"},
             "site_updates_per_s": value * V,
             "per_kernel": per_kernel, "roofline": roofline, "step_hbm": step_hbm, "fp32_12": fp32,
-            "time_to_tol": ttt, "batch64": batch, "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
+            "time_to_tol": ttt, "batch64": batch, "overrelaxation": orx, "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
             "gpu_launches": KERNELS_PER_STEP[decomp] * args.steps * args.reps,
             "autotune": {"fft_decomposition": decomp, "fields_per_cta_xy": chosen["fields_per_cta_xy"],
                          "x_columns_zt": chosen["x_columns_zt"], "threads": chosen["threads"],
@@ -540,6 +592,8 @@ def main():
     ap.add_argument("--no-tol", action="store_true", help="skip the time-to-threshold runs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-configuration batch")
+    ap.add_argument("--no-or", action="store_true", help="skip the overrelaxation measurements")
+    ap.add_argument("--or-max-sweeps", type=int, default=20000)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

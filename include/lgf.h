@@ -169,6 +169,42 @@ lgf_status lgf_measure(lgf_handle h, double* F, double* theta);
 lgf_status lgf_fix(lgf_handle h, double theta_tol, int32_t max_iter, double alpha, int32_t* iters, double* F,
                    double* theta);
 
+/* Overrelaxation gauge fixing, the lower-memory alternative that Sec. 3.2
+ * names beside the Fourier-accelerated method.  The paper gives no algorithm
+ * for it; this is the published one it refers to: F of Sec. 2, eq. 3, is
+ * maximised one site at a time over all sites of one checkerboard colour at
+ * once, the SU(3) maximisation done in the SU(2) subgroups (0,1), (0,2),
+ * (1,2) in turn (Cabibbo and Marinari, 1982), each SU(2) maximiser r replaced
+ * by r^omega ~ 1 + omega (r - 1) projected back onto SU(2) (Mandula and
+ * Ogilvie, 1990).  One sweep is the even colour (x + y + z + t even), then
+ * the odd one; each colour applies the gauge transformation of Sec. 2, eq. 2,
+ * with g = 1 on the other colour, so G (LGF_TRACK_G, lgf_get_transform)
+ * accumulates it like the Fourier-accelerated steps.
+ * Needs every extent even and a handle without LGF_LEARNED, else
+ * LGF_E_UNSUPPORTED.  The site algebra runs in the link precision; the
+ * F/theta measurement is the one of lgf_measure.  After overrelaxation
+ * sweeps lgf_get_gauge gives LGF_E_STATE (no g of a single step describes
+ * them).
+ *
+ * lgf_or_sweep: nsweeps >= 0 sweeps with 1 <= omega < 2 (else LGF_E_ARG),
+ * then one measurement; the update counter advances by nsweeps.
+ * Asynchronous, except that an LGF_MIXED handle in its FP32 phase reads
+ * theta first and switches to FP64 below the switch level, as lgf_step does. */
+lgf_status lgf_or_sweep(lgf_handle h, double omega, int32_t nsweeps);
+
+/* lgf_or_fix: measure, then while theta >= theta_tol and fewer than
+ * max_sweeps sweeps: check_every sweeps and a measurement, all on the device
+ * (CUDA graph WHILE node).  The count may pass max_sweeps by less than
+ * check_every.  LGF_MIXED runs the FP32 phase to the switch level, rebuilds
+ * the FP64 links as lgf_fix does and continues in FP64.  sweeps, F, theta
+ * (each may be NULL) receive the sweep count and the final measurement; the
+ * trace (lgf_set_trace) holds entry i after i sweeps at the measured counts.
+ * Returns LGF_E_NOTCONV when max_sweeps is reached, LGF_E_ARG unless
+ * 1 <= omega < 2, check_every >= 1, max_sweeps >= 0 and theta_tol >= 0.
+ * Synchronises. */
+lgf_status lgf_or_fix(lgf_handle h, double theta_tol, int32_t max_sweeps, double omega, int32_t check_every,
+                      int32_t* sweeps, double* F, double* theta);
+
 /* Copy out the accumulated transform G(x) = g_k(x) ... g_1(x) (site layout,
  * FP64): the product of the gauge transformations of Sec. 2, eq. 2, applied
  * by the steps since lgf_set_links, so that the current links equal

@@ -148,3 +148,31 @@ def paper_fft_flops_per_site(extents) -> float:
     import math
     lx, ly, lz, lt = extents
     return 5.0 * (math.log2(lx * ly) + math.log2(lz * lt))
+
+
+def or_bytes_per_site_sweep(real_bytes: int, rows: int, track_G: bool = False) -> int:
+    """Compulsory DRAM bytes per site of one overrelaxation sweep: each colour
+    reads and writes every link of the lattice once (the forward links of its
+    own sites and the backward links of theirs), i.e. 2 x 2 x 4 S_L per site
+    and sweep; G, when tracked, is read and written once per sweep."""
+    S_L = rows * 3 * 2 * real_bytes
+    G = 2 * 9 * 2 * real_bytes if track_G else 0
+    return 2 * 2 * 4 * S_L + G
+
+
+def or_ops_per_site_sweep(rows: int = 3, track_G: bool = False) -> int:
+    """Floating-point instructions (lane precision; FMA, MUL, ADD one each) per
+    site of one overrelaxation sweep (every site is updated once per sweep):
+      * w(x): 8 links summed, 18 each, plus the third rows of 12-real links (24);
+      * the Cabibbo-Marinari hit: 3 subgroups of 35 (components, two
+        normalisations with rsqrt counted as 6) and the rotations of M and g,
+        18 per column pair: 3 (M, first subgroup) + 3 + 3 (g) + 1 (M, second
+        subgroup, one row of two columns: 10 each) -> 54 + 20 + 54 + 54;
+      * the 8 link products: rows 1-2 (72) and the third row (24) each, plus
+        the third rows the forward products need from 12-real links (24);
+      * G <- g G: 108 when tracked."""
+    recon = 24 if rows == 2 else 0
+    w = 8 * (18 + recon)
+    hit = 3 * 35 + 54 + 20 + 54 + 54
+    products = 8 * (72 + 24) + 4 * recon
+    return w + hit + products + (108 if track_G else 0)

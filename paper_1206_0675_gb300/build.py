@@ -18,7 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblgf.so")
-SOURCES = ["lgf_site.cu", "lgf_fft.cu", "lgf_api.cu", "lgf_static.cu", "lgf_mlp.cu", "lgf_batch.cu"]
+SOURCES = ["lgf_site.cu", "lgf_fft.cu", "lgf_api.cu", "lgf_static.cu", "lgf_mlp.cu", "lgf_batch.cu", "lgf_or.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -42,6 +42,11 @@ template <typename R> struct Lane {
   int decomp = FFT_2D2D;   // decomposition of the 4D transform (lgf_set_fft_decomposition, lgf_autotune)
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
+  // overrelaxation loop graph and the parameters captured in it
+  cudaGraphExec_t or_exec = nullptr;
+  cudaGraph_t or_graph = nullptr;
+  double or_omega = NAN;
+  int or_check = 0;
   bool active = false;
   // learned multiplier and mode log
   float* mtab = nullptr;   // multiplier per momentum class
@@ -176,8 +181,16 @@ template <typename R> void set_decomp(Lane<R>& L, int decomposition) {
   L.decomp = decomposition;
 }
 
+template <typename R> void drop_or_graph(Lane<R>& L) {
+  if (L.or_exec) cudaGraphExecDestroy(L.or_exec);
+  if (L.or_graph) cudaGraphDestroy(L.or_graph);
+  L.or_exec = nullptr;
+  L.or_graph = nullptr;
+}
+
 template <typename R> void free_lane(lgf_ctx* h, Lane<R>& L) {
   drop_graph(L);
+  drop_or_graph(L);
   for (void* p : {(void*)L.U, (void*)L.U2, (void*)L.g, (void*)L.D, (void*)L.K, (void*)L.tw, (void*)L.pos,
                   (void*)L.G, (void*)L.p2f, (void*)L.Dlog, (void*)L.Dprev, (void*)L.Dprev2})
     h->mem.put(p);
@@ -516,6 +529,49 @@ template <typename R> lgf_status ensure_graph(lgf_ctx* h, Lane<R>& L) {
   return LGF_OK;
 }
 
+// n overrelaxation sweeps (even colour, then odd) of a lane's current links,
+// with G <- g G where the lane tracks G.
+template <typename R> cudaError_t enqueue_or_sweeps(lgf_ctx* h, Lane<R>& L, double omega, int n, cudaStream_t s) {
+  C2<R>* U1 = L.fused ? L.U2 : nullptr;
+  for (int k = 0; k < n; ++k)
+    for (int parity = 0; parity < 2; ++parity) {
+      cudaError_t e = L.rows == 3 ? launch_or_half_sweep<R, 3>(h->geom, L.U, U1, h->st, L.G, parity, omega, s)
+                                  : launch_or_half_sweep<R, 2>(h->geom, L.U, U1, h->st, L.G, parity, omega, s);
+      if (e != cudaSuccess) return e;
+    }
+  return cudaSuccess;
+}
+
+// Build (once per omega and check_every) the overrelaxation loop graph
+// WHILE(theta >= tol && sweeps < max) { check_every sweeps; measure }.
+template <typename R> lgf_status ensure_or_graph(lgf_ctx* h, Lane<R>& L, double omega, int check_every) {
+  if (L.or_exec && L.or_omega == omega && L.or_check == check_every) return LGF_OK;
+  drop_or_graph(L);
+  cudaGraph_t graph;
+  LGF_CK(h, cudaGraphCreate(&graph, 0));
+  L.or_graph = graph;
+  cudaGraphConditionalHandle cond;
+  LGF_CK(h, cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+  np.conditional.handle = cond;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  LGF_CK(h, cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np));
+  LGF_CK(h, cudaStreamBeginCaptureToGraph(h->cap_stream, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeRelaxed));
+  cudaError_t e = enqueue_or_sweeps<R>(h, L, omega, check_every, h->cap_stream);
+  if (e == cudaSuccess) e = enqueue_measure<R>(h, L, check_every, (unsigned long long)cond, 1, h->cap_stream);
+  cudaGraph_t captured = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &captured);
+  if (e != cudaSuccess) return fail_cuda(h, e, "capture of the overrelaxation body");
+  if (e2 != cudaSuccess) return fail_cuda(h, e2, "cudaStreamEndCapture");
+  LGF_CK(h, cudaGraphInstantiate(&L.or_exec, graph, 0));
+  L.or_omega = omega;
+  L.or_check = check_every;
+  return LGF_OK;
+}
+
 lgf_status sync_state(lgf_ctx* h) {
   LGF_CK(h, cudaMemcpyAsync(h->st_host, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
   LGF_CK(h, cudaStreamSynchronize(h->stream));
@@ -577,7 +633,11 @@ template <typename R> lgf_status repair_links(lgf_ctx* h, Lane<R>& L) {
   return sync_state(h);
 }
 
-template <typename R> lgf_status run_loop(lgf_ctx* h, Lane<R>& L, double tol, int max_iter, int reset) {
+// The device loop of a lane until theta < tol or max_iter updates: the
+// Fourier-accelerated body, or with or_check > 0 the overrelaxation body of
+// or_check sweeps with parameter or_omega.
+template <typename R> lgf_status run_loop(lgf_ctx* h, Lane<R>& L, double tol, int max_iter, int reset,
+                                          double or_omega = 0.0, int or_check = 0) {
   const bool f64 = sizeof(R) == sizeof(double);
   LGF_CK(h, launch_set_state(h->st, tol, max_iter, reset, h->hist_cap, h->hist_F, h->hist_T, h->stream,
                              h->hist_flags, h->hist_defect, f64 ? h->defect_bound64 : h->defect_bound32,
@@ -598,7 +658,7 @@ template <typename R> lgf_status run_loop(lgf_ctx* h, Lane<R>& L, double tol, in
     }
     if (!(std::isfinite(S.F) && std::isfinite(S.theta))) return LGF_OK;
     if ((S.theta < tol || S.iter >= max_iter) && !S.revert) return LGF_OK;
-    s = ensure_graph<R>(h, L);
+    s = or_check > 0 ? ensure_or_graph<R>(h, L, or_omega, or_check) : ensure_graph<R>(h, L);
     if (s != LGF_OK) return s;
     // the graph's undo node is off at launch: a rejected step left over from
     // an earlier launch (stopped by the defect guard) is undone here first
@@ -606,7 +666,7 @@ template <typename R> lgf_status run_loop(lgf_ctx* h, Lane<R>& L, double tol, in
       cudaError_t eu = enqueue_body<R>(h, L, 0, 0, h->stream, PART_UNDO);
       if (eu != cudaSuccess) return fail_cuda(h, eu, "undo of a rejected step");
     }
-    LGF_CK(h, cudaGraphLaunch(L.exec, h->stream));
+    LGF_CK(h, cudaGraphLaunch(or_check > 0 ? L.or_exec : L.exec, h->stream));
     if ((s = sync_state(h)) != LGF_OK) return s;
   }
 }
@@ -675,6 +735,19 @@ struct MlpScratch {
     if (loss) cudaFreeAsync(loss, s);
   }
 };
+
+lgf_status finish_fix(lgf_ctx* h, double theta_tol, int32_t* iters, double* F, double* theta);
+
+// Overrelaxation needs a checkerboard (every extent even); the learned
+// multiplier belongs to the Fourier-accelerated filter and is not combined
+// with it.
+lgf_status or_supported(lgf_ctx* h) {
+  for (int mu = 0; mu < 4; ++mu)
+    if (h->geom.L[mu] % 2 != 0)
+      return fail(h, LGF_E_UNSUPPORTED, "overrelaxation needs every extent even (checkerboard colours)");
+  if (h->learned) return fail(h, LGF_E_UNSUPPORTED, "overrelaxation does not run on LGF_LEARNED handles");
+  return LGF_OK;
+}
 }  // namespace
 
 // ===========================================================================
@@ -952,6 +1025,69 @@ lgf_status lgf_fix(lgf_handle h, double theta_tol, int32_t max_iter, double alph
     if ((s = run_loop<double>(h, h->d, theta_tol, max_iter, 0)) != LGF_OK) return s;
     h->have_g = h->have_g || h->st_host->iter > 0;
   }
+  return finish_fix(h, theta_tol, iters, F, theta);
+}
+
+lgf_status lgf_or_sweep(lgf_handle h, double omega, int32_t nsweeps) {
+  NvtxRange nvtx_("lgf_or_sweep");
+  lgf_status s = check_handle(h);
+  if (s != LGF_OK) return s;
+  if (!h->have_links) return fail(h, LGF_E_STATE, "no links set");
+  if (!(omega >= 1.0 && omega < 2.0) || nsweeps < 0) return fail(h, LGF_E_ARG, "need 1 <= omega < 2, nsweeps >= 0");
+  if ((s = or_supported(h)) != LGF_OK) return s;
+  if (h->prec == LGF_MIXED && h->phase == 32) {
+    // sweeps from links with theta below the switch level run in FP64
+    if ((s = sync_state(h)) != LGF_OK) return s;
+    const double th = h->st_host->theta;
+    if (std::isfinite(th) && th < h->switch_theta && (s = switch_to_fp64(h)) != LGF_OK) return s;
+  }
+  cudaError_t e = h->phase == 64 ? enqueue_or_sweeps<double>(h, h->d, omega, nsweeps, h->stream)
+                                 : enqueue_or_sweeps<float>(h, h->f, omega, nsweeps, h->stream);
+  if (e == cudaSuccess)
+    e = h->phase == 64 ? enqueue_measure<double>(h, h->d, nsweeps, 0, 0, h->stream)
+                       : enqueue_measure<float>(h, h->f, nsweeps, 0, 0, h->stream);
+  if (e != cudaSuccess) return fail_cuda(h, e, "lgf_or_sweep");
+  h->have_g = false;  // g of the last Fourier-accelerated step no longer describes the links
+  return LGF_OK;
+}
+
+lgf_status lgf_or_fix(lgf_handle h, double theta_tol, int32_t max_sweeps, double omega, int32_t check_every,
+                      int32_t* sweeps, double* F, double* theta) {
+  NvtxRange nvtx_("lgf_or_fix");
+  lgf_status s = check_handle(h);
+  if (s != LGF_OK) return s;
+  if (!h->have_links) return fail(h, LGF_E_STATE, "no links set");
+  if (!(theta_tol >= 0.0) || max_sweeps < 0 || !(omega >= 1.0 && omega < 2.0) || check_every < 1)
+    return fail(h, LGF_E_ARG, "bad overrelaxation fix arguments");
+  if ((s = or_supported(h)) != LGF_OK) return s;
+  h->repairs = 0;
+  if (h->phase == 32) {
+    NvtxRange phase32("FP32 phase");
+    const double tol1 = h->prec == LGF_MIXED ? std::max(theta_tol, h->switch_theta) : theta_tol;
+    if ((s = run_loop<float>(h, h->f, tol1, max_sweeps, 1, omega, check_every)) != LGF_OK) return s;
+    const DevState& S = *h->st_host;
+    if (h->prec == LGF_MIXED && std::isfinite(S.theta) && S.theta < tol1 && theta_tol < tol1 &&
+        S.iter < max_sweeps) {
+      if ((s = switch_to_fp64(h)) != LGF_OK) return s;
+    }
+  } else {
+    LGF_CK(h, launch_set_state(h->st, theta_tol, max_sweeps, 1, h->hist_cap, h->hist_F, h->hist_T, h->stream,
+                               h->hist_flags, h->hist_defect, h->defect_bound64, TRACE_FP64));
+  }
+  if (h->phase == 64) {
+    NvtxRange phase64("FP64 phase");
+    if ((s = run_loop<double>(h, h->d, theta_tol, max_sweeps, 0, omega, check_every)) != LGF_OK) return s;
+  }
+  h->have_g = false;
+  return finish_fix(h, theta_tol, sweeps, F, theta);
+}
+
+}  // extern "C"
+
+namespace {
+// Results of a finished fix (either method): counts, F, theta, the trace
+// copied to the caller's buffers, and the status.
+lgf_status finish_fix(lgf_ctx* h, double theta_tol, int32_t* iters, double* F, double* theta) {
   const DevState& S = *h->st_host;
   if (iters) *iters = S.iter;
   if (F) *F = S.F;
@@ -971,6 +1107,9 @@ lgf_status lgf_fix(lgf_handle h, double theta_tol, int32_t max_iter, double alph
   if (S.theta >= theta_tol) return fail(h, LGF_E_NOTCONV, "max_iter reached before theta < tol");
   return LGF_OK;
 }
+}  // namespace
+
+extern "C" {
 
 lgf_status lgf_get_transform(lgf_handle h, double* G, int where) {
   lgf_status s = check_handle(h);

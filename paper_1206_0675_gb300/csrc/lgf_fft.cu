@@ -483,20 +483,6 @@ __global__ void __launch_bounds__(512) fft_xyz_kernel(Geom g, FFTDir dx, FFTDir 
 // Gram-Schmidt on rows 1-2, row 3 = (a x b)^* as in Sec. 3.2)
 // ---------------------------------------------------------------------------
 
-// 1/sqrt(x) in FP64 for finite x > 0: the hardware estimate of PTX
-// rsqrt.approx.ftz.f64 refined by one third-order Householder step for
-// f(y) = y^-2 - x.  With e = 1 - x y0^2 the exact value is
-// y0 (1 - e)^(-1/2) = y0 (1 + e/2 + 3e^2/8 + 5e^3/16 + ...); keeping the
-// terms to e^2 leaves a relative error of (5/16) e^3, below 2^-60 for an
-// estimate within 2^-20, so the result is within rounding of 1/sqrt(x).
-// Five FP64 operations after the estimate.
-__device__ __forceinline__ double rsqrt_fp64(double x) {
-  double y;
-  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
-  const double e = fma(-(x * y), y, 1.0);
-  return fma(y * e, fma(0.375, e, 0.5), y);
-}
-
 // f0 = (Im D11, Im D22), f1 = D12, f2 = D13, f3 = D23 of the filtered field.
 // Rows of 1 + X: r1 = (1 + i a, f1, f2) and r2 = (-conj f1, 1 + i d, f3)
 // with a = Re f0, d = Im f0.  Gram-Schmidt: u = r1 / |r1| and
@@ -561,8 +547,8 @@ __device__ __forceinline__ float2 c_f64_to_f32_int(double2 v) { return make_floa
 // from FP64 on the integer pipe.
 template <typename R>
 __device__ __forceinline__ void gauge_rows(C2<R> f0, C2<R> f1, C2<R> f2, C2<R> f3, C2<R> u[3], C2<R> v[3]) {
-  GSFactors o;
   if constexpr (sizeof(R) == sizeof(double)) {
+    GSFactors o;
     gram_schmidt_factors(f0.x, f0.y, f1, f2, f3, o);
     u[0] = mkc<R>(o.i1, f0.x * o.i1);
     u[1] = cscale<R>(f1, o.i1);
@@ -570,6 +556,7 @@ __device__ __forceinline__ void gauge_rows(C2<R> f0, C2<R> f1, C2<R> f2, C2<R> f
 #pragma unroll
     for (int j = 0; j < 3; ++j) v[j] = cscale<double>(o.w[j], o.i2);
   } else {
+    GSFactors o;
     gram_schmidt_factors(f32_to_f64_int(f0.x), f32_to_f64_int(f0.y), c_f32_to_f64_int(f1), c_f32_to_f64_int(f2),
                          c_f32_to_f64_int(f3), o);
     const float i1 = f64_to_f32_int(o.i1), i2 = f64_to_f32_int(o.i2);

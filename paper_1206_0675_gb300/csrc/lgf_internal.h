@@ -69,7 +69,8 @@ inline int64_t measure_blocks(int64_t V) { return (V + MEASURE_THREADS - 1) / ME
 
 // ---- lgf_site.cu -------------------------------------------------------
 // Delta, F and theta of the current links (Sec. 2; kernel k2 of Sec. 3.2).
-// count_iter != 0: this measurement follows a link update (iter += 1).
+// count_iter > 0: this measurement follows count_iter link updates (iter += count_iter):
+// one step of Algorithm 1, or count_iter overrelaxation sweeps.
 // use_cond != 0: set the graph conditional to (theta >= tol && iter < max_iter).
 // count_iter = -1: this measurement follows the undo of a rejected step (iter -= 1).
 // only_if_revert != 0: do nothing unless an undo is pending (st->revert).
@@ -160,6 +161,18 @@ cudaError_t launch_set_identity(const Geom& g, C2<R>* field, cudaStream_t s);
 template <typename R>
 cudaError_t launch_filter_table(const Geom& g, const double* sin2 /* 4 x Lmax: 4 sin^2(pi k/L) */, int lmax,
                                 double alpha, double p2max, int plain_sd, R* K, cudaStream_t s);
+
+// ---- lgf_or.cu ----------------------------------------------------------
+// One colour of an overrelaxation sweep (the local maximisation of F named in
+// Sec. 3.2, Cabibbo-Marinari subgroups, Mandula-Ogilvie overrelaxation):
+// every site x with (x + y + z + t) % 2 == parity gets g(x), and
+// U_mu(x) <- g(x) U_mu(x), U_mu(x - mu^) <- U_mu(x - mu^) g^dag(x), in place.
+// Links of precision R with ROWS stored rows; U1 != nullptr (fused lanes):
+// the current links are U1 when st->ubuf is set, else U0.  G != nullptr:
+// G(x) <- g(x) G(x) (3 rows, precision R).  Every extent must be even.
+template <typename R, int ROWS>
+cudaError_t launch_or_half_sweep(const Geom& g, C2<R>* U0, C2<R>* U1, const DevState* st, C2<R>* G, int parity,
+                                 double omega, cudaStream_t s);
 
 // ---- lgf_fft.cu ---------------------------------------------------------
 // Radix schedule of one lattice direction.

@@ -116,7 +116,7 @@ __device__ __forceinline__ void measure_tail(const Geom& g, double fsum, double 
     int revert = 0;
     int flags = fp64 ? TRACE_FP64 : 0;
     if (count_iter > 0) {
-      it += 1;
+      it += count_iter;  // one FA step, or count_iter overrelaxation sweeps
       st->iter = it;
       st->F_prev = st->F;
       st->theta_prev = st->theta;

@@ -7,6 +7,8 @@ exact-exponential and plain-SD variants, and scans over alpha.
         --modes fp64,fp64_exp,fp64_sd --alphas 0.04,0.06,0.08,0.1,0.12 --tol 1e-12
     python -m paper_1206_0675_gb300.evaluate --run-steps 3 --lattice 32 --eps 1.0 --seeds 0 \
         --modes fp32 --store12 --decomps 2d2d     # a few steps of one lattice (profiling case)
+    python -m paper_1206_0675_gb300.evaluate --lattice 32 --eps 1.0 --seeds 0-3 \
+        --modes fp64,fp64_or,mixed_or --omega 1.7  # overrelaxation against FA-SD (sweeps under "iters")
 
 Prints one JSON line per configuration and a summary line.
 """
@@ -34,11 +36,36 @@ MODES = {
     "fp64_exp": dict(precision="fp64", exact_exp=True),
     "mixed_exp": dict(precision="mixed", store12=True, exact_exp=True),
     "fp64_sd": dict(precision="fp64", plain_sd=True),
+    # overrelaxation (omega = --omega, theta measured every OR_CHECK sweeps)
+    "fp64_or": dict(precision="fp64"),
+    "fp32_or": dict(precision="fp32", store12=True),
+    "mixed_or": dict(precision="mixed", store12=True),
 }
+OR_CHECK = 10
 
 
-def run_mode(mode, ext, U, tol, max_iter, weights, switch=None, alpha=0.08):
+def run_or(mode, ext, U, tol, max_sweeps, omega, switch=None):
+    """Overrelaxation to tol: seconds, sweeps, final F and theta."""
     import torch
+    kw = MODES[mode]
+    with lgf.Lattice(ext, **kw) as lat:
+        if switch is not None and kw["precision"] == "mixed":
+            lat.set_switch_theta(switch)
+        lat.set_links(U)
+        lat.or_fix(tol, 1, omega, OR_CHECK)   # builds the loop graph
+        lat.set_links(U)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        n, F, th, conv = lat.or_fix(tol, max_sweeps, omega, OR_CHECK)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+    return {"seconds": dt, "iters": n, "F": F, "theta": th, "converged": conv, "omega": omega}
+
+
+def run_mode(mode, ext, U, tol, max_iter, weights, switch=None, alpha=0.08, omega=1.7):
+    import torch
+    if mode.endswith("_or"):
+        return run_or(mode, ext, U, tol, max_iter, omega, switch)
     kw = MODES[mode]
     with lgf.Lattice(ext, **kw) as lat:
         if kw.get("learned"):
@@ -122,10 +149,21 @@ def kernel_table(ext, U, steps=20, warmup=5, peak_gbs=None, decomps=("2d2d",), u
     return out
 
 
-def run_steps(ext, eps, seed, mode, store12, decomp, steps, weights):
-    """A few lgf_step calls on one lattice with a fixed plan: the small case a
-    profiler captures one kernel of."""
+def run_steps(ext, eps, seed, mode, store12, decomp, steps, weights, omega=1.7):
+    """A few lgf_step calls (modes fp64_or / fp32_or: overrelaxation sweeps) on
+    one lattice with a fixed plan: the small case a profiler captures one
+    kernel of."""
     import torch
+    if mode.endswith("_or"):
+        U = fields.random_links(ext, eps, seed)
+        with lgf.Lattice(ext, mode[:4], store12=store12) as lat:
+            lat.set_links(U)
+            lat.or_sweep(omega, steps)
+            torch.cuda.synchronize()
+            F, th = lat.measure()
+        print(json.dumps({"extents": ext, "mode": mode, "store12": store12, "sweeps": steps, "omega": omega,
+                          "F": F, "theta": th}), flush=True)
+        return
     prec = {"fp64": "fp64", "fp32": "fp32", "mixed": "mixed", "fp32_learned": "fp32", "fp64_learned": "fp64"}[mode]
     learned = mode.endswith("_learned")
     U = fields.random_links(ext, eps, seed)
@@ -163,12 +201,13 @@ def main():
                     help="only run this many steps of one lattice (first seed, first mode of fp64, fp32, mixed, "
                          "fp32_learned, fp64_learned; first of --decomps) and print F and theta")
     ap.add_argument("--store12", action="store_true", help="with --run-steps: 12-real link storage")
+    ap.add_argument("--omega", type=float, default=1.7, help="overrelaxation parameter of the *_or modes")
     args = ap.parse_args()
     a, b = (int(v) for v in args.seeds.split("-")) if "-" in args.seeds else (int(args.seeds),) * 2
     ext = tuple(int(v) for v in args.extents.split(",")) if args.extents else (args.lattice,) * 4
     if args.run_steps:
         run_steps(ext, args.eps, a, args.modes.split(",")[0], args.store12, args.decomps.split(",")[0], args.run_steps,
-                  np.load(args.weights))
+                  np.load(args.weights), args.omega)
         return
     if args.kernels:
         peak = None
@@ -193,7 +232,7 @@ def main():
         U = fields.random_links(ext, args.eps, seed)
         row = {"lattice": list(ext), "eps": args.eps, "seed": seed}
         for m, al, key in runs:
-            r = run_mode(m, ext, U, args.tol, args.max_iter, weights, args.switch, al)
+            r = run_mode(m, ext, U, args.tol, args.max_iter, weights, args.switch, al, args.omega)
             row[key] = r
             tot[key][0] += r["seconds"]
             tot[key][1] += r["iters"]

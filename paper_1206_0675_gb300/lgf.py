@@ -62,6 +62,9 @@ SIGNATURES = [
     ("lgf_measure", ctypes.c_int, [ctypes.c_void_p, _c_dbl_p, _c_dbl_p]),
     ("lgf_fix", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int32, ctypes.c_double, _c_int_p,
                                _c_dbl_p, _c_dbl_p]),
+    ("lgf_or_sweep", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int32]),
+    ("lgf_or_fix", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
+                                  _c_int_p, _c_dbl_p, _c_dbl_p]),
     ("lgf_get_transform", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     ("lgf_get_gauge", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     ("lgf_get_divergence", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
@@ -213,6 +216,20 @@ def lgf_fix(h: int, theta_tol: float, max_iter: int, alpha: float) -> tuple[int,
                                 ctypes.byref(F), ctypes.byref(th))
     _check(h, st, "lgf_fix", allow=(LGF_E_NOTCONV,))
     return it.value, F.value, th.value, st
+
+
+def lgf_or_sweep(h: int, omega: float, nsweeps: int) -> None:
+    _check(h, load_library().lgf_or_sweep(ctypes.c_void_p(h), float(omega), int(nsweeps)), "lgf_or_sweep")
+
+
+def lgf_or_fix(h: int, theta_tol: float, max_sweeps: int, omega: float,
+               check_every: int) -> tuple[int, float, float, int]:
+    """Returns (sweeps, F, theta, status); status is LGF_OK or LGF_E_NOTCONV."""
+    n, F, th = ctypes.c_int32(), ctypes.c_double(), ctypes.c_double()
+    st = load_library().lgf_or_fix(ctypes.c_void_p(h), float(theta_tol), int(max_sweeps), float(omega),
+                                   int(check_every), ctypes.byref(n), ctypes.byref(F), ctypes.byref(th))
+    _check(h, st, "lgf_or_fix", allow=(LGF_E_NOTCONV,))
+    return n.value, F.value, th.value, st
 
 
 def lgf_get_transform(h: int, ptr: int, where: int) -> None:
@@ -539,6 +556,15 @@ class Lattice:
         """Returns (iters, F, theta, converged)."""
         it, F, th, st = lgf_fix(self.handle, theta_tol, max_iter, alpha)
         return it, F, th, st == LGF_OK
+
+    def or_sweep(self, omega: float = 1.7, nsweeps: int = 1) -> None:
+        """nsweeps overrelaxation sweeps (even colour, then odd), then a measurement."""
+        lgf_or_sweep(self.handle, omega, nsweeps)
+
+    def or_fix(self, theta_tol: float = 1e-15, max_sweeps: int = 100000, omega: float = 1.7, check_every: int = 1):
+        """Overrelaxation gauge fixing; returns (sweeps, F, theta, converged)."""
+        n, F, th, st = lgf_or_fix(self.handle, theta_tol, max_sweeps, omega, check_every)
+        return n, F, th, st == LGF_OK
 
     def set_trace(self, cap: int, flags: bool = False):
         """Record F and theta of every measurement of the next fix(); returns the (F, theta) arrays, or
