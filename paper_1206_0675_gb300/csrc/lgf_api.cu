@@ -127,6 +127,11 @@ struct lgf_ctx {
   double defect_bound32 = 1e-4;   // the same for FP32 phases
   int repairs = 0;                // reunitarisations of the links during the last lgf_fix
   TimingRing timing;
+  // lgf_set_links from host memory: the copy runs in kSetChunks pieces on the
+  // handle's stream and the SU(3) check of each piece on cap_stream as soon as
+  // it has arrived, so that the check overlaps the copy of the next piece
+  static constexpr int kSetChunks = 8;
+  cudaEvent_t set_ev[kSetChunks + 1] = {};
   double switch_theta = 1e-9;     // FP32 -> FP64 switch level of LGF_MIXED
   bool learned = false;           // LGF_LEARNED
   float* mtab = nullptr;          // learned multiplier tables of even and odd steps [2][nclass]
@@ -787,6 +792,8 @@ lgf_status lgf_destroy(lgf_handle h) {
   if (h->st_host) cudaFreeHost(h->st_host);
   if (h->defect_host) cudaFreeHost(h->defect_host);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  for (cudaEvent_t e : h->set_ev)
+    if (e) cudaEventDestroy(e);
   for (int i = 0; i < TimingRing::kSlots; ++i)
     for (int k = 0; k <= TimingRing::kMaxK; ++k)
       if (h->timing.ev[i][k]) cudaEventDestroy(h->timing.ev[i][k]);
@@ -855,6 +862,8 @@ lgf_status lgf_create_with_allocator(const int32_t extents[4], lgf_precision pre
       if (e == cudaSuccess) e = cudaMallocHost((void**)&h->st_host, sizeof(DevState));
       if (e == cudaSuccess) e = cudaMallocHost((void**)&h->defect_host, sizeof(unsigned long long));
       if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+      for (cudaEvent_t& ev : h->set_ev)
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
       h->lmax = 0;
       for (int mu = 0; mu < 4; ++mu) h->lmax = std::max(h->lmax, g.L[mu]);
       std::vector<double> sin2((size_t)4 * h->lmax, 0.0);
@@ -897,10 +906,28 @@ lgf_status lgf_set_links(lgf_handle h, const double* U, int where) {
     const size_t n = (size_t)4 * 18 * g.V;
     const double* src = U;
     if (where == LGF_HOST) {
-      LGF_CK(h, cudaMemcpyAsync(h->stage, U, n * 8, cudaMemcpyHostToDevice, h->stream));
+      // piece k of the links: copy on the handle's stream, check on cap_stream
+      // after the copy's event; the stream waits for the last check
+      const int64_t nmat = 4 * g.V, per = (nmat + lgf_ctx::kSetChunks - 1) / lgf_ctx::kSetChunks;
+      LGF_CK(h, cudaMemsetAsync(h->defect, 0, sizeof(unsigned long long), h->stream));
+      LGF_CK(h, cudaEventRecord(h->set_ev[lgf_ctx::kSetChunks], h->stream));
+      LGF_CK(h, cudaStreamWaitEvent(h->cap_stream, h->set_ev[lgf_ctx::kSetChunks], 0));
+      for (int k = 0; k < lgf_ctx::kSetChunks; ++k) {
+        const int64_t m0 = k * per, m1 = std::min(nmat, m0 + per);
+        if (m1 <= m0) break;
+        const size_t off = (size_t)m0 * 18;
+        LGF_CK(h, cudaMemcpyAsync(h->stage + off, U + off, (size_t)(m1 - m0) * 18 * 8, cudaMemcpyHostToDevice,
+                                  h->stream));
+        LGF_CK(h, cudaEventRecord(h->set_ev[k], h->stream));
+        LGF_CK(h, cudaStreamWaitEvent(h->cap_stream, h->set_ev[k], 0));
+        LGF_CK(h, launch_su3_defect(h->stage + off, m1 - m0, h->defect, h->cap_stream, /*reset=*/0));
+      }
+      LGF_CK(h, cudaEventRecord(h->set_ev[lgf_ctx::kSetChunks], h->cap_stream));
+      LGF_CK(h, cudaStreamWaitEvent(h->stream, h->set_ev[lgf_ctx::kSetChunks], 0));
       src = h->stage;
+    } else {
+      LGF_CK(h, launch_su3_defect(src, 4 * g.V, h->defect, h->stream));
     }
-    LGF_CK(h, launch_su3_defect(src, 4 * g.V, h->defect, h->stream));
     LGF_CK(h, cudaMemcpyAsync(h->defect_host, h->defect, 8, cudaMemcpyDeviceToHost, h->stream));
     LGF_CK(h, cudaStreamSynchronize(h->stream));
     double defect;

@@ -513,6 +513,33 @@ __device__ __forceinline__ void gram_schmidt_factors(double a, double d, double2
   o.i2 = rsqrt_fp64(n2);
 }
 
+// The FP64 factors for fields stored in FP32: i1 = 1/|r1|, the projection
+// coefficient k = <r1, r2>/|r1|^2 and i2 = 1/|w| with w = r2 - k r1, where
+// |w|^2 = |r2|^2 - |<r1, r2>|^2/|r1|^2 (Pythagoras for the projection) is
+// formed from the inputs, so that w itself is never needed in FP64: the
+// FP32 field applies k in FP32.  For 1 + X with X anti-Hermitian the rows are
+// nearly orthogonal (|<r1, r2>| <= |X|^2 while |r1|, |r2| >= 1), so the
+// difference does not cancel.  33 FP64 operations and two estimates, against
+// 43 when w is formed in FP64.
+struct GSFactors32 {
+  double i1, i2, kx, ky;
+};
+
+__device__ __forceinline__ void gram_schmidt_factors_f32(double a, double d, double2 f1, double2 f2, double2 f3,
+                                                         GSFactors32& o) {
+  const double n1 = fma(f2.x, f2.x, fma(f2.y, f2.y, fma(f1.x, f1.x, fma(f1.y, f1.y, fma(a, a, 1.0)))));
+  o.i1 = rsqrt_fp64(n1);
+  const double s = a + d;
+  const double q = o.i1 * o.i1;  // 1 / |r1|^2
+  const double cx = fma(f2.x, f3.x, fma(f2.y, f3.y, s * f1.y));
+  const double cy = fma(f2.x, f3.y, fma(-f2.y, f3.x, s * f1.x));
+  const double nr2 = fma(f3.x, f3.x, fma(f3.y, f3.y, fma(d, d, fma(f1.x, f1.x, fma(f1.y, f1.y, 1.0)))));
+  const double n2 = fma(-q, fma(cx, cx, cy * cy), nr2);
+  o.kx = q * cx;
+  o.ky = q * cy;
+  o.i2 = rsqrt_fp64(n2);
+}
+
 // FP32 <-> FP64 conversions on the integer pipe, written from the IEEE 754
 // binary32 / binary64 layouts.  On this GPU the conversion instructions run
 // on the FP64 pipe, which bounds pass C of FP32 lanes; these take sign,
@@ -556,15 +583,22 @@ __device__ __forceinline__ void gauge_rows(C2<R> f0, C2<R> f1, C2<R> f2, C2<R> f
 #pragma unroll
     for (int j = 0; j < 3; ++j) v[j] = cscale<double>(o.w[j], o.i2);
   } else {
-    GSFactors o;
-    gram_schmidt_factors(f32_to_f64_int(f0.x), f32_to_f64_int(f0.y), c_f32_to_f64_int(f1), c_f32_to_f64_int(f2),
-                         c_f32_to_f64_int(f3), o);
-    const float i1 = f64_to_f32_int(o.i1), i2 = f64_to_f32_int(o.i2);
-    u[0] = mkc<R>(i1, f0.x * i1);
+    GSFactors32 o32;
+    gram_schmidt_factors_f32(f32_to_f64_int(f0.x), f32_to_f64_int(f0.y), c_f32_to_f64_int(f1), c_f32_to_f64_int(f2),
+                             c_f32_to_f64_int(f3), o32);
+    const float i1 = f64_to_f32_int(o32.i1), i2 = f64_to_f32_int(o32.i2);
+    const float kx = f64_to_f32_int(o32.kx), ky = f64_to_f32_int(o32.ky);
+    const float a = f0.x, d = f0.y;
+    u[0] = mkc<R>(i1, a * i1);
     u[1] = cscale<R>(f1, i1);
     u[2] = cscale<R>(f2, i1);
-#pragma unroll
-    for (int j = 0; j < 3; ++j) v[j] = cscale<R>(c_f64_to_f32_int(o.w[j]), i2);
+    // w = r2 - k r1 in FP32, normalised by the FP64 factor
+    const C2<R> w0 = mkc<R>(fmaf(ky, a, -f1.x - kx), fmaf(-kx, a, f1.y - ky));
+    const C2<R> w1 = mkc<R>(fmaf(ky, f1.y, fmaf(-kx, f1.x, 1.f)), fmaf(-ky, f1.x, fmaf(-kx, f1.y, d)));
+    const C2<R> w2 = mkc<R>(fmaf(ky, f2.y, fmaf(-kx, f2.x, f3.x)), fmaf(-ky, f2.x, fmaf(-kx, f2.y, f3.y)));
+    v[0] = cscale<R>(w0, i2);
+    v[1] = cscale<R>(w1, i2);
+    v[2] = cscale<R>(w2, i2);
   }
 }
 

@@ -131,7 +131,9 @@ cudaError_t launch_delta_to_aos(const Geom& g, const C2<R>* delta, double* aos, 
 
 // Largest SU(3) defect max(|U U^dag - 1|, |det U - 1|) of an AoS link array,
 // as the bit pattern of a non-negative double (NaN maps to +inf bits).
-cudaError_t launch_su3_defect(const double* aos, int64_t nmat, unsigned long long* out_bits, cudaStream_t s);
+// reset = 0: fold into the maximum already in *out_bits (checks of pieces).
+cudaError_t launch_su3_defect(const double* aos, int64_t nmat, unsigned long long* out_bits, cudaStream_t s,
+                              int reset = 1);
 
 // Loop parameters of the controller state (tol, max_iter, history);
 // reset_iter != 0 also zeroes the iteration counter and the status word.

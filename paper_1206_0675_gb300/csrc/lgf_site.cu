@@ -681,9 +681,12 @@ __global__ void su3_defect_kernel(const double2* __restrict__ aos, int64_t nmat,
   }
 }
 
-cudaError_t launch_su3_defect(const double* aos, int64_t nmat, unsigned long long* out_bits, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(out_bits, 0, sizeof(unsigned long long), s);
-  if (e != cudaSuccess) return e;
+cudaError_t launch_su3_defect(const double* aos, int64_t nmat, unsigned long long* out_bits, cudaStream_t s,
+                              int reset) {
+  if (reset) {
+    cudaError_t e = cudaMemsetAsync(out_bits, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+  }
   const int64_t blocks = std::min<int64_t>((nmat + CONV_THREADS - 1) / CONV_THREADS, 152 * 8);
   su3_defect_kernel<<<(unsigned)(blocks > 0 ? blocks : 1), CONV_THREADS, 0, s>>>(
       reinterpret_cast<const double2*>(aos), nmat, out_bits);
