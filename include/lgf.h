@@ -26,8 +26,11 @@
  *   from CUDA's stream-ordered allocator or from a caller-supplied allocator
  *   (lgf_create_with_allocator).
  * Streams: all device work of a handle runs on the stream given to
- *   lgf_create (NULL = the legacy default stream).  lgf_step is asynchronous;
- *   every call that returns numbers to the host synchronises that stream.
+ *   lgf_create (NULL = the legacy default stream), except that lgf_set_links
+ *   from host memory checks the copied pieces on a second, internal stream
+ *   of the handle, which it joins to the first before returning.  lgf_step
+ *   is asynchronous; every call that returns numbers to the host
+ *   synchronises that stream.
  * Errors: every call returns an lgf_status and never aborts; no C++
  *   exception crosses this interface.  A CUDA error is sticky for the handle:
  *   afterwards only lgf_destroy and lgf_last_error are meaningful.
@@ -323,6 +326,15 @@ lgf_status lgf_get_timing(lgf_handle h, double* ms, int32_t nkernels, int32_t* n
 /* Load BF16 network parameters (n_w must be LGF_MLP_NPARAM) into the
  * handle; where = LGF_HOST or LGF_DEVICE.  Synchronises. */
 lgf_status lgf_load_preconditioner(lgf_handle h, const uint16_t* bf16_w, size_t n_w, int where);
+
+/* Level below which the learned multiplier is applied (not in the paper: a
+ * setting of the learned filter).  A step of an LGF_LEARNED handle from
+ * links with theta >= theta uses the plain filter of Eq. (eq:gx) (the
+ * network still runs, and writes a table of ones); below it the learned
+ * table.  Default +inf: every step.  0 gives the plain method exactly.
+ * LGF_E_STATE on a handle without LGF_LEARNED, LGF_E_ARG for a negative or
+ * NaN level.  Takes effect from the next step. */
+lgf_status lgf_set_learned_theta(lgf_handle h, double theta);
 
 /* Number of learned steps that were rejected (F did not increase) and redone
  * with the plain filter during the last lgf_fix. */

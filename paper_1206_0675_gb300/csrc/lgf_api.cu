@@ -253,6 +253,7 @@ template <typename R> lgf_status alloc_lane(lgf_ctx* h, Lane<R>& L, int rows, in
   }
   L.mg.m_lo = MLP_M_LO;
   L.mg.m_hi = MLP_M_HI;
+  L.mg.theta_on = INFINITY;  // every step (lgf_set_learned_theta)
   LGF_CK(h, h->mem.get(&L.p2f, p2.size()));
   LGF_CK(h, cudaMemcpyAsync(L.p2f, p2.data(), p2.size() * sizeof(float), cudaMemcpyHostToDevice, h->stream));
   if (h->learned) {
@@ -1411,6 +1412,19 @@ lgf_status lgf_mlp_train(float* P, float* adam, const float* X, const float* Y, 
 lgf_status lgf_mlp_to_bf16(const float* P, uint16_t* out, void* cuda_stream) {
   if (!P || !out) return LGF_E_ARG;
   return launch_f32_to_bf16(P, out, MLP_NPARAM, (cudaStream_t)cuda_stream) == cudaSuccess ? LGF_OK : LGF_E_CUDA;
+}
+
+lgf_status lgf_set_learned_theta(lgf_handle h, double theta) {
+  lgf_status s = check_handle(h);
+  if (s != LGF_OK) return s;
+  if (!h->learned) return fail(h, LGF_E_STATE, "not an LGF_LEARNED handle");
+  if (!(theta >= 0.0)) return fail(h, LGF_E_ARG, "the learned level must be >= 0 (or +inf)");
+  // the level is a kernel argument of the captured loop bodies: capture again
+  h->d.mg.theta_on = theta;
+  drop_graph(h->d);
+  h->f.mg.theta_on = theta;
+  drop_graph(h->f);
+  return LGF_OK;
 }
 
 lgf_status lgf_set_switch_theta(lgf_handle h, double theta) {

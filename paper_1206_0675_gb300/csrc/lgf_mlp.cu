@@ -206,8 +206,11 @@ __global__ void __launch_bounds__(128) mlp_multiplier_kernel(const __nv_bfloat16
     sf[2] = iter > 0 ? mlp_rate_feature(theta, theta_prev) : 0.f;
   }
   __syncthreads();
+  // the plain filter: a redo of a rejected step, or a step from links whose
+  // theta is not yet below the level where the table is applied
+  const bool plain = redo || !(st->theta < mg.theta_on);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    st->use_m = redo ? 0 : 1;
+    st->use_m = plain ? 0 : 1;
     st->redo = redo;
   }
   float* mtab = mtab_base + (int64_t)(iter & 1) * mg.nclass;
@@ -220,7 +223,7 @@ __global__ void __launch_bounds__(128) mlp_multiplier_kernel(const __nv_bfloat16
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t n = mg.nclass;
   for (int64_t base = wid * 16; base < n; base += nw * 16) {
-    if (redo) {
+    if (plain) {
       if (tig == 0) {
         if (base + g < n) mtab[base + g] = 1.f;
         if (base + g + 8 < n) mtab[base + g + 8] = 1.f;

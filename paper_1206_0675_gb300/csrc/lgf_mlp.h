@@ -25,6 +25,7 @@ struct MlpGeom {
   int off[4];      // offsets of the per-direction p2 tables
   int64_t nclass;
   float m_lo, m_hi;
+  double theta_on;  // the table is applied only to steps from links with theta < theta_on
 };
 
 // bucket index of the mode log: b = clamp(4 - 2 * bucket(theta), 0, 39)
@@ -44,7 +45,8 @@ cudaError_t launch_mlp_eval(const uint16_t* P, const float* X, int64_t n, float*
 // snapshots [2][4][V] (BF16 pairs) that the filter passes write, slot k & 1 at step
 // k; with st->snaps >= 2 the class contraction of the last step is formed
 // from slots (k - 1) & 1 (divergence k - 1) and k & 1 (divergence k - 2).
-// A step that redoes a rejected one writes m = 1 (the plain filter it uses).
+// A step that redoes a rejected one, or starts from links with
+// theta >= mg.theta_on, writes m = 1 (the plain filter it uses).
 cudaError_t launch_mlp_multiplier(const uint16_t* P, const MlpGeom& mg, const Geom& g, const float* p2, DevState* st,
                                   float* mtab, const uint32_t* snap, cudaStream_t s);
 size_t mlp_train_smem();

@@ -62,7 +62,7 @@ def run_or(mode, ext, U, tol, max_sweeps, omega, switch=None):
     return {"seconds": dt, "iters": n, "F": F, "theta": th, "converged": conv, "omega": omega}
 
 
-def run_mode(mode, ext, U, tol, max_iter, weights, switch=None, alpha=0.08, omega=1.7):
+def run_mode(mode, ext, U, tol, max_iter, weights, switch=None, alpha=0.08, omega=1.7, learned_theta=None):
     import torch
     if mode.endswith("_or"):
         return run_or(mode, ext, U, tol, max_iter, omega, switch)
@@ -70,6 +70,8 @@ def run_mode(mode, ext, U, tol, max_iter, weights, switch=None, alpha=0.08, omeg
     with lgf.Lattice(ext, **kw) as lat:
         if kw.get("learned"):
             lat.load_preconditioner(weights)
+            if learned_theta is not None:
+                lat.set_learned_theta(learned_theta)
         if switch is not None and kw["precision"] == "mixed":
             lat.set_switch_theta(switch)
         lat.set_links(U)
@@ -202,6 +204,8 @@ def main():
                          "fp32_learned, fp64_learned; first of --decomps) and print F and theta")
     ap.add_argument("--store12", action="store_true", help="with --run-steps: 12-real link storage")
     ap.add_argument("--omega", type=float, default=1.7, help="overrelaxation parameter of the *_or modes")
+    ap.add_argument("--learned-theta", default=None,
+                    help="comma-separated levels below which the learned modes apply the table (a scan if several)")
     args = ap.parse_args()
     a, b = (int(v) for v in args.seeds.split("-")) if "-" in args.seeds else (int(args.seeds),) * 2
     ext = tuple(int(v) for v in args.extents.split(",")) if args.extents else (args.lattice,) * 4
@@ -226,20 +230,22 @@ def main():
     weights = np.load(args.weights)
     alphas = [float(v) for v in args.alphas.split(",")]
     scan = len(alphas) > 1
-    runs = [(m, al, f"{m}@{al:g}" if scan else m) for al in alphas for m in args.modes.split(",")]
-    tot = {key: [0.0, 0, 0] for _, _, key in runs}
+    levels = [None] if args.learned_theta is None else [float(v) for v in args.learned_theta.split(",")]
+    runs = [(m, al, lv, (f"{m}@{al:g}" if scan else m) + (f"<{lv:g}" if lv is not None and "learned" in m else ""))
+            for al in alphas for m in args.modes.split(",") for lv in (levels if "learned" in m else [None])]
+    tot = {key: [0.0, 0, 0] for _, _, _, key in runs}
     for seed in range(a, b + 1):
         U = fields.random_links(ext, args.eps, seed)
         row = {"lattice": list(ext), "eps": args.eps, "seed": seed}
-        for m, al, key in runs:
-            r = run_mode(m, ext, U, args.tol, args.max_iter, weights, args.switch, al, args.omega)
+        for m, al, lv, key in runs:
+            r = run_mode(m, ext, U, args.tol, args.max_iter, weights, args.switch, al, args.omega, lv)
             row[key] = r
             tot[key][0] += r["seconds"]
             tot[key][1] += r["iters"]
             tot[key][2] += int(not r["converged"])
         print(json.dumps(row), flush=True)
     summary = {k: {"seconds": v[0], "iters": v[1], "not_converged": v[2]} for k, v in tot.items()}
-    for m, al, key in runs:
+    for m, al, _, key in runs:
         base = f"fp64@{al:g}" if scan else "fp64"
         if base in tot:
             summary[key]["speedup_vs_fp64"] = tot[base][0] / tot[key][0]

@@ -62,6 +62,7 @@ SIGNATURES = [
     ("lgf_measure", ctypes.c_int, [ctypes.c_void_p, _c_dbl_p, _c_dbl_p]),
     ("lgf_fix", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int32, ctypes.c_double, _c_int_p,
                                _c_dbl_p, _c_dbl_p]),
+    ("lgf_set_learned_theta", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
     ("lgf_or_sweep", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int32]),
     ("lgf_or_fix", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
                                   _c_int_p, _c_dbl_p, _c_dbl_p]),
@@ -216,6 +217,10 @@ def lgf_fix(h: int, theta_tol: float, max_iter: int, alpha: float) -> tuple[int,
                                 ctypes.byref(F), ctypes.byref(th))
     _check(h, st, "lgf_fix", allow=(LGF_E_NOTCONV,))
     return it.value, F.value, th.value, st
+
+
+def lgf_set_learned_theta(h: int, theta: float) -> None:
+    _check(h, load_library().lgf_set_learned_theta(ctypes.c_void_p(h), float(theta)), "lgf_set_learned_theta")
 
 
 def lgf_or_sweep(h: int, omega: float, nsweeps: int) -> None:
@@ -556,6 +561,10 @@ class Lattice:
         """Returns (iters, F, theta, converged)."""
         it, F, th, st = lgf_fix(self.handle, theta_tol, max_iter, alpha)
         return it, F, th, st == LGF_OK
+
+    def set_learned_theta(self, theta: float) -> None:
+        """Apply the learned multiplier only to steps from links with theta below this level."""
+        lgf_set_learned_theta(self.handle, theta)
 
     def or_sweep(self, omega: float = 1.7, nsweeps: int = 1) -> None:
         """nsweeps overrelaxation sweeps (even colour, then odd), then a measurement."""

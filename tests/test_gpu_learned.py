@@ -232,6 +232,59 @@ def test_learned_step_api_redoes_rejected_steps(torch):
             F_prev = F
 
 
+def test_learned_level_zero_is_the_plain_method(torch):
+    """With the learned level at 0 no step uses the table: a learned handle
+    runs the plain method bit for bit (a multiplier of 2 would otherwise
+    overshoot at this alpha and be redone)."""
+    ext = (6, 4, 8, 4)
+    U = fields.random_links(ext, eps=0.9, seed=21)
+    out = []
+    for learned in (True, False):
+        with lgf.Lattice(ext, "fp64", learned=learned) as lat:
+            if learned:
+                lat.load_preconditioner(constant_multiplier_bits(3.0))
+                lat.set_learned_theta(0.0)
+            lat.set_links(U)
+            Fh, Th = lat.set_trace(31)
+            it, F, th, conv = lat.fix(0.0, 30, 0.128)
+            out.append((Fh.copy(), Th.copy(), lat.get_links(), lat.fallbacks() if learned else 0))
+    a, b = out
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+    assert a[3] == 0
+
+
+def test_learned_level_gates_steps_by_theta(torch):
+    """Steps from links with theta at or above the level use the plain filter
+    (no learned flag in the trace); the others use the table (m = 1.10)."""
+    ext = (6, 4, 8, 4)
+    U = fields.random_links(ext, eps=0.9, seed=21)
+    with lgf.Lattice(ext, "fp64") as lat:
+        lat.set_links(U)
+        Fp, Tp = lat.set_trace(41)
+        lat.fix(0.0, 40, 0.08)
+    level = float(Tp[12])  # about a third of the way down
+    with lgf.Lattice(ext, "fp64", learned=True) as lat:
+        lat.load_preconditioner(constant_multiplier_bits(0.7))
+        lat.set_learned_theta(level)
+        lat.set_links(U)
+        Fh, Th, Fl, Dh = lat.set_trace(41, flags=True)
+        it, F, th, conv = lat.fix(0.0, 40, 0.08)
+        assert lat.fallbacks() == 0
+    on = [(Fl[k] & lgf.LGF_TRACE_LEARNED) != 0 for k in range(1, 41)]
+    for k in range(1, 41):
+        assert on[k - 1] == (Th[k - 1] < level), k
+    assert any(on) and not all(on)
+    # until the level is reached the run is the plain one
+    first = on.index(True) + 1
+    assert np.array_equal(Fh[:first], Fp[:first]) and np.array_equal(Th[:first], Tp[:first])
+    with pytest.raises(lgf.LgfError):
+        lat2 = lgf.Lattice(ext, "fp64")
+        try:
+            lat2.set_learned_theta(1e-6)  # not a learned handle
+        finally:
+            lat2.close()
+
+
 def packed_hat(D):
     """Fourier transforms of the four packed divergence fields from the oracle's 3x3 Delta_A."""
     Dh = O.fft4(D)
