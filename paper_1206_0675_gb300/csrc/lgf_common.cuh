@@ -169,6 +169,21 @@ __device__ __forceinline__ int64_t site_back(const Geom& g, int64_t s, const int
   return c[mu] == 0 ? s + (int64_t)(g.L[mu] - 1) * g.stride[mu] : s - g.stride[mu];
 }
 
+// x + mu^ and x - mu^ for a direction known only at run time, by selects:
+// coordinates and geometry stay in registers (no local-memory copy of c[]
+// or of the geometry inside a loop over mu).
+__device__ __forceinline__ void site_nbrs_sel(const Geom& g, int64_t s, const int c[4], int mu, int64_t& fwd,
+                                              int64_t& back) {
+  int cm = c[0], L = g.L[0];
+  int64_t st = 1;
+  if (mu == 1) { cm = c[1]; L = g.L[1]; st = g.stride[1]; }
+  if (mu == 2) { cm = c[2]; L = g.L[2]; st = g.stride[2]; }
+  if (mu == 3) { cm = c[3]; L = g.L[3]; st = g.stride[3]; }
+  const int64_t wrap = (int64_t)(L - 1) * st;
+  fwd = cm == L - 1 ? s - wrap : s + st;
+  back = cm == 0 ? s + wrap : s - st;
+}
+
 __device__ __forceinline__ int64_t site_fwd(const Geom& g, int64_t s, const int c[4], int mu) {
   return c[mu] == g.L[mu] - 1 ? s - (int64_t)(g.L[mu] - 1) * g.stride[mu] : s + g.stride[mu];
 }

@@ -406,7 +406,9 @@ update_kernel(Geom g, MatField<R, LROWS> U, MatField<R, GROWS> Gf, Batch B) {
     M3<R> u;
     U.load(mu, s, u);
     M3<R> h;
-    Gf.load_ro(0, site_fwd(g, s, c, mu), h);
+    int64_t sf, sb;
+    site_nbrs_sel(g, s, c, mu, sf, sb);  // selects: no local-memory copy of c[] in the loop
+    Gf.load_ro(0, sf, h);
     // T = g(x)[rows 0,1] * U
     C2<R> T[2][3];
 #pragma unroll
