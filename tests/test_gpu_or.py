@@ -261,7 +261,7 @@ def test_full_size_32x4_one_sweep_fp32_12real(sweep_32x4):
     # The SU(2) maximiser r = b~/|b| passes the FP32 rounding of the local
     # field on amplified by |w|/|b|, large where a subgroup block is small: over
     # the 4 x 2^20 links of this field the largest entry error is 6.3e-6, about
-    # a hundred FP32 units; bounded by the benchmark spec's FP32 tolerance.
+    # a hundred FP32 units; bounded by the 1e-5 relative FP32 tolerance of the FP32 paths.
     assert np.max(np.abs(U1 - Uo)) < 1e-5
 
 
