@@ -10,8 +10,10 @@ F and theta) in plain FP64 with 18-real links, run through the C-ABI.
 Printed: one JSON line with iterations/s (the headline), site updates/s,
 per-kernel times, the roofline of the dominant kernel, the FP32 12-real
 rate, the wall time to theta < 1e-15 of plain FP64 and of the mixed
-FP32 -> FP64 mode, an end-to-end figure through host buffers, the CPU
-oracle's rate on the host cores, and the SM clocks seen while timing.
+FP32 -> FP64 mode (with and without the learned multiplier), the 64-lattice
+batch, overrelaxation sweeps/s and its time to theta < 1e-15 (the other
+gauge-fixing method of Sec. 3.2), an end-to-end figure through host buffers,
+the CPU oracle's rate on the host cores, and the SM clocks seen while timing.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lgf|reference]
 
